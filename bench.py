@@ -1,0 +1,340 @@
+"""Benchmark: masked forward+backward of MaskGaussian's rasteriser on GB300.
+
+One step = the whole hot path over one view of the 1.2M-Gaussian clustered
+scene at 1557x1038: mask sampling + preprocess, binning, radix sort, tile
+ranges, masked render, L1 loss gradient, render backward, preprocess
+backward.  Inputs are resident in HBM; they (293 MB of parameters) are larger
+than the 129 MB L2, so no separate flush is done.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (FP64,
+host cores) on a bounded crop of the same workload.  Under torchrun (N > 1)
+every rank renders its own replica (no data-path collective: the views are
+independent); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "masked fwd+bwd ms & Mpix/s per view (1.2M Gaussians, 1557x1038) vs plain FP32 form"
+WORKLOAD = "scene-scale single view, FP32: 1.2M clustered Gaussians, 1557x1038, f=1150"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 flops per evaluated (pixel, splat) pair of the render kernels, counted
+# from the arithmetic of the method (FMA = 2, ex2 / div = 1); see the design doc.
+FLOPS_FWD_PER_FRAG = 24
+FLOPS_BWD_PER_FRAG = 62
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2412_20522_gb300 import abi, scenes
+    from paper_2412_20522_gb300.rasterize import PARAM_NAMES, RasterConfig, Rasterizer
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    g, cams, target = scenes.scene_workload()
+    W, H = cams[0].width, cams[0].height
+    params = {k: torch.as_tensor(np.ascontiguousarray(getattr(g, k))).to(dev)
+              for k in PARAM_NAMES}
+    tgt = torch.as_tensor(target).to(dev).reshape(-1)
+    cfg = RasterConfig()
+    rast = Rasterizer(dev)
+    grads = {k: torch.empty_like(v) for k, v in params.items()}
+    stream = torch.cuda.current_stream(dev)
+
+    # size the instance buffers once (one synchronising step), then run the
+    # whole sequence asynchronously
+    rast.forward(params, cams, cfg, check=True)
+    torch.cuda.synchronize()
+
+    stage_names = ["preprocess", "bin", "sort", "render", "loss", "render_bwd", "preprocess_bwd"]
+
+    def step(ev=None, count=False):
+        img = rast.forward(params, cams, cfg, check=False, count_fragments=count,
+                           stage_events=ev)
+        if ev is not None:
+            ev["loss"][0].record(stream)
+        loss, dimg = rast.l1_loss_grad(img, tgt)
+        if ev is not None:
+            ev["loss"][1].record(stream)
+        rast.backward(dimg, grads, stage_events=ev)
+        return loss
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = abi.mg_read_status(rast.status, rast._stream())
+    if st.status != abi.MG_OK:
+        raise RuntimeError(f"device status {st.status} after warm-up")
+
+    # per-stage CUDA events over the timed steps (same stream as the kernels)
+    evs = [{k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for k in stage_names} for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stage_ms = {k: statistics.mean(e[k][0].elapsed_time(e[k][1]) for e in evs) for k in stage_names}
+
+    # counts of this workload (one extra counted step, outside the timed region)
+    step(count=True)
+    torch.cuda.synchronize()
+    frags = int(rast.frag_count.item())
+    K = int(rast.num_instances.item())
+    so = rast.splat_outputs()
+    visible = int((so["radius"] > 0).sum().item())
+    mask_on = float(so["mask"].float().mean().item())
+    gpu_launches_per_step = rast.launches_per_step() + 1 + rast.backward_launches()
+
+    # end to end through the C ABI with host buffers: pinned H2D of the
+    # parameters and target, the step, D2H of the image, loss and gradients
+    host_params = {k: v.cpu().pin_memory() for k, v in params.items()}
+    host_tgt = tgt.cpu().pin_memory()
+    host_img = torch.empty(3 * W * H, dtype=torch.float32).pin_memory()
+    host_grads = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in params.items()}
+    host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host_params.values()) + host_tgt.numel() * 4
+    d2h = host_img.numel() * 4 + 4 + sum(v.numel() * v.element_size() for v in host_grads.values())
+
+    def e2e_step():
+        for k in PARAM_NAMES:
+            params[k].copy_(host_params[k], non_blocking=True)
+        tgt.copy_(host_tgt, non_blocking=True)
+        img = rast.forward(params, cams, cfg, check=False)
+        loss, dimg = rast.l1_loss_grad(img, tgt)
+        rast.backward(dimg, grads)
+        host_img.copy_(img, non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+        for k in PARAM_NAMES:
+            host_grads[k].copy_(grads[k], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_n = max(3, args.steps // 2)
+    for _ in range(e2e_n):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_n
+
+    peaks, peak_src = _peaks()
+    mpix = W * H / 1e6
+    # dominant kernel: the stage with the largest share
+    dom = max(("render_bwd", "render", "sort", "preprocess", "preprocess_bwd"),
+              key=lambda k: stage_ms[k])
+    smmax = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak_tflops = sms * 128 * 2 * smmax * 1e6 / 1e12
+    if dom in ("render", "render_bwd"):
+        per = FLOPS_FWD_PER_FRAG if dom == "render" else FLOPS_BWD_PER_FRAG
+        achieved = frags * per / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)"}
+    else:
+        bytes_per = {"sort": K * 152, "preprocess": g.n * 244 + visible * 60,
+                     "preprocess_bwd": g.n * (244 + 244) + visible * 48}[dom]
+        achieved = bytes_per / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved,
+                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                "peak_source": peak_src}
+
+    line = {
+        "metric": METRIC, "value": ws * mpix / (ms * 1e-3), "unit": "Mpix/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded cluster-mixture scene standing in for Mip-NeRF360-scale captures)",
+        "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W, "height": H, "views": 1,
+                   "tile": "16x16", "sh_degree": 3, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{ws}", "instances_K": K, "fragments_F": frags,
+                   "visible": visible, "mask_on_fraction": mask_on},
+        "stage_ms": stage_ms,
+        "roofline": roof,
+        "e2e": {"value": ws * mpix / (e2e_ms * 1e-3), "unit": "Mpix/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": gpu_launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(steps=1)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _crop_camera(cam, cw, ch):
+    from paper_2412_20522_gb300 import scenes
+    x0 = (cam.width - cw) // 2
+    y0 = (cam.height - ch) // 2
+    return scenes.Camera(cw, ch, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, cam.viewmat,
+                         cam.cam_pos, cam.near)
+
+
+def cpu_baseline_sample(steps=1):
+    """The oracle (FP64, all host cores through OpenMP) on a bounded sample of
+    the same workload: the centre 389x259 crop (1/16 of the pixels) of the
+    1557x1038 view, full masked forward + backward including the preprocess
+    of all 1.2M Gaussians."""
+    from oracle import pipeline
+    from paper_2412_20522_gb300 import scenes
+    g, cams, target = scenes.scene_workload()
+    cw, ch = 389, 259
+    cam = _crop_camera(cams[0], cw, ch)
+    x0, y0 = (cams[0].width - cw) // 2, (cams[0].height - ch) // 2
+    tgt = target[:, y0:y0 + ch, x0:x0 + cw]
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        pipeline.forward_backward_l1(g, [cam], [tgt], pipeline.OracleConfig())
+        times.append(time.perf_counter() - t)
+    t = statistics.median(times)
+    return {"value": cw * ch / 1e6 / t, "unit": "Mpix/s", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds_per_step": t,
+            "sample": f"centre {cw}x{ch} crop of the 1557x1038 view, masked fwd+bwd of the "
+                      "1.2M-Gaussian scene (all Gaussians preprocessed)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass          # the oracle has no warm state; one crop step is the unit of work
+    cb = cpu_baseline_sample(steps=max(args.steps, 1))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "Mpix/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["seconds_per_step"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,280 @@
+/*
+ * maskgs.h -- C ABI of libmaskgs, a GB300 (sm_103a) rasteriser for
+ * MaskGaussian's masked rasterisation (Liu et al., "MaskGaussian: Adaptive 3D
+ * Gaussian Representation from Probabilistic Masks", CVPR 2025,
+ * arXiv 2412.20522).
+ *
+ * One training step of the method, as the paper describes it:
+ *   1. mg_preprocess          sample each Gaussian's mask M_i (Sec. 3.3,
+ *                             Gumbel-softmax over two existence scores) and
+ *                             splat every Gaussian, unmasked, to a 2D
+ *                             Gaussian with a view-dependent colour (Sec. 3.1)
+ *   2. mg_bin                 duplicate each visible splat once per 16x16 tile
+ *                             it intersects (Sec. 3.1), keyed by (tile, depth)
+ *   3. mg_sort                order every tile's splats by depth (Sec. 3.1,
+ *                             "the i-th Gaussian in the depth order") and find
+ *                             each tile's range
+ *   4. mg_render              masked alpha blending, Eq. 3-4
+ *   5. mg_l1_loss_grad        an L1 render loss and dL/dC (Eq. 8's L_render)
+ *   6. mg_render_backward     the mask gradient of Eq. 6 with the background
+ *                             term of Appendix A, and the colour, opacity and
+ *                             2D-geometry gradients of the same blend
+ *   7. mg_preprocess_backward the chain rule back to the Gaussian parameters,
+ *                             and through the straight-through Gumbel-softmax
+ *                             to the existence scores
+ *
+ * Conventions
+ *   - Every array pointer is a caller-owned DEVICE pointer unless the comment
+ *     says "host".  The library allocates nothing.
+ *   - Every call only enqueues work on `stream` (a cudaStream_t); none
+ *     synchronises, so the whole sequence can be captured in a CUDA graph.
+ *   - Every call returns an mg_status.  Argument errors are detected on the
+ *     host before anything is enqueued (MG_ERR_INVALID_ARG); a failed launch
+ *     returns MG_ERR_CUDA.  Errors found on the device (instance capacity
+ *     exceeded, a bounded wait that gave up) are written to the caller's
+ *     device mg_status_word; read it after a synchronisation with
+ *     mg_read_status.  No C++ exception crosses this interface.
+ *   - Gaussians of all views live in one set of arrays.  A view sees the
+ *     Gaussians [gaussian_offset, gaussian_offset + gaussian_count); several
+ *     views of one scene share the range, a batch of scenes uses disjoint
+ *     ranges.  Per-view outputs are concatenated in view order: view v's
+ *     splat records start at record index R_v = sum_{u<v} gaussian_count_u,
+ *     its tiles at T_v = sum_{u<v} tiles_x_u * tiles_y_u, its pixels at
+ *     P_v = sum_{u<v} W_u * H_u.
+ *   - Thread safety: no global state; concurrent calls on distinct buffers
+ *     are independent.
+ */
+#ifndef MASKGS_H
+#define MASKGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mg_stream_t;   /* same type as cudaStream_t */
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,
+    MG_ERR_CUDA = 2,
+    MG_ERR_CAPACITY = 3,     /* more (tile, Gaussian) instances than the buffers hold */
+    MG_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    MG_ERR_UNSUPPORTED = 5
+} mg_status;
+
+enum { MG_MASK_GUMBEL = 0, MG_MASK_ALL_ONES = 1, MG_MASK_GIVEN = 2 };
+enum { MG_DTYPE_F32 = 0 };
+enum { MG_MAX_VIEWS = 64, MG_RECORD_FLOATS = 12, MG_GRAD2D_FLOATS = 12 };
+
+/* Device status word.  Zero it before a step; kernels only ever raise it.
+ * status: an mg_status; detail: which stage raised it (1 bin, 2 sort);
+ * required: for MG_ERR_CAPACITY, the number of instances that was needed. */
+typedef struct {
+    int32_t status;
+    int32_t detail;
+    uint64_t required;
+} mg_status_word;
+
+/* Gaussian parameters (Sec. 3.1: centre p, opacity o, scales s, rotation q,
+ * SH; Sec. 3.3: two mask scores).  Device arrays, FP32:
+ *   means[n][3]; log_scales[n][3] (s = exp(log_scales));
+ *   quats[n][4] as (w, x, y, z), normalised inside;
+ *   opacity_logit[n] (o = sigmoid(opacity_logit));
+ *   sh[n][(sh_degree+1)^2][3], real SH with the Condon-Shortley phase,
+ *     basis order l = 0..D, m = -l..l, colour = sum_k Y_k(dir) sh[k] + 0.5,
+ *     clamped at 0; dir = normalise(p - cam_pos);
+ *   mask_logits[n][2], index 0 = "present". */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;       /* 0..3 */
+    int32_t dtype;           /* MG_DTYPE_F32 */
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logit;
+    const float *sh;
+    const float *mask_logits;
+} mg_gaussians;
+
+/* Pinhole camera with OpenCV axes (x right, y down, z forward).
+ * viewmat: row-major 3x4 world->camera, t = R p + t_cam.  Pixel (u, v) is
+ * evaluated at its centre (u + 0.5, v + 0.5); p_bar = (fx tx/tz + cx,
+ * fy ty/tz + cy).  Gaussians with tz <= near_plane are culled. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[12];
+    float cam_pos[3];
+    float near_plane;
+} mg_camera;
+
+typedef struct {
+    mg_camera cam;
+    int64_t gaussian_offset;
+    int64_t gaussian_count;
+} mg_view;
+
+/* tile_w x tile_h must be 256 pixels with both sides powers of two
+ * (16x16 is the paper's grid, Sec. 3.1; 8x32 and 32x8 are also accepted).
+ * Gumbel noise: u_k from Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (i, iteration_lo, iteration_hi, 0) and key (seed_lo, seed_hi), outputs 0 and
+ * 1 mapped to (2 (x >> 9) + 1) 2^-24.  mask_mode MG_MASK_GIVEN reads
+ * given_mask[n] (device, 0/1 bytes). */
+typedef struct {
+    int32_t tile_w, tile_h;
+    float bg[3];
+    float tau;               /* Gumbel-softmax temperature, > 0 */
+    uint64_t seed;
+    uint64_t iteration;
+    int32_t mask_mode;
+    int32_t reserved;
+    const uint8_t *given_mask;
+} mg_raster_cfg;
+
+/* Per-view preprocess outputs (R = sum_v gaussian_count_v records):
+ *   record[R][12] FP32 render record: mean2d x, y; major axis ux, uy of the
+ *     2D covariance; h1 = -log2(e)/(2 lambda_1), h2 = -log2(e)/(2 lambda_2)
+ *     (so that o exp(-1/2 d^T Sigma^-1 d) = o exp2(h1 (d.u)^2 + h2 (d.u_perp)^2));
+ *     opacity o; mask M as 0.0/1.0; r, g, b; depth tz.
+ *   tiles_touched[R] u32 (0 = culled), radius[R] i32 (pixels, 0 = culled),
+ *   clamp[R] u8 (bit c: colour channel c was clamped at 0).
+ * Per-Gaussian (n):
+ *   mask[n] u8 sampled M_i; mask_soft[n] f32 soft sample y_0 of the
+ *   Gumbel-softmax (1 for all-ones / given masks). */
+typedef struct {
+    float *record;
+    uint32_t *tiles_touched;
+    int32_t *radius;
+    uint8_t *clamp;
+    uint8_t *mask;
+    float *mask_soft;
+} mg_splats;
+
+/* Gradients w.r.t. the per-view splats, grad2d[R][12] FP32:
+ *   dL/dmean2d x, y; dL/dconic a, b, c (conic = Sigma^-1 = [[a, b], [b, c]],
+ *   b the off-diagonal entry); dL/dopacity; dL/dr, g, b; dL/dM; 2 unused. */
+
+/* Gradients w.r.t. the Gaussian parameters, same shapes as mg_gaussians,
+ * FP32, OVERWRITTEN (summed over all views that see the Gaussian). */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logit;
+    float *sh;
+    float *mask_logits;
+} mg_param_grads;
+
+/* ---- 1. preprocess (Sec. 3.1, Sec. 3.3) -------------------------------- */
+/* Samples M_i once per Gaussian and splats every Gaussian of every view.
+ * views: HOST array of n_views (1..MG_MAX_VIEWS) views.  The tile rectangle,
+ * radius and depth key are computed by a fixed sequence of correctly rounded
+ * FP32 operations (reproducible bit for bit).  Errors: MG_ERR_INVALID_ARG for
+ * null pointers, n < 0, bad tile shape, sh_degree outside 0..3, a view range
+ * outside [0, n), non-positive image size, tau <= 0. */
+mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, int32_t n_views,
+                        const mg_raster_cfg *cfg, const mg_splats *out,
+                        mg_status_word *d_status, mg_stream_t stream);
+
+/* ---- 2. bin (Sec. 3.1) ---------------------------------------------------- */
+/* Exclusive scan of tiles_touched over all R records into offsets[R] (u32)
+ * and the total K into *d_num_instances (device u64); then writes, for every
+ * visible record r and every tile of its rectangle (row-major), the key
+ * (global tile id << 32) | float bits of depth and the value r at
+ * offsets[r] + k.  Instances beyond `capacity` are not written and raise
+ * MG_ERR_CAPACITY with `required` = K.  workspace: device scratch of
+ * mg_bin_workspace_bytes(R) bytes, any content. */
+mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
+                 const mg_raster_cfg *cfg, uint32_t *offsets, uint64_t *keys,
+                 uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
+                 void *workspace, size_t workspace_bytes, mg_status_word *d_status,
+                 mg_stream_t stream);
+size_t mg_bin_workspace_bytes(int64_t n_records);
+
+/* ---- 3. sort + tile ranges (Sec. 3.1) -------------------------------------- */
+/* Stable LSD radix sort (8-bit digits, single-pass "onesweep" passes with
+ * decoupled look-back) of the first *d_num_instances (key, value) pairs by
+ * the low key_bits bits of the key, then ranges[t] = [start, end) of the
+ * instances of global tile t (n_tiles_total = sum of all views' tiles).
+ * Because the instances are emitted in record order, ties in depth are
+ * broken by record index.  The sorted pairs end in (keys, vals) when
+ * *result_in_alt (host int) is set to 0, else in (keys_alt, vals_alt); it is
+ * known on the host from key_bits alone.  When *d_num_instances exceeds
+ * capacity (mg_bin raised MG_ERR_CAPACITY) nothing is sorted and every range
+ * is empty.  workspace: mg_sort_workspace_bytes(capacity, key_bits) bytes, any
+ * content.  key_bits: 33..64; capacity < 2^30. */
+mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                  const uint64_t *d_num_instances, uint64_t capacity, int32_t key_bits,
+                  uint32_t *ranges, int64_t n_tiles_total, void *workspace,
+                  size_t workspace_bytes, int32_t *result_in_alt, mg_status_word *d_status,
+                  mg_stream_t stream);
+size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);
+/* Number of key bits for a set of views: ceil(log2(n_tiles_total)) + 32. */
+int32_t mg_key_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
+int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
+
+/* ---- 4. render forward (Eq. 3-4) -------------------------------------------- */
+/* Per pixel, front to back over its tile's range: alpha = min(0.99,
+ * o exp(power)); splats with alpha < 1/255 are skipped (masked or not);
+ * test T' = T (1 - M alpha); if T' < 1e-4 blending stops before this splat;
+ * else C += M alpha T c, T = T'.  Finally C += T bg.
+ * Outputs: image[3][H][W] per view (at 3 P_v), final_T[H][W] and
+ * n_contrib[H][W] per view (at P_v): n_contrib is the index in the tile's
+ * list where blending stopped (the list length if it did not).
+ * frag_count (nullable): device u64 += sum over pixels of n_contrib, the
+ * number of (pixel, splat) pairs both render kernels walk. */
+mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
+                    const uint32_t *ranges, const mg_view *views, int32_t n_views,
+                    const mg_raster_cfg *cfg, float *image, float *final_T,
+                    uint32_t *n_contrib, uint64_t *frag_count, mg_stream_t stream);
+
+/* ---- 5. L1 render loss ------------------------------------------------------ */
+/* For count = sum_v 3 W_v H_v values: dL_dimage[i] = sign(image[i] - target[i])
+ * / (3 W_v H_v) of the view holding i (sign(0) = 0), and *loss (device f32)
+ * += sum_v mean |image_v - target_v|.  The caller zeroes *loss. */
+mg_status mg_l1_loss_grad(const float *image, const float *target, const mg_view *views,
+                          int32_t n_views, float *dL_dimage, float *loss,
+                          mg_stream_t stream);
+
+/* ---- 6. render backward (Eq. 6, Appendix A) --------------------------------- */
+/* Back-to-front replay of each pixel from n_contrib, recovering T_i =
+ * T_{i+1} / (1 - M_i alpha_i) from final_T.  With b_{N+1} = bg and
+ * b_i = M_i alpha_i c_i + (1 - M_i alpha_i) b_{i+1} (the colour behind and at
+ * i, background folded in):
+ *   dL/dM_i     = alpha_i T_i g.(c_i - b_{i+1})   (Eq. 6 + Appendix A)
+ *   dL/dalpha_i = M_i T_i g.(c_i - b_{i+1})       (0 for a masked splat)
+ *   dL/dc_i     = M_i alpha_i T_i g,   g = dL/dC,
+ * then through the 0.99 clamp to opacity, conic and 2D mean.
+ * grad2d[R][12] is ZEROED by this call and then accumulated. */
+mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
+                             const uint32_t *ranges, const mg_view *views,
+                             int32_t n_views, const mg_raster_cfg *cfg,
+                             const float *final_T, const uint32_t *n_contrib,
+                             const float *dL_dimage, float *grad2d, mg_stream_t stream);
+
+/* ---- 7. preprocess backward ------------------------------------------------- */
+/* Chain rule from grad2d through the 2D covariance (P = J W R S), the
+ * quaternion normalisation, the scale exponential, the projection and the
+ * SH colour (zero for clamped channels) to every parameter, summed over
+ * views; mask_logits receive dL/dM y_0 (1 - y_0) / tau and its negative
+ * (straight-through Gumbel-softmax, Sec. 3.3) for MG_MASK_GUMBEL, zero
+ * otherwise.  Outputs are overwritten. */
+mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view *views,
+                                 int32_t n_views, const mg_raster_cfg *cfg,
+                                 const mg_splats *splats, const float *grad2d,
+                                 const mg_param_grads *out, mg_stream_t stream);
+
+/* ---- helpers ------------------------------------------------------------------ */
+/* Synchronises `stream` and copies the device status word to *h_out (host). */
+mg_status mg_read_status(const mg_status_word *d_status, mg_status_word *h_out,
+                         mg_stream_t stream);
+const char *mg_status_string(int32_t status);
+const char *mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MASKGS_H */

@@ -254,7 +254,8 @@ def project32(means, log_scales, quats, cam, tile_w=16, tile_h=16):
     lam = mid + np.sqrt(np.maximum(f32(0.1), disc))
     rf = np.ceil(f32(3.0) * np.sqrt(lam))
     ok = in_front & qvalid & (det > f32(0.0)) & np.isfinite(px) & np.isfinite(py) & np.isfinite(rf)
-    rf = np.where(ok, rf, f32(0.0)).astype(np.float32)
+    # radius capped at 1e9 px (exact in float32 and in int32)
+    rf = np.where(ok, np.minimum(rf, f32(1e9)), f32(0.0)).astype(np.float32)
 
     gx = (W + tile_w - 1) // tile_w
     gy = (H + tile_h - 1) // tile_h
@@ -269,7 +270,7 @@ def project32(means, log_scales, quats, cam, tile_w=16, tile_h=16):
     y0i = np.where(nonempty, y0, 0).astype(np.int64)
     y1i = np.where(nonempty, y1, -1).astype(np.int64)
     tiles = ((x1i - x0i + 1) * (y1i - y0i + 1)).astype(np.uint32)
-    radius = np.where(nonempty, np.minimum(rf, f32(1e9)), f32(0.0)).astype(np.int32)
+    radius = np.where(nonempty, rf, f32(0.0)).astype(np.int32)
     return dict(tz=tz, px=px, py=py, a=a, b=b, c=c, det=det, disc=disc, radius=radius,
                 x0=x0i, x1=x1i, y0=y0i, y1=y1i, tiles=tiles,
                 depth_bits=tz.view(np.uint32).copy(), visible=nonempty,

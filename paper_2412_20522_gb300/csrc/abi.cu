@@ -1,0 +1,87 @@
+// Host-side helpers of the C ABI: argument checks, the view table, status.
+#include <math.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace mg_host {
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+mg_status build_view_table(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                           mg::ViewTable *vt) {
+    if (views == nullptr || cfg == nullptr || vt == nullptr) return MG_ERR_INVALID_ARG;
+    if (n_views < 1 || n_views > MG_MAX_VIEWS) return MG_ERR_INVALID_ARG;
+    if (!pow2(cfg->tile_w) || !pow2(cfg->tile_h) || cfg->tile_w * cfg->tile_h != mg::kTilePixels)
+        return MG_ERR_INVALID_ARG;
+    memset(vt, 0, sizeof(*vt));
+    vt->n_views = n_views;
+    vt->tile_w = cfg->tile_w;
+    vt->tile_h = cfg->tile_h;
+    int l = 0;
+    while ((1 << l) < cfg->tile_w) ++l;
+    vt->log2_tw = l;
+    for (int v = 0; v < n_views; ++v) {
+        const mg_view &w = views[v];
+        if (w.cam.width <= 0 || w.cam.height <= 0 || w.gaussian_offset < 0 ||
+            w.gaussian_count < 0 || !(w.cam.fx > 0.0f) || !(w.cam.fy > 0.0f))
+            return MG_ERR_INVALID_ARG;
+        vt->cam[v] = w.cam;
+        vt->g_off[v] = w.gaussian_offset;
+        vt->g_cnt[v] = w.gaussian_count;
+        vt->gx[v] = (w.cam.width + cfg->tile_w - 1) / cfg->tile_w;
+        vt->gy[v] = (w.cam.height + cfg->tile_h - 1) / cfg->tile_h;
+        vt->rec_off[v + 1] = vt->rec_off[v] + w.gaussian_count;
+        vt->tile_off[v + 1] = vt->tile_off[v] + (int64_t)vt->gx[v] * vt->gy[v];
+        vt->pix_off[v + 1] = vt->pix_off[v] + (int64_t)w.cam.width * w.cam.height;
+    }
+    return MG_OK;
+}
+
+mg_status launch_status(void) {
+    return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+}  // namespace mg_host
+
+extern "C" {
+
+int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg) {
+    mg::ViewTable vt;
+    if (mg_host::build_view_table(views, n_views, cfg, &vt) != MG_OK) return -1;
+    return vt.tile_off[n_views];
+}
+
+int32_t mg_key_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg) {
+    const int64_t t = mg_total_tiles(views, n_views, cfg);
+    if (t <= 0) return -1;
+    int b = 0;
+    while ((int64_t(1) << b) < t) ++b;
+    return 32 + (b > 0 ? b : 1);
+}
+
+mg_status mg_read_status(const mg_status_word *d_status, mg_status_word *h_out,
+                         mg_stream_t stream) {
+    if (d_status == nullptr || h_out == nullptr) return MG_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(h_out, d_status, sizeof(mg_status_word), cudaMemcpyDeviceToHost,
+                        (cudaStream_t)stream) != cudaSuccess)
+        return MG_ERR_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return MG_ERR_CUDA;
+    return MG_OK;
+}
+
+const char *mg_status_string(int32_t status) {
+    switch (status) {
+        case MG_OK: return "ok";
+        case MG_ERR_INVALID_ARG: return "invalid argument";
+        case MG_ERR_CUDA: return "CUDA error";
+        case MG_ERR_CAPACITY: return "instance capacity exceeded";
+        case MG_ERR_TIMEOUT: return "device-side wait timed out";
+        case MG_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char *mg_version(void) { return "maskgs 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,455 @@
+// Tile binning (Sec. 3.1: a Gaussian takes part in a tile's pixels only if it
+// intersects the tile) and depth ordering (Sec. 3.1: Gaussians blended "in
+// the depth order").
+//
+//   scan      single-pass exclusive scan of tiles_touched (decoupled look-back)
+//   duplicate one (tile | depth) key per intersected tile, row-major per splat
+//   sort      stable LSD radix sort, 8-bit digits, one "onesweep" kernel per
+//             digit (Adinets & Merrill, "Onesweep: a faster least significant
+//             digit radix sort for GPUs", 2022): local ranking by warp
+//             match-any multi-split, global offsets by decoupled look-back
+//   ranges    [start, end) of every tile in the sorted list
+//
+// Every cross-block wait is bounded: after kMaxTimeoutSpins polls the kernel
+// records MG_ERR_TIMEOUT in the status word and carries on (results are then
+// invalid, but the GPU never hangs).  Partition ids come from an atomic
+// counter, so a block only ever waits on partitions held by running blocks.
+#include "internal.cuh"
+
+namespace mg {
+
+constexpr int kScanThreads = 256, kScanItems = 8, kScanPart = kScanThreads * kScanItems;
+constexpr int kSortThreads = 256, kSortItems = 12, kSortPart = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValMask = (1u << 30) - 1u;
+constexpr uint64_t kFlagAgg64 = 1ull << 62, kFlagPrefix64 = 2ull << 62,
+                   kValMask64 = (1ull << 62) - 1ull;
+constexpr int kMaxPasses = 8;
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
+    return *reinterpret_cast<const volatile uint64_t *>(p);
+}
+
+// --------------------------------------------------------------------------
+// scan of tiles_touched
+// --------------------------------------------------------------------------
+struct ScanWS {
+    uint32_t counter;
+    uint32_t pad;
+    uint64_t status[1];   // [n_parts]
+};
+
+__device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t *sm_warp,
+                                                             uint64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sm_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < (int)(blockDim.x >> 5) ? sm_warp[lane] : 0;
+        uint64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < (int)(blockDim.x >> 5)) sm_warp[lane] = wi - w;
+        if (lane == 31) sm_warp[32] = wi;
+    }
+    __syncthreads();
+    total = sm_warp[32];
+    return sm_warp[warp] + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_kernel(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ out,
+            uint64_t *d_total, uint64_t capacity, ScanWS *ws, int64_t n_parts,
+            mg_status_word *st) {
+    __shared__ uint64_t sm_warp[33];
+    __shared__ uint64_t sm_prefix;
+    __shared__ int64_t sm_part;
+    if (threadIdx.x == 0) sm_part = atomicAdd(&ws->counter, 1u);
+    __syncthreads();
+    const int64_t part = sm_part;
+    if (part >= n_parts) return;
+    const int64_t base = part * kScanPart + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint64_t sum = 0;
+    if (base + kScanItems <= n) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(in + base);
+        const uint4 b = *reinterpret_cast<const uint4 *>(in + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
+    uint64_t agg;
+    const uint64_t excl = block_exclusive_scan_u64(sum, sm_warp, agg);
+    if (threadIdx.x == 0) {
+        uint64_t prefix = 0;
+        if (part == 0) {
+            atomicExch((unsigned long long *)&ws->status[0], (unsigned long long)(kFlagPrefix64 | agg));
+        } else {
+            atomicExch((unsigned long long *)&ws->status[part], (unsigned long long)(kFlagAgg64 | agg));
+            for (int64_t q = part - 1; q >= 0; --q) {
+                uint64_t s = ld_volatile(&ws->status[q]);
+                int spins = 0;
+                while ((s >> 62) == 0 && spins < kMaxTimeoutSpins) {
+                    __nanosleep(20);
+                    s = ld_volatile(&ws->status[q]);
+                    ++spins;
+                }
+                if ((s >> 62) == 0) {
+                    raise_status(st, MG_ERR_TIMEOUT, 1, 0);
+                    break;
+                }
+                prefix += s & kValMask64;
+                if ((s >> 62) == 2) break;
+            }
+            atomicExch((unsigned long long *)&ws->status[part],
+                       (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
+        }
+        sm_prefix = prefix;
+        if (part == n_parts - 1) {
+            *d_total = prefix + agg;
+            if (prefix + agg > capacity) raise_status(st, MG_ERR_CAPACITY, 1, prefix + agg);
+        }
+    }
+    __syncthreads();
+    uint64_t run = sm_prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)run;
+        run += v[k];
+    }
+}
+
+// --------------------------------------------------------------------------
+// key duplication
+// --------------------------------------------------------------------------
+__global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
+                                 const int32_t *__restrict__ radius,
+                                 const uint32_t *__restrict__ tiles,
+                                 const uint32_t *__restrict__ offsets, int64_t n_records,
+                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                 uint64_t capacity) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_records) return;
+    const uint32_t nt = tiles[r];
+    if (nt == 0) return;
+    const uint64_t off = offsets[r];
+    if (off + nt > capacity) return;
+    int v = 0;
+    while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= r) ++v;
+    const float4 a = *reinterpret_cast<const float4 *>(record + 12 * r);
+    const float depth = record[12 * r + 11];
+    int x0, x1, y0, y1;
+    if (!tile_rect(a.x, a.y, (float)radius[r], vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x0, x1,
+                   y0, y1))
+        return;
+    const uint64_t dbits = __float_as_uint(depth);
+    const uint64_t t0 = (uint64_t)vt.tile_off[v];
+    uint64_t k = off;
+    const uint64_t k_end = off + nt;
+    for (int ty = y0; ty <= y1; ++ty)
+        for (int tx = x0; tx <= x1 && k < k_end; ++tx, ++k) {
+            keys[k] = ((t0 + (uint64_t)ty * vt.gx[v] + tx) << 32) | dbits;
+            vals[k] = (uint32_t)r;
+        }
+}
+
+// --------------------------------------------------------------------------
+// radix sort
+// --------------------------------------------------------------------------
+// Instances to sort: all of them, or none when they overflowed the capacity
+// (the buffers then hold an incomplete list; the status word says so).
+__device__ __forceinline__ int64_t sort_count(const uint64_t *d_n, uint64_t capacity) {
+    const uint64_t n = *d_n;
+    return n <= capacity ? (int64_t)n : 0;
+}
+
+struct SortWS {
+    uint32_t hist[kMaxPasses][256];    // digit counts, then exclusive offsets
+    uint32_t counter[kMaxPasses];
+    uint32_t pad[8];
+    uint32_t status[1];                // [2][max_parts][256]
+};
+
+__global__ void sort_histogram_kernel(const uint64_t *__restrict__ keys, const uint64_t *d_n,
+                                      uint64_t capacity, int passes, SortWS *ws,
+                                      int64_t max_parts) {
+    __shared__ uint32_t h[kMaxPasses][256];
+    for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t n = sort_count(d_n, capacity);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+    }
+    // clear the look-back status of the first pass for the partitions in use
+    const int64_t parts = (n + kSortPart - 1) / kSortPart;
+    const int64_t lim = min(parts, max_parts) * 256;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += stride)
+        ws->status[i] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&(&ws->hist[0][0])[i], c);
+    }
+}
+
+__global__ void sort_offsets_kernel(SortWS *ws) {
+    // one block per pass, 256 threads: exclusive scan of the digit counts
+    __shared__ uint64_t sm_warp[33];
+    const int p = blockIdx.x;
+    const uint32_t c = ws->hist[p][threadIdx.x];
+    uint64_t tot;
+    const uint64_t e = block_exclusive_scan_u64(c, sm_warp, tot);
+    ws->hist[p][threadIdx.x] = (uint32_t)e;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                const uint64_t *d_n, uint64_t capacity, int pass, int shift, SortWS *ws,
+                int64_t max_parts, mg_status_word *st) {
+    __shared__ uint64_t sk[kSortPart];
+    __shared__ uint32_t sv[kSortPart];
+    __shared__ uint32_t whist[kSortWarps][256];
+    __shared__ uint32_t dstart[256];
+    __shared__ int64_t gbase[256];
+    __shared__ uint64_t sm_warp[33];
+    __shared__ int64_t sm_part;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = sort_count(d_n, capacity);
+    const int64_t parts = min((n + kSortPart - 1) / kSortPart, max_parts);
+    uint32_t *status = ws->status + (int64_t)(pass & 1) * max_parts * 256;
+    uint32_t *status_next = ws->status + (int64_t)((pass + 1) & 1) * max_parts * 256;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sm_part = atomicAdd(&ws->counter[pass], 1u);
+        for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&whist[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t part = sm_part;
+        if (part >= parts) break;
+        status_next[part * 256 + threadIdx.x] = 0u;   // ready for the next pass
+
+        // ---- load and rank within the warp (stable: slot-major, lane-minor)
+        const int64_t wbase = part * kSortPart + (int64_t)warp * (32 * kSortItems);
+        uint64_t k[kSortItems];
+        uint32_t val[kSortItems], rank[kSortItems];
+        int dig[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const int64_t idx = wbase + i * 32 + lane;
+            const bool valid = idx < n;
+            k[i] = valid ? keys_in[idx] : 0ull;
+            val[i] = valid ? vals_in[idx] : 0u;
+            dig[i] = valid ? (int)((k[i] >> shift) & 0xFF) : 256;
+        }
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader && dig[i] < 256) {
+                old = whist[warp][dig[i]];
+                whist[warp][dig[i]] = old + __popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[i] = old + __popc(peers & lanemask_lt);
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // ---- block digit counts, per-warp offsets, local digit starts
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = whist[w][d];
+            whist[w][d] = tot;
+            tot += c;
+        }
+        if (part == 0)
+            atomicExch(&status[d], kFlagPrefix | tot);
+        else
+            atomicExch(&status[part * 256 + d], kFlagAgg | tot);
+        uint64_t dummy;
+        const uint64_t ds = block_exclusive_scan_u64(tot, sm_warp, dummy);
+        dstart[d] = (uint32_t)ds;
+
+        // ---- decoupled look-back per digit
+        uint32_t excl = 0;
+        if (part > 0) {
+            for (int64_t q = part - 1; q >= 0; --q) {
+                uint32_t s = ld_volatile(&status[q * 256 + d]);
+                int spins = 0;
+                while ((s >> 30) == 0 && spins < kMaxTimeoutSpins) {
+                    __nanosleep(20);
+                    s = ld_volatile(&status[q * 256 + d]);
+                    ++spins;
+                }
+                if ((s >> 30) == 0) {
+                    raise_status(st, MG_ERR_TIMEOUT, 2, 0);
+                    break;
+                }
+                excl += s & kValMask;
+                if ((s >> 30) == 2) break;
+            }
+            atomicExch(&status[part * 256 + d], kFlagPrefix | ((excl + tot) & kValMask));
+        }
+        gbase[d] = (int64_t)ws->hist[pass][d] + excl - (int64_t)ds;
+        __syncthreads();
+
+        // ---- scatter into shared memory in block order, then out
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            if (dig[i] < 256) {
+                const uint32_t pos = dstart[dig[i]] + whist[warp][dig[i]] + rank[i];
+                sk[pos] = k[i];
+                sv[pos] = val[i];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)(n - part * kSortPart < kSortPart ? n - part * kSortPart : kSortPart);
+        for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+            const uint64_t kk = sk[j];
+            const int64_t dst = gbase[(kk >> shift) & 0xFF] + j;
+            keys_out[dst] = kk;
+            vals_out[dst] = sv[j];
+        }
+    }
+}
+
+__global__ void ranges_kernel(const uint64_t *__restrict__ keys, const uint64_t *d_n,
+                              uint64_t capacity, uint32_t *__restrict__ ranges, int64_t n_tiles) {
+    const int64_t n = sort_count(d_n, capacity);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t t = (int64_t)(keys[i] >> 32);
+        if (t >= n_tiles) continue;
+        if (i == 0 || (int64_t)(keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
+        if (i == n - 1 || (int64_t)(keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+    }
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+static int64_t sort_max_parts(uint64_t capacity) {
+    return (int64_t)((capacity + kSortPart - 1) / kSortPart) + 1;
+}
+
+extern "C" size_t mg_bin_workspace_bytes(int64_t n_records) {
+    const int64_t parts = (n_records + kScanPart - 1) / kScanPart + 1;
+    return sizeof(ScanWS) + sizeof(uint64_t) * (size_t)parts + 256;
+}
+
+extern "C" size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits) {
+    (void)key_bits;
+    return sizeof(SortWS) + sizeof(uint32_t) * 2 * 256 * (size_t)sort_max_parts(capacity) + 256;
+}
+
+extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
+                            const mg_raster_cfg *cfg, uint32_t *offsets, uint64_t *keys,
+                            uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
+                            void *workspace, size_t workspace_bytes, mg_status_word *d_status,
+                            mg_stream_t stream) {
+    if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
+        !offsets || !d_num_instances || !workspace)
+        return MG_ERR_INVALID_ARG;
+    if (capacity > 0 && (!keys || !vals)) return MG_ERR_INVALID_ARG;
+    if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    const int64_t R = vt.rec_off[n_views];
+    if (workspace_bytes < mg_bin_workspace_bytes(R)) return MG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats->tiles_touched) & 15u) != 0) return MG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t parts = (R + kScanPart - 1) / kScanPart;
+    ScanWS *ws = reinterpret_cast<ScanWS *>(workspace);
+    if (cudaMemsetAsync(ws, 0, sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(parts + 1), s) !=
+        cudaSuccess)
+        return MG_ERR_CUDA;
+    if (R == 0) {
+        if (cudaMemsetAsync(d_num_instances, 0, sizeof(uint64_t), s) != cudaSuccess)
+            return MG_ERR_CUDA;
+        return MG_OK;
+    }
+    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, R, offsets,
+                                                         d_num_instances, capacity, ws, parts,
+                                                         d_status);
+    if (capacity > 0)
+        duplicate_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(
+            vt, splats->record, splats->radius, splats->tiles_touched, offsets, R, keys, vals,
+            capacity);
+    return mg_host::launch_status();
+}
+
+extern "C" mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                             uint32_t *vals_alt, const uint64_t *d_num_instances,
+                             uint64_t capacity, int32_t key_bits, uint32_t *ranges,
+                             int64_t n_tiles_total, void *workspace, size_t workspace_bytes,
+                             int32_t *result_in_alt, mg_status_word *d_status,
+                             mg_stream_t stream) {
+    if (!keys || !vals || !keys_alt || !vals_alt || !d_num_instances || !ranges || !workspace ||
+        !result_in_alt || key_bits < 33 || key_bits > 64 || n_tiles_total <= 0)
+        return MG_ERR_INVALID_ARG;
+    if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
+    if (workspace_bytes < mg_sort_workspace_bytes(capacity, key_bits)) return MG_ERR_INVALID_ARG;
+    if ((n_tiles_total >> 32) != 0) return MG_ERR_INVALID_ARG;
+    const int passes = (key_bits + 7) / 8;
+    *result_in_alt = passes & 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    SortWS *ws = reinterpret_cast<SortWS *>(workspace);
+    const int64_t max_parts = sort_max_parts(capacity);
+    if (cudaMemsetAsync(ws, 0, offsetof(SortWS, status), s) != cudaSuccess) return MG_ERR_CUDA;
+    if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) !=
+        cudaSuccess)
+        return MG_ERR_CUDA;
+    if (capacity == 0) return MG_OK;
+    const int sms = sm_count();
+    sort_histogram_kernel<<<sms * 4, 256, 0, s>>>(keys, d_num_instances, capacity, passes, ws,
+                                                  max_parts);
+    sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kSortThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = (int64_t)sms * per_sm < max_parts ? (int64_t)sms * per_sm : max_parts;
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        onesweep_kernel<<<(unsigned)grid, kSortThreads, 0, s>>>(kin, vin, kout, vout,
+                                                                d_num_instances, capacity, p,
+                                                                8 * p, ws, max_parts, d_status);
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+    }
+    ranges_kernel<<<sms * 4, 256, 0, s>>>(kin, d_num_instances, capacity, ranges, n_tiles_total);
+    return mg_host::launch_status();
+}

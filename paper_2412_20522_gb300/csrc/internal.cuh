@@ -1,0 +1,200 @@
+// Internal device helpers of libmaskgs (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/maskgs.h"
+
+namespace mg {
+
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLowpass = 0.3f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kTilePixels = 256;
+constexpr int kMaxTimeoutSpins = 1 << 22;   // bounded waits: ~4M polls, then give up
+
+// Views in kernel parameter space (captured by value in CUDA graphs).
+struct ViewTable {
+    int32_t n_views;
+    int32_t tile_w, tile_h, log2_tw;
+    mg_camera cam[MG_MAX_VIEWS];
+    int64_t g_off[MG_MAX_VIEWS];     // first Gaussian of the view
+    int64_t g_cnt[MG_MAX_VIEWS];     // Gaussians seen by the view
+    int64_t rec_off[MG_MAX_VIEWS + 1];   // first record of the view
+    int64_t tile_off[MG_MAX_VIEWS + 1];  // first global tile of the view
+    int64_t pix_off[MG_MAX_VIEWS + 1];   // first pixel of the view
+    int32_t gx[MG_MAX_VIEWS], gy[MG_MAX_VIEWS];
+};
+
+// device status word helpers -------------------------------------------------
+__device__ __forceinline__ void raise_status(mg_status_word *w, int32_t st, int32_t detail,
+                                             uint64_t required) {
+    if (w == nullptr) return;
+    atomicCAS(&w->status, 0, st);
+    atomicMax((unsigned long long *)&w->required, (unsigned long long)required);
+    atomicCAS(&w->detail, 0, detail);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
+// (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float uniform24(uint32_t x) {
+    return __fmul_rn((float)(((x >> 9) << 1) | 1u), 0x1p-24f);
+}
+
+// ---------------------------------------------------------------------------
+// Own FP32 log / exp for decisions, each step one correctly rounded op.
+// log: x = m 2^e, m in [1/sqrt2, sqrt2), log m = 2 atanh((m-1)/(m+1)) by its
+// series to s^11/11, Cody-Waite split of ln 2.
+// exp: x = k ln2 + r, Taylor series of exp(r) to r^7/7!, times 2^k.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float log32(float x) {
+    const uint32_t bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+    if (m >= 0x1.6a09e6p+0f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float s = __fdiv_rn(__fadd_rn(m, -1.0f), __fadd_rn(m, 1.0f));
+    const float z = __fmul_rn(s, s);
+    float p = 0x1.745d18p-4f;
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.c71c72p-4f);
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.24924ap-3f);
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.99999ap-3f);
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.555556p-2f);
+    p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+    const float lm = __fmul_rn(__fmul_rn(s, 2.0f), p);
+    const float ef = (float)e;
+    return __fadd_rn(__fmul_rn(ef, 0x1.62e4p-1f), __fadd_rn(__fmul_rn(ef, 0x1.7f7d1cp-20f), lm));
+}
+
+__device__ __forceinline__ float exp32(float x) {
+    x = fminf(fmaxf(x, -80.0f), 80.0f);
+    const float k = rintf(__fmul_rn(x, 0x1.715476p+0f));
+    const float r = __fadd_rn(__fadd_rn(x, -__fmul_rn(k, 0x1.62e4p-1f)), -__fmul_rn(k, 0x1.7f7d1cp-20f));
+    float p = 0x1.a01a02p-13f;
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.6c16c2p-10f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.111112p-7f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-5f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-3f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    const float two_k = __uint_as_float((uint32_t)((int)k + 127) << 23);
+    return __fmul_rn(p, two_k);
+}
+
+// exact-rounding shorthands for the decision path
+__device__ __forceinline__ float ad(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ml(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float dv(float a, float b) { return __fdiv_rn(a, b); }
+// (a*b + c*d) + e*f with every product and sum rounded
+__device__ __forceinline__ float dot3(float a, float b, float c, float d, float e, float f) {
+    return ad(ad(ml(a, b), ml(c, d)), ml(e, f));
+}
+
+// Rectangle of tiles overlapped by the square [p - r, p + r] (inclusive),
+// clamped to the grid; false when empty.  Same operations in preprocess and
+// in key duplication, so both see the same rectangle.
+__device__ __forceinline__ bool tile_rect(float px, float py, float rf, int tw, int th, int gx,
+                                          int gy, int &x0, int &x1, int &y0, int &y1) {
+    const float fx0 = fmaxf(floorf(dv(sb(px, rf), (float)tw)), 0.0f);
+    const float fx1 = fminf(floorf(dv(ad(px, rf), (float)tw)), (float)(gx - 1));
+    const float fy0 = fmaxf(floorf(dv(sb(py, rf), (float)th)), 0.0f);
+    const float fy1 = fminf(floorf(dv(ad(py, rf), (float)th)), (float)(gy - 1));
+    if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
+    x0 = (int)fx0; x1 = (int)fx1; y0 = (int)fy0; y1 = (int)fy1;
+    return true;
+}
+
+// Real SH basis with the Condon-Shortley phase, m = -l..l, degree <= 3.
+constexpr float kSH0 = 0.28209479177387814f;
+constexpr float kSH1 = 0.4886025119029199f;
+constexpr float kSH2a = 1.0925484305920792f, kSH2b = 0.31539156525252005f,
+                kSH2c = 0.5462742152960396f;
+constexpr float kSH3a = 0.5900435899266435f, kSH3b = 2.890611442640554f,
+                kSH3c = 0.4570457994644658f, kSH3d = 0.3731763325901154f,
+                kSH3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y) {
+    Y[0] = kSH0;
+    if (deg < 1) return;
+    Y[1] = -kSH1 * y;
+    Y[2] = kSH1 * z;
+    Y[3] = -kSH1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, yz = y * z, xz = x * z;
+    Y[4] = kSH2a * xy;
+    Y[5] = -kSH2a * yz;
+    Y[6] = kSH2b * (3.0f * zz - 1.0f);
+    Y[7] = -kSH2a * xz;
+    Y[8] = kSH2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -kSH3a * y * (3.0f * xx - yy);
+    Y[10] = kSH3b * xy * z;
+    Y[11] = -kSH3c * y * (5.0f * zz - 1.0f);
+    Y[12] = kSH3d * z * (5.0f * zz - 3.0f);
+    Y[13] = -kSH3c * x * (5.0f * zz - 1.0f);
+    Y[14] = kSH3e * z * (xx - yy);
+    Y[15] = -kSH3a * x * (xx - 3.0f * yy);
+}
+
+// d Y_k / d(x, y, z) for the same basis (direction not yet normalised out).
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float *dx,
+                                              float *dy, float *dz) {
+    dx[0] = dy[0] = dz[0] = 0.0f;
+    if (deg < 1) return;
+    dx[1] = 0.0f;  dy[1] = -kSH1;  dz[1] = 0.0f;
+    dx[2] = 0.0f;  dy[2] = 0.0f;   dz[2] = kSH1;
+    dx[3] = -kSH1; dy[3] = 0.0f;   dz[3] = 0.0f;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    dx[4] = kSH2a * y;          dy[4] = kSH2a * x;           dz[4] = 0.0f;
+    dx[5] = 0.0f;               dy[5] = -kSH2a * z;          dz[5] = -kSH2a * y;
+    dx[6] = 0.0f;               dy[6] = 0.0f;                dz[6] = 6.0f * kSH2b * z;
+    dx[7] = -kSH2a * z;         dy[7] = 0.0f;                dz[7] = -kSH2a * x;
+    dx[8] = 2.0f * kSH2c * x;   dy[8] = -2.0f * kSH2c * y;   dz[8] = 0.0f;
+    if (deg < 3) return;
+    dx[9] = -kSH3a * 6.0f * x * y;            dy[9] = -kSH3a * 3.0f * (xx - yy);       dz[9] = 0.0f;
+    dx[10] = kSH3b * y * z;                   dy[10] = kSH3b * x * z;                  dz[10] = kSH3b * x * y;
+    dx[11] = 0.0f;                            dy[11] = -kSH3c * (5.0f * zz - 1.0f);    dz[11] = -kSH3c * 10.0f * y * z;
+    dx[12] = 0.0f;                            dy[12] = 0.0f;                           dz[12] = kSH3d * (15.0f * zz - 3.0f);
+    dx[13] = -kSH3c * (5.0f * zz - 1.0f);     dy[13] = 0.0f;                           dz[13] = -kSH3c * 10.0f * x * z;
+    dx[14] = kSH3e * 2.0f * x * z;            dy[14] = -kSH3e * 2.0f * y * z;          dz[14] = kSH3e * (xx - yy);
+    dx[15] = -kSH3a * 3.0f * (xx - yy);       dy[15] = kSH3a * 6.0f * x * y;           dz[15] = 0.0f;
+}
+
+__host__ __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int64_t t) {
+    int v = 0;
+    while (v + 1 < vt.n_views && vt.tile_off[v + 1] <= t) ++v;
+    return v;
+}
+
+}  // namespace mg
+
+// host-side helpers shared by the entry points
+namespace mg_host {
+mg_status build_view_table(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                           mg::ViewTable *vt);
+mg_status launch_status(void);
+}

@@ -1,0 +1,527 @@
+// Preprocess (forward and backward): mask sampling (Sec. 3.3) fused with the
+// splat of every Gaussian (Sec. 3.1) for every view.
+//
+// One thread per Gaussian; the attributes are read once and reused for all
+// views that see the Gaussian.  The SH block of a warp's 32 Gaussians is
+// staged through shared memory with 128-bit coalesced loads.
+//
+// Decisions (cull, radius, tile rectangle, depth key, mask) use a fixed
+// sequence of correctly rounded FP32 operations (__fadd_rn, __fmul_rn, ...),
+// never a contracted FMA, so that they reproduce bit for bit.  The 2D
+// covariance is formed from its factor P = J W R S: Sigma_bar = P P^T + 0.3 I,
+// det by Cauchy-Binet, eigenvalue gap as a sum of squares.  The splat is
+// stored in eigen form (major axis u, h_k = -log2(e) / (2 lambda_k)), which
+// stays accurate in FP32 for needle-shaped splats whose conic entries cancel.
+#include "internal.cuh"
+
+namespace mg {
+
+constexpr int kPreThreads = 128;
+
+template <int ROW>
+struct StageStride { static constexpr int value = (ROW % 2 == 0) ? ROW + 1 : ROW; };
+
+// Copy rows [row0, row0 + nrows) of a row-major [*, ROW] array to shared
+// memory with an odd row stride (conflict-free per-lane reads).
+template <int ROW>
+__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int64_t row0, int nrows,
+                                           float *sm, int lane) {
+    constexpr int S = StageStride<ROW>::value;
+    const float *base = src + row0 * ROW;
+    const int total = nrows * ROW;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(base);
+        const int n4 = total >> 2;
+        for (int q = lane; q < n4; q += 32) {
+            const float4 v = __ldg(b4 + q);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int f = 4 * q + k;
+                sm[(f / ROW) * S + (f % ROW)] = e[k];
+            }
+        }
+        done = n4 << 2;
+    }
+    for (int f = done + lane; f < total; f += 32) sm[(f / ROW) * S + (f % ROW)] = __ldg(base + f);
+    __syncwarp();
+}
+
+struct Splat32 {
+    // decision-path quantities
+    float tz, px, py, a, b, c, det, mid, disc, rf;
+    int x0, x1, y0, y1;
+    bool visible;
+    // factor and pieces reused by the backward
+    float P[2][3], M[3][3], R[3][3], T[2][3], s[3], qn[4], nrm, tzs, txc, tyc, ux, uy;
+    bool clampx, clampy;
+};
+
+// The FP32 decision path for one Gaussian and one camera (every op rounded).
+__device__ __forceinline__ void splat_fp32(const mg_camera &C, int tw, int th, int gx, int gy,
+                                           float x, float y, float z, const float ls[3],
+                                           const float q[4], Splat32 &S) {
+    const float *V = C.viewmat;
+    const float tx = ad(dot3(V[0], x, V[1], y, V[2], z), V[3]);
+    const float ty = ad(dot3(V[4], x, V[5], y, V[6], z), V[7]);
+    S.tz = ad(dot3(V[8], x, V[9], y, V[10], z), V[11]);
+    const bool in_front = S.tz > C.near_plane;
+    S.tzs = in_front ? S.tz : 1.0f;
+    S.ux = dv(tx, S.tzs);
+    S.uy = dv(ty, S.tzs);
+    S.px = ad(ml(C.fx, S.ux), C.cx);
+    S.py = ad(ml(C.fy, S.uy), C.cy);
+
+    S.s[0] = exp32(ls[0]);
+    S.s[1] = exp32(ls[1]);
+    S.s[2] = exp32(ls[2]);
+    float w = q[0], qx = q[1], qy = q[2], qz = q[3];
+    const float n2 = ad(ad(ad(ml(w, w), ml(qx, qx)), ml(qy, qy)), ml(qz, qz));
+    const bool qvalid = n2 > 0.0f;
+    S.nrm = __fsqrt_rn(qvalid ? n2 : 1.0f);
+    w = dv(w, S.nrm); qx = dv(qx, S.nrm); qy = dv(qy, S.nrm); qz = dv(qz, S.nrm);
+    S.qn[0] = w; S.qn[1] = qx; S.qn[2] = qy; S.qn[3] = qz;
+    S.R[0][0] = sb(1.0f, ml(2.0f, ad(ml(qy, qy), ml(qz, qz))));
+    S.R[0][1] = ml(2.0f, sb(ml(qx, qy), ml(w, qz)));
+    S.R[0][2] = ml(2.0f, ad(ml(qx, qz), ml(w, qy)));
+    S.R[1][0] = ml(2.0f, ad(ml(qx, qy), ml(w, qz)));
+    S.R[1][1] = sb(1.0f, ml(2.0f, ad(ml(qx, qx), ml(qz, qz))));
+    S.R[1][2] = ml(2.0f, sb(ml(qy, qz), ml(w, qx)));
+    S.R[2][0] = ml(2.0f, sb(ml(qx, qz), ml(w, qy)));
+    S.R[2][1] = ml(2.0f, ad(ml(qy, qz), ml(w, qx)));
+    S.R[2][2] = sb(1.0f, ml(2.0f, ad(ml(qx, qx), ml(qy, qy))));
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) S.M[j][k] = ml(S.R[j][k], S.s[k]);
+
+    const float tanx = dv(ml((float)C.width, 0.5f), C.fx);
+    const float tany = dv(ml((float)C.height, 0.5f), C.fy);
+    const float limx = ml(1.3f, tanx), limy = ml(1.3f, tany);
+    const float cux = fminf(limx, fmaxf(-limx, S.ux));
+    const float cuy = fminf(limy, fmaxf(-limy, S.uy));
+    S.clampx = cux != S.ux;
+    S.clampy = cuy != S.uy;
+    S.txc = ml(cux, S.tzs);
+    S.tyc = ml(cuy, S.tzs);
+    const float tz2 = ml(S.tzs, S.tzs);
+    const float j00 = dv(C.fx, S.tzs);
+    const float j02 = -dv(ml(C.fx, S.txc), tz2);
+    const float j11 = dv(C.fy, S.tzs);
+    const float j12 = -dv(ml(C.fy, S.tyc), tz2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        S.T[0][k] = ad(ml(j00, V[k]), ml(j02, V[8 + k]));
+        S.T[1][k] = ad(ml(j11, V[4 + k]), ml(j12, V[8 + k]));
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            S.P[i][k] = dot3(S.T[i][0], S.M[0][k], S.T[i][1], S.M[1][k], S.T[i][2], S.M[2][k]);
+    const float n0 = dot3(S.P[0][0], S.P[0][0], S.P[0][1], S.P[0][1], S.P[0][2], S.P[0][2]);
+    const float n1 = dot3(S.P[1][0], S.P[1][0], S.P[1][1], S.P[1][1], S.P[1][2], S.P[1][2]);
+    S.a = ad(n0, kLowpass);
+    S.b = dot3(S.P[0][0], S.P[1][0], S.P[0][1], S.P[1][1], S.P[0][2], S.P[1][2]);
+    S.c = ad(n1, kLowpass);
+    const float m01 = sb(ml(S.P[0][0], S.P[1][1]), ml(S.P[0][1], S.P[1][0]));
+    const float m02 = sb(ml(S.P[0][0], S.P[1][2]), ml(S.P[0][2], S.P[1][0]));
+    const float m12 = sb(ml(S.P[0][1], S.P[1][2]), ml(S.P[0][2], S.P[1][1]));
+    S.det = ad(ad(dot3(m01, m01, m02, m02, m12, m12), ml(kLowpass, ad(n0, n1))),
+               ml(kLowpass, kLowpass));
+    S.mid = ml(0.5f, ad(S.a, S.c));
+    const float hd = ml(0.5f, sb(S.a, S.c));
+    S.disc = ad(ml(hd, hd), ml(S.b, S.b));
+    const float lam = ad(S.mid, __fsqrt_rn(fmaxf(0.1f, S.disc)));
+    float rf = ceilf(ml(3.0f, __fsqrt_rn(lam)));
+    const bool ok = in_front && qvalid && (S.det > 0.0f) && isfinite(S.px) && isfinite(S.py) &&
+                    isfinite(rf);
+    rf = ok ? fminf(rf, 1e9f) : 0.0f;   // radius capped at 1e9 px (exact in float and int)
+    S.rf = rf;
+    S.visible = ok && rf > 0.0f &&
+                tile_rect(S.px, S.py, rf, tw, th, gx, gy, S.x0, S.x1, S.y0, S.y1);
+}
+
+// Major axis (cos, sin) and the two eigenvalues of [[a, b], [b, c]] from the
+// Cauchy-Binet determinant; continuous, so ordinary fast arithmetic.
+__device__ __forceinline__ void eigen2(const Splat32 &S, float &uxo, float &uyo, float &lam1,
+                                       float &lam2) {
+    const float sq = sqrtf(S.disc);
+    lam1 = S.mid + sq;
+    lam2 = S.det / lam1;
+    if (sq > 0.0f) {
+        const float c2 = 0.5f * (S.a - S.c) / sq, s2 = S.b / sq;
+        if (c2 >= 0.0f) {
+            uxo = sqrtf(0.5f * (1.0f + c2));
+            uyo = s2 / (2.0f * uxo);
+        } else {
+            uyo = sqrtf(0.5f * (1.0f - c2));
+            uxo = s2 / (2.0f * uyo);
+        }
+    } else {
+        uxo = 1.0f;
+        uyo = 0.0f;
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int ROW = 3 * K;
+    constexpr int S_ = StageStride<ROW>::value;
+    __shared__ float sm_sh[kPreThreads / 32][32 * S_];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw0 = ((int64_t)blockIdx.x * kPreThreads) + warp * 32;
+    if (gw0 >= g.n) return;
+    const int nrows = (int)(g.n - gw0 < 32 ? g.n - gw0 : 32);
+    stage_rows<ROW>(g.sh, gw0, nrows, sm_sh[warp], lane);
+    const int64_t i = gw0 + lane;
+    if (lane >= nrows) return;
+
+    // --- mask sample (Sec. 3.3): Gumbel-max over the two existence scores
+    float Mf = 1.0f;
+    if (cfg.mask_mode == MG_MASK_GUMBEL) {
+        const uint4 x = philox4x32_10(
+            make_uint4((uint32_t)i, (uint32_t)cfg.iteration, (uint32_t)(cfg.iteration >> 32), 0u),
+            make_uint2((uint32_t)cfg.seed, (uint32_t)(cfg.seed >> 32)));
+        const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);
+        const float g0 = -log32(-log32(uniform24(x.x)));
+        const float g1 = -log32(-log32(uniform24(x.y)));
+        const float d = sb(ad(l.x, g0), ad(l.y, g1));
+        Mf = d >= 0.0f ? 1.0f : 0.0f;
+        out.mask_soft[i] = 1.0f / (1.0f + expf(-d / cfg.tau));
+    } else {
+        if (cfg.mask_mode == MG_MASK_GIVEN) Mf = cfg.given_mask[i] ? 1.0f : 0.0f;
+        out.mask_soft[i] = 1.0f;
+    }
+    out.mask[i] = Mf != 0.0f;
+
+    const float x = __ldg(g.means + 3 * i), y = __ldg(g.means + 3 * i + 1),
+                z = __ldg(g.means + 3 * i + 2);
+    const float ls[3] = {__ldg(g.log_scales + 3 * i), __ldg(g.log_scales + 3 * i + 1),
+                         __ldg(g.log_scales + 3 * i + 2)};
+    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
+    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
+    const float *shr = sm_sh[warp] + lane * S_;
+
+    for (int v = 0; v < vt.n_views; ++v) {
+        if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
+        const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
+        const mg_camera &C = vt.cam[v];
+        Splat32 S;
+        splat_fp32(C, vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z, ls, q, S);
+        if (!S.visible) {
+            out.tiles_touched[r] = 0u;
+            out.radius[r] = 0;
+            out.clamp[r] = 0;
+            continue;
+        }
+        out.tiles_touched[r] = (uint32_t)((S.x1 - S.x0 + 1) * (S.y1 - S.y0 + 1));
+        out.radius[r] = (int32_t)S.rf;
+        float ux, uy, l1, l2;
+        eigen2(S, ux, uy, l1, l2);
+        // view-dependent colour: SH at dir = normalise(p - cam_pos)
+        float dx = x - C.cam_pos[0], dy = y - C.cam_pos[1], dz = z - C.cam_pos[2];
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv; dy *= inv; dz *= inv;
+        float Y[16];
+        sh_basis(DEG, dx, dy, dz, Y);
+        float rgb[3];
+        uint8_t cl = 0;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], shr[3 * k + ch], acc);
+            if (acc < 0.0f) {
+                cl |= (uint8_t)(1u << ch);
+                acc = 0.0f;
+            }
+            rgb[ch] = acc;
+        }
+        out.clamp[r] = cl;
+        float4 *rec = reinterpret_cast<float4 *>(out.record) + 3 * r;
+        rec[0] = make_float4(S.px, S.py, ux, uy);
+        rec[1] = make_float4(-0.5f * kLog2e / l1, -0.5f * kLog2e / l2, op, Mf);
+        rec[2] = make_float4(rgb[0], rgb[1], rgb[2], S.tz);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward
+// ---------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats sp,
+                           const float *__restrict__ grad2d, mg_param_grads out) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int ROW = 3 * K;
+    constexpr int S_ = StageStride<ROW>::value;
+    __shared__ float sm_sh[kPreThreads / 32][32 * S_];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw0 = ((int64_t)blockIdx.x * kPreThreads) + warp * 32;
+    if (gw0 >= g.n) return;
+    const int nrows = (int)(g.n - gw0 < 32 ? g.n - gw0 : 32);
+    stage_rows<ROW>(g.sh, gw0, nrows, sm_sh[warp], lane);
+    const int64_t i = gw0 + lane;
+    if (lane >= nrows) return;
+    const float *shr = sm_sh[warp] + lane * S_;
+
+    const float x = __ldg(g.means + 3 * i), y = __ldg(g.means + 3 * i + 1),
+                z = __ldg(g.means + 3 * i + 2);
+    const float ls[3] = {__ldg(g.log_scales + 3 * i), __ldg(g.log_scales + 3 * i + 1),
+                         __ldg(g.log_scales + 3 * i + 2)};
+    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
+    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
+
+    float d_mean[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0}, d_op = 0.0f,
+          d_M = 0.0f;
+    float d_sh[ROW];
+#pragma unroll
+    for (int k = 0; k < ROW; ++k) d_sh[k] = 0.0f;
+
+    for (int v = 0; v < vt.n_views; ++v) {
+        if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
+        const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
+        if (sp.radius[r] == 0) continue;
+        const float4 *G4 = reinterpret_cast<const float4 *>(grad2d) + 3 * r;
+        const float4 g0 = G4[0], g1 = G4[1], g2 = G4[2];
+        // g0 = (dmx, dmy, dca, dcb), g1 = (dcc, dop, dr, dg), g2 = (db, dM, -, -)
+        d_M += g2.y;
+        d_op += g1.y;
+        const mg_camera &C = vt.cam[v];
+        Splat32 S;
+        splat_fp32(C, vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z, ls, q, S);
+        const float *V = C.viewmat;
+        float dL_dt[3] = {0, 0, 0};   // camera-space centre
+
+        // ---- colour: rgb_c = max(0, sum_k Y_k sh_kc + 0.5)
+        {
+            const float vx = x - C.cam_pos[0], vy = y - C.cam_pos[1], vz = z - C.cam_pos[2];
+            const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+            const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
+            float Y[16];
+            sh_basis(DEG, dx, dy, dz, Y);
+            const uint8_t cl = sp.clamp[r];
+            const float grgb[3] = {(cl & 1) ? 0.0f : g1.z, (cl & 2) ? 0.0f : g1.w,
+                                   (cl & 4) ? 0.0f : g2.x};
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) d_sh[3 * k + ch] = fmaf(Y[k], grgb[ch], d_sh[3 * k + ch]);
+            if (DEG > 0) {
+                float Yx[16], Yy[16], Yz[16];
+                sh_basis_grad(DEG, dx, dy, dz, Yx, Yy, Yz);
+                float gd[3] = {0, 0, 0};
+#pragma unroll
+                for (int k = 1; k < K; ++k) {
+                    const float t = grgb[0] * shr[3 * k] + grgb[1] * shr[3 * k + 1] +
+                                    grgb[2] * shr[3 * k + 2];
+                    gd[0] = fmaf(t, Yx[k], gd[0]);
+                    gd[1] = fmaf(t, Yy[k], gd[1]);
+                    gd[2] = fmaf(t, Yz[k], gd[2]);
+                }
+                // through dir = v / |v|
+                const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+                d_mean[0] += (gd[0] - dot * dx) * inv;
+                d_mean[1] += (gd[1] - dot * dy) * inv;
+                d_mean[2] += (gd[2] - dot * dz) * inv;
+            }
+        }
+
+        // ---- 2D mean: px = fx tx/tz + cx, py = fy ty/tz + cy
+        {
+            const float itz = 1.0f / S.tzs;
+            dL_dt[0] += g0.x * C.fx * itz;
+            dL_dt[1] += g0.y * C.fy * itz;
+            dL_dt[2] -= (g0.x * C.fx * S.ux + g0.y * C.fy * S.uy) * itz;
+        }
+
+        // ---- conic -> Sigma_bar (dSigma = -Q Ghat Q, Ghat symmetric with G_b/2 off-diagonal)
+        float ux, uy, l1, l2;
+        eigen2(S, ux, uy, l1, l2);
+        const float w1 = 1.0f / l1, w2 = 1.0f / l2;
+        const float Q00 = w1 * ux * ux + w2 * uy * uy;
+        const float Q01 = (w1 - w2) * ux * uy;
+        const float Q11 = w1 * uy * uy + w2 * ux * ux;
+        const float G00 = g0.z, G01 = 0.5f * g0.w, G11 = g1.x;
+        // A = Q Ghat
+        const float A00 = Q00 * G00 + Q01 * G01, A01 = Q00 * G01 + Q01 * G11;
+        const float A10 = Q01 * G00 + Q11 * G01, A11 = Q01 * G01 + Q11 * G11;
+        const float dS00 = -(A00 * Q00 + A01 * Q01);
+        const float dS01 = -(A00 * Q01 + A01 * Q11);
+        const float dS11 = -(A10 * Q01 + A11 * Q11);
+        // Sigma_bar = P P^T + 0.3 I  =>  dL/dP = 2 dSigma P  (dSigma symmetric)
+        float dP[2][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dP[0][k] = 2.0f * (dS00 * S.P[0][k] + dS01 * S.P[1][k]);
+            dP[1][k] = 2.0f * (dS01 * S.P[0][k] + dS11 * S.P[1][k]);
+        }
+        // P = T M:  dT = dP M^T, dM = T^T dP
+        float dT[2][3], dM[3][3];
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dT[r2][j] = dP[r2][0] * S.M[j][0] + dP[r2][1] * S.M[j][1] + dP[r2][2] * S.M[j][2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dM[j][k] = S.T[0][j] * dP[0][k] + S.T[1][j] * dP[1][k];
+        // M = R diag(s)
+        float dR[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dR[j][k] = dM[j][k] * S.s[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float ds = dM[0][k] * S.R[0][k] + dM[1][k] * S.R[1][k] + dM[2][k] * S.R[2][k];
+            d_ls[k] += ds * S.s[k];
+        }
+        // R(q_hat)
+        {
+            const float w = S.qn[0], qx = S.qn[1], qy = S.qn[2], qz = S.qn[3];
+            float gw = 2.0f * (qz * (dR[1][0] - dR[0][1]) + qy * (dR[0][2] - dR[2][0]) +
+                               qx * (dR[2][1] - dR[1][2]));
+            float gx = 2.0f * (qy * (dR[1][0] + dR[0][1]) + qz * (dR[2][0] + dR[0][2]) +
+                               w * (dR[2][1] - dR[1][2])) - 4.0f * qx * (dR[1][1] + dR[2][2]);
+            float gy = 2.0f * (qx * (dR[1][0] + dR[0][1]) + w * (dR[0][2] - dR[2][0]) +
+                               qz * (dR[1][2] + dR[2][1])) - 4.0f * qy * (dR[0][0] + dR[2][2]);
+            float gz = 2.0f * (w * (dR[1][0] - dR[0][1]) + qx * (dR[2][0] + dR[0][2]) +
+                               qy * (dR[1][2] + dR[2][1])) - 4.0f * qz * (dR[0][0] + dR[1][1]);
+            // through q_hat = q / |q|
+            const float dot = gw * w + gx * qx + gy * qy + gz * qz;
+            const float in = 1.0f / S.nrm;
+            d_q[0] += (gw - dot * w) * in;
+            d_q[1] += (gx - dot * qx) * in;
+            d_q[2] += (gy - dot * qy) * in;
+            d_q[3] += (gz - dot * qz) * in;
+        }
+        // T = J W:  dJ = dT W^T ; J = [[fx/tz, 0, -fx txc/tz^2], [0, fy/tz, -fy tyc/tz^2]]
+        {
+            float dJ00 = 0, dJ02 = 0, dJ11 = 0, dJ12 = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dJ00 += dT[0][k] * V[k];
+                dJ02 += dT[0][k] * V[8 + k];
+                dJ11 += dT[1][k] * V[4 + k];
+                dJ12 += dT[1][k] * V[8 + k];
+            }
+            const float itz = 1.0f / S.tzs, itz2 = itz * itz, itz3 = itz2 * itz;
+            // d J02 / d tz: 2 fx txc / tz^3 unclamped, fx txc / tz^3 clamped
+            dL_dt[2] += -dJ00 * C.fx * itz2 - dJ11 * C.fy * itz2 +
+                        dJ02 * C.fx * S.txc * itz3 * (S.clampx ? 1.0f : 2.0f) +
+                        dJ12 * C.fy * S.tyc * itz3 * (S.clampy ? 1.0f : 2.0f);
+            if (!S.clampx) dL_dt[0] += -dJ02 * C.fx * itz2;
+            if (!S.clampy) dL_dt[1] += -dJ12 * C.fy * itz2;
+        }
+        // t = W p + t_cam  =>  dp += W^T dt
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d_mean[k] += V[k] * dL_dt[0] + V[4 + k] * dL_dt[1] + V[8 + k] * dL_dt[2];
+    }
+
+    out.means[3 * i] = d_mean[0];
+    out.means[3 * i + 1] = d_mean[1];
+    out.means[3 * i + 2] = d_mean[2];
+    out.log_scales[3 * i] = d_ls[0];
+    out.log_scales[3 * i + 1] = d_ls[1];
+    out.log_scales[3 * i + 2] = d_ls[2];
+    reinterpret_cast<float4 *>(out.quats)[i] = make_float4(d_q[0], d_q[1], d_q[2], d_q[3]);
+    out.opacity_logit[i] = d_op * op * (1.0f - op);
+    float *dsh = out.sh + (int64_t)ROW * i;
+#pragma unroll
+    for (int k = 0; k < ROW; ++k) dsh[k] = d_sh[k];
+    float dl0 = 0.0f;
+    if (cfg.mask_mode == MG_MASK_GUMBEL) {
+        const float y0 = sp.mask_soft[i];
+        dl0 = d_M * y0 * (1.0f - y0) / cfg.tau;
+    }
+    reinterpret_cast<float2 *>(out.mask_logits)[i] = make_float2(dl0, -dl0);
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static mg_status check_gaussians(const mg_gaussians *g) {
+    if (g == nullptr || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3 ||
+        g->dtype != MG_DTYPE_F32)
+        return MG_ERR_INVALID_ARG;
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->sh ||
+                     !g->mask_logits))
+        return MG_ERR_INVALID_ARG;
+    if (!aligned(g->quats, 16) || !aligned(g->mask_logits, 8)) return MG_ERR_INVALID_ARG;
+    if (g->n >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
+    return MG_OK;
+}
+
+static mg_status check_views(const mg_gaussians *g, const mg_view *views, int32_t n_views,
+                             const mg_raster_cfg *cfg, ViewTable *vt) {
+    mg_status st = mg_host::build_view_table(views, n_views, cfg, vt);
+    if (st != MG_OK) return st;
+    for (int v = 0; v < n_views; ++v)
+        if (views[v].gaussian_offset + views[v].gaussian_count > g->n) return MG_ERR_INVALID_ARG;
+    if (vt->rec_off[n_views] >= (int64_t(1) << 32)) return MG_ERR_INVALID_ARG;
+    return MG_OK;
+}
+
+extern "C" mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, int32_t n_views,
+                                   const mg_raster_cfg *cfg, const mg_splats *out,
+                                   mg_status_word *d_status, mg_stream_t stream) {
+    (void)d_status;
+    if (check_gaussians(g) != MG_OK || cfg == nullptr || out == nullptr || !(cfg->tau > 0.0f))
+        return MG_ERR_INVALID_ARG;
+    if (cfg->mask_mode < 0 || cfg->mask_mode > 2) return MG_ERR_INVALID_ARG;
+    if (cfg->mask_mode == MG_MASK_GIVEN && cfg->given_mask == nullptr) return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = check_views(g, views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    if (g->n == 0) return MG_OK;
+    if (!out->record || !out->tiles_touched || !out->radius || !out->clamp || !out->mask ||
+        !out->mask_soft || !aligned(out->record, 16))
+        return MG_ERR_INVALID_ARG;
+    const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (g->sh_degree) {
+        case 0: preprocess_kernel<0><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
+        case 1: preprocess_kernel<1><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
+        case 2: preprocess_kernel<2><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
+        default: preprocess_kernel<3><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
+    }
+    return mg_host::launch_status();
+}
+
+extern "C" mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view *views,
+                                            int32_t n_views, const mg_raster_cfg *cfg,
+                                            const mg_splats *splats, const float *grad2d,
+                                            const mg_param_grads *out, mg_stream_t stream) {
+    if (check_gaussians(g) != MG_OK || cfg == nullptr || splats == nullptr || out == nullptr ||
+        !(cfg->tau > 0.0f))
+        return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = check_views(g, views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    if (g->n == 0) return MG_OK;
+    if (!grad2d || !aligned(grad2d, 16) || !out->means || !out->log_scales || !out->quats ||
+        !aligned(out->quats, 16) || !out->opacity_logit || !out->sh || !out->mask_logits ||
+        !aligned(out->mask_logits, 8) || !splats->radius || !splats->clamp || !splats->mask_soft)
+        return MG_ERR_INVALID_ARG;
+    const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (g->sh_degree) {
+        case 0: preprocess_backward_kernel<0><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
+        case 1: preprocess_backward_kernel<1><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
+        case 2: preprocess_backward_kernel<2><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
+        default: preprocess_backward_kernel<3><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
+    }
+    return mg_host::launch_status();
+}

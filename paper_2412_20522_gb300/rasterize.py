@@ -1,0 +1,301 @@
+"""Masked rasterisation step on the GPU: buffers, launch sequence, autograd.
+
+PyTorch provides device memory and the stream; every stage of the step runs
+in libmaskgs through the C ABI (``abi``).  The per-step state kept between
+forward and backward is per-pixel only (final transmittance and stop index):
+the backward recomputes every fragment instead of storing it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import abi
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")
+
+
+@dataclass
+class RasterConfig:
+    tile_w: int = 16
+    tile_h: int = 16
+    bg: tuple = (0.0, 0.0, 0.0)
+    tau: float = 1.0
+    seed: int = 2024124
+    iteration: int = 0
+    mask_mode: int = abi.MG_MASK_GUMBEL
+    given_mask: torch.Tensor | None = None     # uint8 [n] on the device
+
+    def c(self) -> abi.mg_raster_cfg:
+        cfg = abi.mg_raster_cfg()
+        cfg.tile_w, cfg.tile_h = self.tile_w, self.tile_h
+        for i in range(3):
+            cfg.bg[i] = float(self.bg[i])
+        cfg.tau = float(self.tau)
+        cfg.seed = int(self.seed)
+        cfg.iteration = int(self.iteration)
+        cfg.mask_mode = int(self.mask_mode)
+        cfg.given_mask = abi.ptr(self.given_mask) if self.given_mask is not None else None
+        return cfg
+
+
+def make_views(cams, ranges=None):
+    """ctypes array of mg_view.  ``ranges``: per view (gaussian_offset, count);
+    None means every view sees the same n Gaussians (set later by the caller)."""
+    n = len(cams)
+    if not 1 <= n <= abi.MG_MAX_VIEWS:
+        raise ValueError(f"1..{abi.MG_MAX_VIEWS} views supported, got {n}")
+    arr = (abi.mg_view * n)()
+    for i, cam in enumerate(cams):
+        c = arr[i].cam
+        c.width, c.height = int(cam.width), int(cam.height)
+        c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+        vm = [float(x) for x in cam.viewmat.reshape(-1)]
+        for k in range(12):
+            c.viewmat[k] = vm[k]
+        for k in range(3):
+            c.cam_pos[k] = float(cam.cam_pos[k])
+        c.near_plane = float(cam.near)
+        if ranges is not None:
+            arr[i].gaussian_offset, arr[i].gaussian_count = (int(x) for x in ranges[i])
+    return arr
+
+
+def _gaussians_struct(p: dict, sh_degree: int) -> abi.mg_gaussians:
+    g = abi.mg_gaussians()
+    g.n = int(p["means"].shape[0])
+    g.sh_degree = int(sh_degree)
+    g.dtype = abi.MG_DTYPE_F32
+    for name in PARAM_NAMES:
+        t = p[name]
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: contiguous float32 CUDA tensor required")
+        setattr(g, name, t.data_ptr())
+    return g
+
+
+class _Events:
+    """Optional per-stage CUDA events {name: (start, end)} on the current stream."""
+
+    def __init__(self, events):
+        self.events = events
+
+    def begin(self, name):
+        if self.events is not None and name in self.events:
+            self.events[name][0].record()
+
+    def end(self, name):
+        if self.events is not None and name in self.events:
+            self.events[name][1].record()
+
+
+class Rasterizer:
+    """Owns the device buffers of one masked forward+backward and issues the
+    C-ABI calls on the current torch stream."""
+
+    def __init__(self, device="cuda", capacity: int = 0, capacity_headroom: float = 1.25):
+        self.device = torch.device(device)
+        self.capacity = int(capacity)
+        self.headroom = capacity_headroom
+        self._buf = {}
+        self.status = torch.zeros(2, dtype=torch.int64, device=self.device)   # mg_status_word
+        self.frag_count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.num_instances = torch.zeros(1, dtype=torch.int64, device=self.device)
+
+    # -- buffers -------------------------------------------------------------
+    def _get(self, name, numel, dtype):
+        t = self._buf.get(name)
+        if t is None or t.numel() < numel or t.dtype != dtype:
+            t = torch.empty(max(int(numel), 1), dtype=dtype, device=self.device)
+            self._buf[name] = t
+        return t[:max(int(numel), 1)]
+
+    def _stream(self):
+        return C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _splats(self, R, n):
+        s = abi.mg_splats()
+        s.record = self._get("record", R * abi.MG_RECORD_FLOATS, torch.float32).data_ptr()
+        s.tiles_touched = self._get("tiles", R, torch.int32).data_ptr()
+        s.radius = self._get("radius", R, torch.int32).data_ptr()
+        s.clamp = self._get("clamp", R, torch.uint8).data_ptr()
+        s.mask = self._get("mask", n, torch.uint8).data_ptr()
+        s.mask_soft = self._get("mask_soft", n, torch.float32).data_ptr()
+        return s
+
+    def _ensure_sort_buffers(self, cap, key_bits):
+        self._get("keys", cap, torch.int64)
+        self._get("vals", cap, torch.int32)
+        self._get("keys_alt", cap, torch.int64)
+        self._get("vals_alt", cap, torch.int32)
+        self._get("sort_ws", abi.mg_sort_workspace_bytes(cap, key_bits), torch.uint8)
+
+    # -- forward --------------------------------------------------------------
+    def forward(self, params: dict, cams, cfg: RasterConfig, view_ranges=None, check=True,
+                count_fragments=False, stage_events=None):
+        """Masked forward.  Returns the concatenated images (flat float32,
+        per view [3][H][W])."""
+        n = int(params["means"].shape[0])
+        sh_degree = int(round(math.sqrt(params["sh"].shape[1]))) - 1
+        ranges = view_ranges if view_ranges is not None else [(0, n)] * len(cams)
+        views = make_views(cams, ranges)
+        V = len(cams)
+        ccfg = cfg.c()
+        g = _gaussians_struct(params, sh_degree)
+        R = sum(int(r[1]) for r in ranges)
+        pix = sum(int(c.width) * int(c.height) for c in cams)
+        tiles = abi.mg_total_tiles(views, V, ccfg)
+        key_bits = abi.mg_key_bits(views, V, ccfg)
+        stream = self._stream()
+        ev = _Events(stage_events)
+        self.status.zero_()
+        splats = self._splats(R, n)
+        ev.begin("preprocess")
+        abi.mg_preprocess(g, views, V, ccfg, splats, self.status, stream)
+        ev.end("preprocess")
+        offsets = self._get("offsets", R, torch.int32)
+        bin_ws = self._get("bin_ws", abi.mg_bin_workspace_bytes(R), torch.uint8)
+        if self.capacity <= 0:
+            # size the instance buffers from this step's own count
+            abi.mg_bin(splats, views, V, ccfg, offsets, None, None, 0, self.num_instances,
+                       bin_ws, bin_ws.numel(), self.status, stream)
+            k = int(self.num_instances.item())
+            self.capacity = max(int(k * self.headroom), 1024)
+            self.status.zero_()
+        self._ensure_sort_buffers(self.capacity, key_bits)
+        ev.begin("bin")
+        abi.mg_bin(splats, views, V, ccfg, offsets, self._buf["keys"], self._buf["vals"],
+                   self.capacity, self.num_instances, bin_ws, bin_ws.numel(), self.status, stream)
+        ev.end("bin")
+        if check:
+            st = abi.mg_read_status(self.status, stream)
+            if st.status == abi.MG_ERR_CAPACITY:
+                self.capacity = int(st.required * self.headroom) + 1024
+                self._ensure_sort_buffers(self.capacity, key_bits)
+                self.status.zero_()
+                abi.mg_bin(splats, views, V, ccfg, offsets, self._buf["keys"], self._buf["vals"],
+                           self.capacity, self.num_instances, bin_ws, bin_ws.numel(),
+                           self.status, stream)
+            elif st.status != abi.MG_OK:
+                raise abi.MaskgsError("mg_bin", st.status)
+        ranges_buf = self._get("ranges", 2 * tiles, torch.int32)
+        sort_ws = self._buf["sort_ws"]
+        ev.begin("sort")
+        alt = abi.mg_sort(self._buf["keys"], self._buf["vals"], self._buf["keys_alt"],
+                          self._buf["vals_alt"], self.num_instances, self.capacity, key_bits,
+                          ranges_buf, tiles, sort_ws, sort_ws.numel(), self.status, stream)
+        ev.end("sort")
+        sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
+        image = self._get("image", 3 * pix, torch.float32)
+        final_T = self._get("final_T", pix, torch.float32)
+        n_contrib = self._get("n_contrib", pix, torch.int32)
+        if count_fragments:
+            self.frag_count.zero_()
+        ev.begin("render")
+        abi.mg_render(splats, sorted_vals, ranges_buf, views, V, ccfg, image, final_T, n_contrib,
+                      self.frag_count if count_fragments else None, stream)
+        ev.end("render")
+        # kernels of ours per forward: preprocess; scan + duplicate; histogram,
+        # offsets, one per digit pass, ranges; render
+        self._fwd_launches = 1 + 2 + 3 + (key_bits + 7) // 8 + 1
+        self._state = dict(g=g, views=views, V=V, cfg=ccfg, splats=splats, R=R, n=n, pix=pix,
+                           sorted_vals=sorted_vals, ranges=ranges_buf, tiles=tiles,
+                           sh_degree=sh_degree, params=params, cams=cams)
+        if check:
+            st = abi.mg_read_status(self.status, stream)
+            if st.status != abi.MG_OK:
+                raise abi.MaskgsError("masked forward", st.status)
+        return image
+
+    # -- loss -----------------------------------------------------------------
+    def launches_per_step(self):
+        return self._fwd_launches
+
+    def backward_launches(self):
+        return 2
+
+    def l1_loss_grad(self, image, target):
+        s = self._state
+        dimg = self._get("dL_dimage", 3 * s["pix"], torch.float32)
+        loss = self._get("loss", 1, torch.float32)
+        loss.zero_()
+        abi.mg_l1_loss_grad(image, target, s["views"], s["V"], dimg, loss, self._stream())
+        return loss, dimg
+
+    # -- backward -------------------------------------------------------------
+    def backward(self, dL_dimage, out: dict | None = None, stage_events=None):
+        """Gradients of <dL_dimage, image> w.r.t. every parameter (overwritten
+        into ``out`` when given)."""
+        s = self._state
+        stream = self._stream()
+        ev = _Events(stage_events)
+        grad2d = self._get("grad2d", s["R"] * abi.MG_GRAD2D_FLOATS, torch.float32)
+        ev.begin("render_bwd")
+        abi.mg_render_backward(s["splats"], s["sorted_vals"], s["ranges"], s["views"], s["V"],
+                               s["cfg"], self._buf["final_T"], self._buf["n_contrib"], dL_dimage,
+                               grad2d, stream)
+        if out is None:
+            out = {k: torch.empty_like(s["params"][k]) for k in PARAM_NAMES}
+        ev.end("render_bwd")
+        pg = abi.mg_param_grads()
+        for k in PARAM_NAMES:
+            setattr(pg, k, out[k].data_ptr())
+        ev.begin("preprocess_bwd")
+        abi.mg_preprocess_backward(s["g"], s["views"], s["V"], s["cfg"], s["splats"], grad2d, pg,
+                                   stream)
+        ev.end("preprocess_bwd")
+        return out
+
+    # -- views of the forward state -------------------------------------------
+    def splat_outputs(self):
+        s = self._state
+        R, n = s["R"], s["n"]
+        return dict(record=self._buf["record"][:R * 12].view(R, 12),
+                    tiles=self._buf["tiles"][:R], radius=self._buf["radius"][:R],
+                    clamp=self._buf["clamp"][:R], mask=self._buf["mask"][:n],
+                    mask_soft=self._buf["mask_soft"][:n], offsets=self._buf["offsets"][:R],
+                    sorted_vals=s["sorted_vals"], ranges=s["ranges"][:2 * s["tiles"]],
+                    final_T=self._buf["final_T"][:s["pix"]],
+                    n_contrib=self._buf["n_contrib"][:s["pix"]],
+                    num_instances=self.num_instances, grad2d=self._buf.get("grad2d"))
+
+    def sorted_keys(self):
+        s = self._state
+        return self._buf["keys_alt"] if s["sorted_vals"] is self._buf["vals_alt"] else self._buf["keys"]
+
+
+class MaskedRasterize(torch.autograd.Function):
+    """images = MaskedRasterize.apply(means, log_scales, quats, opacity_logit,
+    sh, mask_logits, rasterizer, cams, cfg) -- the concatenated per-view
+    images; the backward is the hand-written one of libmaskgs."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, mask_logits, rast, cams, cfg):
+        params = dict(means=means.detach(), log_scales=log_scales.detach(),
+                      quats=quats.detach(), opacity_logit=opacity_logit.detach(),
+                      sh=sh.detach(), mask_logits=mask_logits.detach())
+        img = rast.forward(params, cams, cfg)
+        ctx.rast = rast
+        return img.clone()
+
+    @staticmethod
+    def backward(ctx, dimg):
+        out = ctx.rast.backward(dimg.contiguous())
+        return (out["means"], out["log_scales"], out["quats"], out["opacity_logit"], out["sh"],
+                out["mask_logits"], None, None, None)
+
+
+def rasterize(params: dict, cams, cfg: RasterConfig, rast: Rasterizer | None = None):
+    """Differentiable masked rasterisation of ``params`` (float32 CUDA tensors)
+    for ``cams``; returns a list of [3, H, W] images."""
+    rast = rast or Rasterizer(params["means"].device)
+    flat = MaskedRasterize.apply(*(params[k] for k in PARAM_NAMES), rast, cams, cfg)
+    out, o = [], 0
+    for c in cams:
+        n = 3 * c.width * c.height
+        out.append(flat[o:o + n].view(3, c.height, c.width))
+        o += n
+    return out

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by
+element, on seeded inputs.
+
+Bit-exact: masks, tile counts, radii, 2D means and depth keys, instance
+offsets and count, sorted keys and values, tile ranges.  Floating point:
+images within 2e-4 absolute per channel and gradients within 1e-3 relative L2
+per tensor (FP32 against FP64).  Pixels where one FP64 fragment decision lies
+within the straddle band of its threshold (alpha floor, termination, power
+sign) are counted and reported; they are excluded from the image bound only
+if flagged, and their upstream gradient is zeroed on both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import rel_l2, split_views, to_device
+from oracle import pipeline
+from paper_2412_20522_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 2e-4
+GRAD_TOL = 1e-3
+EPS = 1e-3          # straddle band (relative), see the oracle's render
+
+
+@pytest.fixture(scope="module")
+def rz():
+    from paper_2412_20522_gb300 import rasterize
+    return rasterize
+
+
+def _run(rz, g, cams, targets, cfg_kw=None, tile=(16, 16), view_ranges=None, capacity=0):
+    cfg_kw = cfg_kw or {}
+    dev = to_device(g)
+    rcfg = rz.RasterConfig(tile_w=tile[0], tile_h=tile[1], **cfg_kw)
+    rast = rz.Rasterizer(capacity=capacity)
+    img = rast.forward(dev, cams, rcfg, view_ranges=view_ranges, count_fragments=True)
+    torch.cuda.synchronize()
+    return rast, dev, img
+
+
+def _oracle(g, cams, cfg_kw=None, tile=(16, 16)):
+    cfg_kw = dict(cfg_kw or {})
+    gm = cfg_kw.pop("given_mask", None)
+    ocfg = pipeline.OracleConfig(tile_w=tile[0], tile_h=tile[1], eps=EPS, **cfg_kw)
+    if gm is not None:
+        ocfg.given_mask = gm.cpu().numpy()
+    views, M, minfo = pipeline.forward(g, cams, ocfg)
+    return ocfg, views, M, minfo
+
+
+def _check_discrete(rast, views, M, cams):
+    so = rast.splat_outputs()
+    assert np.array_equal(so["mask"].cpu().numpy(), M), "sampled masks differ"
+    rec = so["record"].cpu().numpy()
+    tiles = so["tiles"].cpu().numpy().view(np.uint32)
+    radius = so["radius"].cpu().numpy()
+    offs = so["offsets"].cpu().numpy().view(np.uint32)
+    K_gpu = int(so["num_instances"].item())
+    R0 = 0
+    T0 = 0
+    K0 = 0
+    ranges = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
+    vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:K_gpu]
+    keys = rast.sorted_keys().cpu().numpy().view(np.uint64)[:K_gpu]
+    for v, cam in zip(views, cams):
+        n = v.fp32["tiles"].shape[0]
+        fp = v.fp32
+        assert np.array_equal(tiles[R0:R0 + n], fp["tiles"]), "tiles_touched differ"
+        assert np.array_equal(radius[R0:R0 + n], fp["radius"]), "radius differs"
+        vis = fp["visible"]
+        r = rec[R0:R0 + n]
+        assert np.array_equal(r[vis, 0].view(np.uint32), fp["px"][vis].view(np.uint32))
+        assert np.array_equal(r[vis, 1].view(np.uint32), fp["py"][vis].view(np.uint32))
+        assert np.array_equal(r[vis, 11].view(np.uint32), fp["depth_bits"][vis])
+        assert np.array_equal(offs[R0:R0 + n].astype(np.uint64),
+                              v.offsets.astype(np.uint64) + np.uint64(K0)), "scan offsets differ"
+        nt = v.ranges.shape[0]
+        # the oracle's keys are per view: shift its tile ids by the view's tile offset
+        okeys = v.sorted_keys + (np.uint64(T0) << np.uint64(32))
+        assert np.array_equal(keys[K0:K0 + v.K], okeys), "sorted keys differ"
+        assert np.array_equal(vals[K0:K0 + v.K], v.sorted_vals.astype(np.uint32) + R0), "sorted values differ"
+        gr = ranges[T0:T0 + nt].astype(np.int64)
+        orr = v.ranges.astype(np.int64)
+        nonempty = orr[:, 1] > orr[:, 0]
+        assert np.array_equal(gr[nonempty], orr[nonempty] + K0), "tile ranges differ"
+        assert (gr[~nonempty, 1] == gr[~nonempty, 0]).all()
+        R0 += n
+        T0 += nt
+        K0 += v.K
+    assert K_gpu == K0
+
+
+def _check_images(rast, img, views, cams, report):
+    so = rast.splat_outputs()
+    gimgs = split_views(img.cpu().numpy(), cams)
+    gT = split_views(so["final_T"].cpu().numpy(), cams, 1)
+    gN = split_views(so["n_contrib"].cpu().numpy(), cams, 1)
+    masks = []
+    for v, gi, gt, gn in zip(views, gimgs, gT, gN):
+        straddle = (v.out["flags"] & 11) != 0
+        d = np.abs(gi - v.out["image"]).max(0)
+        bad = (d > IMG_TOL) & ~straddle
+        report.append(dict(pixels=d.size, straddle=int(straddle.sum()),
+                           over_tol=int((d > IMG_TOL).sum()), max_err_clean=float(d[~straddle].max()) if (~straddle).any() else 0.0))
+        assert not bad.any(), f"{bad.sum()} non-straddle pixels over {IMG_TOL}: max {d[bad].max()}"
+        assert np.abs(gt - v.out["final_T"])[~straddle].max() < 1e-4
+        assert np.array_equal(gn[~straddle], v.out["n_contrib"][~straddle])
+        assert straddle.mean() < 0.02
+        masks.append(straddle)
+    return masks
+
+
+def _check_backward(rast, dev, g, cams, ocfg, views, M, minfo, straddles, targets):
+    # the same upstream gradient on both sides: the oracle's L1 gradient,
+    # zeroed on straddle pixels
+    dimgs = []
+    for v, t, s in zip(views, targets, straddles):
+        _, d = pipeline.l1_loss_grad(v.out["image"], t)
+        d = d * (~s)[None]
+        dimgs.append(d)
+    grads, per_view = pipeline.backward(g, cams, ocfg, views, M, minfo, dimgs)
+    flat = np.concatenate([d.reshape(-1) for d in dimgs]).astype(np.float32)
+    out = rast.backward(torch.as_tensor(flat).cuda())
+    torch.cuda.synchronize()
+    errs = {}
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits"):
+        errs[k] = rel_l2(out[k].cpu().numpy(), grads[k])
+    g2 = rast.splat_outputs()["grad2d"].cpu().numpy().reshape(-1, 12)
+    R0 = 0
+    for v, pv in zip(views, per_view):
+        n = pv["dmask"].shape[0]
+        G = g2[R0:R0 + n]
+        errs.setdefault("dmean2d", []).append(rel_l2(G[:, 0:2], pv["dmean2d"]))
+        errs.setdefault("dconic", []).append(rel_l2(G[:, 2:5], pv["dconic"]))
+        errs.setdefault("dopacity", []).append(rel_l2(G[:, 5], pv["dopacity"]))
+        errs.setdefault("drgb", []).append(rel_l2(G[:, 6:9], pv["drgb"]))
+        errs.setdefault("dmask", []).append(rel_l2(G[:, 9], pv["dmask"]))
+        R0 += n
+    flatten = {k: (max(v) if isinstance(v, list) else v) for k, v in errs.items()}
+    bad = {k: e for k, e in flatten.items() if not e <= GRAD_TOL}
+    assert not bad, f"gradients over {GRAD_TOL} relative L2: {bad} (all: {flatten})"
+    return flatten
+
+
+def _full_check(rz, g, cams, targets, cfg_kw=None, tile=(16, 16)):
+    rast, dev, img = _run(rz, g, cams, targets, cfg_kw, tile)
+    ocfg, views, M, minfo = _oracle(g, cams, cfg_kw, tile)
+    _check_discrete(rast, views, M, cams)
+    rep = []
+    straddles = _check_images(rast, img, views, cams, rep)
+    errs = _check_backward(rast, dev, g, cams, ocfg, views, M, minfo, straddles, targets)
+    print("image report", rep, "grad errors", errs)
+    return rast, views
+
+
+def test_tiny_workload(rz):
+    g, cams, tgt = scenes.tiny_workload()
+    _full_check(rz, g, cams, [tgt])
+
+
+def test_tiny_workload_background_and_other_seed(rz):
+    g, cams, tgt = scenes.tiny_workload()
+    _full_check(rz, g, cams, [tgt], dict(bg=(0.9, 0.4, 0.1), seed=77, iteration=12345678901))
+
+
+def test_tile_8x32_and_ragged_frame(rz):
+    g = scenes.uniform_gaussians(3000, seed=5)
+    cams = [scenes.look_at_camera((0.2, -0.1, -3.2), (0, 0, 0), 100, 75, 90.0)]
+    tgt = scenes.target_image(75, 100, seed=9)
+    for tile in ((8, 32), (32, 8), (16, 16)):
+        _full_check(rz, g, cams, [tgt], dict(bg=(0.2, 0.3, 0.4)), tile)
+
+
+def test_all_ones_and_given_masks(rz):
+    g, cams, tgt = scenes.tiny_workload(4000)
+    _full_check(rz, g, cams, [tgt], dict(mask_mode=1))
+    gm = torch.as_tensor((np.arange(g.n) % 3 == 0).astype(np.uint8)).cuda()
+    _full_check(rz, g, cams, [tgt], dict(mask_mode=2, given_mask=gm))
+
+
+def test_sh_degrees(rz):
+    for deg in (0, 1, 2):
+        g = scenes.uniform_gaussians(2000, seed=3 + deg, sh_degree=deg)
+        cams = [scenes.look_at_camera((0, 0, -3), (0, 0, 0), 64, 48, 60.0)]
+        _full_check(rz, g, cams, [scenes.target_image(48, 64, seed=4)])
+
+
+def test_multi_view_shared_mask(rz):
+    g = scenes.cluster_gaussians(20_000, seed=21, centre_radius=1.5, reject_radius=2.0,
+                                 log_scale_mu=-4.0, log_scale_sigma=0.5)
+    cams = [scenes.ring_camera(2 * math.pi * k / 3, 4.0, 96 + 16 * k, 64 + 8 * k, 80.0)
+            for k in range(3)]
+    tg = [scenes.target_image(c.height, c.width, seed=30 + k) for k, c in enumerate(cams)]
+    _full_check(rz, g, cams, tg, dict(bg=(0.1, 0.1, 0.1)))
+
+
+def test_mid_scene_clusters(rz):
+    """100k clustered Gaussians, camera inside the cloud: needle splats, huge
+    near-camera splats, long tile lists, many tiles with a ragged edge."""
+    g = scenes.cluster_gaussians(100_000, seed=8)
+    cams = [scenes.ring_camera(0.0, 4.0, 389, 259, 287.5)]
+    _full_check(rz, g, cams, [scenes.target_image(259, 389, seed=2)])
+
+
+def test_empty_scene_renders_background(rz):
+    g = scenes.uniform_gaussians(0)
+    cams = [scenes.look_at_camera((0, 0, -3), (0, 0, 0), 40, 30, 30.0)]
+    rast, dev, img = _run(rz, g, cams, None, dict(bg=(0.25, 0.5, 0.75)))
+    im = img.cpu().numpy().reshape(3, 30, 40)
+    assert np.allclose(im[0], 0.25) and np.allclose(im[1], 0.5) and np.allclose(im[2], 0.75)
+    assert (rast.splat_outputs()["final_T"].cpu().numpy() == 1.0).all()
+
+
+def test_all_culled_scene(rz):
+    g = scenes.uniform_gaussians(500, seed=1)
+    g.means[:, 2] = -10.0                      # every Gaussian behind the camera
+    cams = [scenes.look_at_camera((0, 0, -3), (0, 0, 0), 48, 48, 40.0)]
+    rast, dev, img = _run(rz, g, cams, None)
+    assert int(rast.num_instances.item()) == 0
+    assert np.allclose(img.cpu().numpy(), 0.0)
+    out = rast.backward(torch.ones_like(img))
+    for k in ("means", "sh", "opacity_logit"):
+        assert float(out[k].abs().max()) == 0.0
