@@ -100,10 +100,21 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 flops per evaluated (pixel, splat) pair of the render kernels, counted
-# from the arithmetic of the method (FMA = 2, ex2 / div = 1); see the design doc.
-FLOPS_FWD_PER_FRAG = 24
-FLOPS_BWD_PER_FRAG = 62
+# Algorithmic FP32 flops of the render kernels (FMA = 2; ex2, div = 1), from
+# the arithmetic of the method per (pixel, splat) pair:
+#   alpha evaluation (offset, eigen-form quadratic, exp, opacity)       15
+#   forward blend of an unmasked splat (test T, weight, 3 colours)        9
+#   backward of a masked splat (T_i, g.(c - b), dL/dM)                  12
+#   backward of an unmasked splat (T_i, g.(c - b), dL/dM, dL/dc, b,
+#     dL/dalpha, dL/do, dL/dconic, dL/dmean2d)                           48
+FLOPS_ALPHA, FLOPS_FWD_BLEND, FLOPS_BWD_MASKED, FLOPS_BWD_UNMASKED = 15, 9, 12, 48
+
+
+def render_flops(counts):
+    walked, walked_on, blend_on, contrib_off = (int(x) for x in counts)
+    fwd = walked_on * FLOPS_ALPHA + blend_on * FLOPS_FWD_BLEND
+    bwd = walked * FLOPS_ALPHA + contrib_off * FLOPS_BWD_MASKED + blend_on * FLOPS_BWD_UNMASKED
+    return fwd, bwd
 
 
 def run_ours(args):
@@ -183,7 +194,8 @@ def run_ours(args):
     # counts of this workload (one extra counted step, outside the timed region)
     step(count=True)
     torch.cuda.synchronize()
-    frags = int(rast.frag_count.item())
+    counts = rast.frag_count.cpu().tolist()
+    flops_fwd, flops_bwd = render_flops(counts)
     K = int(rast.num_instances.item())
     so = rast.splat_outputs()
     visible = int((so["radius"] > 0).sum().item())
@@ -234,8 +246,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak_tflops = sms * 128 * 2 * smmax * 1e6 / 1e12
     if dom in ("render", "render_bwd"):
-        per = FLOPS_FWD_PER_FRAG if dom == "render" else FLOPS_BWD_PER_FRAG
-        achieved = frags * per / (stage_ms[dom] * 1e-3) / 1e12
+        achieved = (flops_fwd if dom == "render" else flops_bwd) / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
                 "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)"}
@@ -255,7 +266,9 @@ def run_ours(args):
         "data": "synthetic (seeded cluster-mixture scene standing in for Mip-NeRF360-scale captures)",
         "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W, "height": H, "views": 1,
                    "tile": "16x16", "sh_degree": 3, "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"replicas x{ws}", "instances_K": K, "fragments_F": frags,
+                   "parallelism": f"replicas x{ws}", "instances_K": K, "fragments": {"walked": counts[0], "walked_unmasked": counts[1],
+                                                  "blended": counts[2], "masked_above_floor": counts[3]},
+                   "render_gflop": {"fwd": flops_fwd / 1e9, "bwd": flops_bwd / 1e9},
                    "visible": visible, "mask_on_fraction": mask_on},
         "stage_ms": stage_ms,
         "roofline": roof,

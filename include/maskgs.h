@@ -224,8 +224,11 @@ int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cf
  * Outputs: image[3][H][W] per view (at 3 P_v), final_T[H][W] and
  * n_contrib[H][W] per view (at P_v): n_contrib is the index in the tile's
  * list where blending stopped (the list length if it did not).
- * frag_count (nullable): device u64 += sum over pixels of n_contrib, the
- * number of (pixel, splat) pairs both render kernels walk. */
+ * frag_count (nullable): device u64[4] of counters, accumulated (+=), taken
+ * by a slower counting variant of the kernel: [0] (pixel, splat) pairs walked
+ * (the sum of n_contrib, the pairs both render kernels evaluate), [1] of which
+ * unmasked, [2] unmasked splats blended, [3] masked splats at or above the
+ * alpha floor (the ones that receive dL/dM). */
 mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
                     const uint32_t *ranges, const mg_view *views, int32_t n_views,
                     const mg_raster_cfg *cfg, float *image, float *final_T,

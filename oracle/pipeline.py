@@ -32,7 +32,8 @@ class OracleConfig:
     tau: float = 1.0
     mask_mode: int = MASK_GUMBEL
     given_mask: np.ndarray | None = None
-    eps: float = 1e-3           # straddle band
+    eps: float = 1e-3           # straddle band of the alpha floor / power sign (relative)
+    eps_T: float = 1e-2         # straddle band of the termination test (relative)
 
 
 @dataclass
@@ -92,7 +93,7 @@ def forward(g, cams, cfg: OracleConfig):
         rgb[vis] = sp["rgb"].numpy()
         splats = render.SplatsF64(mean2d, conic, opac, rgb, M.astype(np.float64))
         out = render.render_tiled(splats, cam.width, cam.height, cfg.tile_w, cfg.tile_h,
-                                  svals, ranges, cfg.bg, True, cfg.eps)
+                                  svals, ranges, cfg.bg, True, cfg.eps, cfg.eps_T)
         views.append(OracleView(fp, keys, vals, offsets, K, skeys, svals, ranges, vis,
                                 splats, out,
                                 dict(mean2d=mean2d, conic=conic, opacity=opac, rgb=rgb,

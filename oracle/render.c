@@ -25,8 +25,10 @@
  * (true derivative: zero when clamped) to o_i, the conic and the 2D mean.
  * T_i is taken from a forward prefix recomputed per pixel, not by division.
  *
- * Straddles: a decision whose FP64 operand lies within a relative band eps
- * of its threshold is flagged per pixel (bit 1: alpha floor, bit 2:
+ * Straddles: a decision whose FP64 operand lies within a relative band (eps
+ * for the alpha floor and the power sign, eps_T for the termination test,
+ * whose operand T accumulates the rounding of every blended splat) of its
+ * threshold is flagged per pixel (bit 1: alpha floor, bit 2:
  * termination, bit 4: 0.99 clamp, bit 8: sign of power); an FP32 evaluation
  * may fall on the other side there.
  */
@@ -51,7 +53,8 @@ typedef struct {
 typedef struct {
     int width, height, tile_w, tile_h;
     double bg[3];
-    double eps;            /* straddle band (relative) */
+    double eps;            /* straddle band (relative) of the alpha floor and the power sign */
+    double eps_T;          /* straddle band (relative) of the termination test */
 } orc_frame;
 
 static void eval_fragment(const orc_splats *s, int g, double px, double py,
@@ -92,12 +95,12 @@ static void composite(const orc_splats *s, const orc_frame *f, const uint32_t *l
         if (masked) {
             double M = s->mask[g];
             testT = T * (1.0 - M * alpha);
-            if (near_rel(testT, T_MIN, f->eps)) fl |= 2;
+            if (near_rel(testT, T_MIN, f->eps_T)) fl |= 2;
             if (testT < T_MIN) { last = j; break; }
             for (int ch = 0; ch < 3; ++ch) C[ch] += ((M * alpha) * T) * s->rgb[3 * g + ch];
         } else {
             testT = T * (1.0 - alpha);
-            if (near_rel(testT, T_MIN, f->eps)) fl |= 2;
+            if (near_rel(testT, T_MIN, f->eps_T)) fl |= 2;
             if (testT < T_MIN) { last = j; break; }
             for (int ch = 0; ch < 3; ++ch) C[ch] += (alpha * T) * s->rgb[3 * g + ch];
         }

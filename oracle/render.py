@@ -35,7 +35,8 @@ class _Splats(C.Structure):
 
 class _Frame(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("tile_w", C.c_int),
-                ("tile_h", C.c_int), ("bg", C.c_double * 3), ("eps", C.c_double)]
+                ("tile_h", C.c_int), ("bg", C.c_double * 3), ("eps", C.c_double),
+                ("eps_T", C.c_double)]
 
 
 class _Grads(C.Structure):
@@ -86,14 +87,15 @@ class SplatsF64:
                          self.opacity.ctypes.data, self.rgb.ctypes.data, self.mask.ctypes.data)
 
 
-def _frame(width, height, tile_w, tile_h, bg, eps):
+def _frame(width, height, tile_w, tile_h, bg, eps, eps_T=None):
     return _Frame(int(width), int(height), int(tile_w), int(tile_h),
-                  (C.c_double * 3)(*[float(x) for x in bg]), float(eps))
+                  (C.c_double * 3)(*[float(x) for x in bg]), float(eps),
+                  float(10 * eps if eps_T is None else eps_T))
 
 
 def render_tiled(splats: SplatsF64, width, height, tile_w, tile_h, vals, ranges,
-                 bg=(0.0, 0.0, 0.0), masked=True, eps=1e-3):
-    f = _frame(width, height, tile_w, tile_h, bg, eps)
+                 bg=(0.0, 0.0, 0.0), masked=True, eps=1e-3, eps_T=None):
+    f = _frame(width, height, tile_w, tile_h, bg, eps, eps_T)
     vals = np.ascontiguousarray(vals, dtype=np.uint32)
     ranges = np.ascontiguousarray(ranges, dtype=np.uint32)
     img = np.zeros((3, height, width), np.float64)
@@ -107,8 +109,8 @@ def render_tiled(splats: SplatsF64, width, height, tile_w, tile_h, vals, ranges,
 
 
 def render_bruteforce(splats: SplatsF64, width, height, tile_w, tile_h, rect, depth_bits,
-                      bg=(0.0, 0.0, 0.0), masked=True, eps=1e-3):
-    f = _frame(width, height, tile_w, tile_h, bg, eps)
+                      bg=(0.0, 0.0, 0.0), masked=True, eps=1e-3, eps_T=None):
+    f = _frame(width, height, tile_w, tile_h, bg, eps, eps_T)
     rect = np.ascontiguousarray(rect, dtype=np.int32)
     depth_bits = np.ascontiguousarray(depth_bits, dtype=np.uint32)
     img = np.zeros((3, height, width), np.float64)

@@ -63,13 +63,17 @@ __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
     return ti;
 }
 
+// COUNT = true adds per-fragment counters (an untimed diagnostic variant):
+// [0] positions walked (sum of n_contrib), [1] unmasked positions walked,
+// [2] unmasked splats blended, [3] masked splats above the alpha floor.
+template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, float bg0, float bg1, float bg2,
                       float *__restrict__ image, float *__restrict__ final_T,
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count) {
     __shared__ float4 sA[kRenderThreads], sB[kRenderThreads], sC[kRenderThreads];
-    __shared__ unsigned long long s_frags;
+    __shared__ unsigned long long s_frags[4];
     const int64_t t = blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
@@ -77,7 +81,8 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     bool done = !ti.inside;
     uint32_t stop = end - start;
-    if (threadIdx.x == 0) s_frags = 0ull;
+    uint32_t c_unmasked = 0, c_blend = 0, c_masked = 0;
+    if (threadIdx.x < 4) s_frags[threadIdx.x] = 0ull;
 
     for (uint32_t b0 = start; b0 < end; b0 += kRenderThreads) {
         if (__syncthreads_count(done) == kRenderThreads) break;
@@ -94,7 +99,15 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
             int j = 0;
             for (; j < cnt; ++j) {
                 const float4 B = sB[j];
-                if (B.w == 0.0f) continue;          // masked: no colour, no attenuation
+                if (B.w == 0.0f) {                  // masked: no colour, no attenuation
+                    if (COUNT) {
+                        Frag f;
+                        frag_alpha(sA[j], B, fpx, fpy, f);
+                        c_masked += f.alpha >= kAlphaMin;
+                    }
+                    continue;
+                }
+                if (COUNT) ++c_unmasked;
                 Frag f;
                 frag_alpha(sA[j], B, fpx, fpy, f);
                 if (f.alpha < kAlphaMin) continue;
@@ -102,8 +115,10 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 if (testT < kTMin) {
                     done = true;
                     stop = (b0 - start) + j;
+                    if (COUNT) --c_unmasked;        // the stopping splat is not walked
                     break;
                 }
+                if (COUNT) ++c_blend;
                 const float4 c = sC[j];
                 const float w = f.alpha * T;
                 C0 = fmaf(w, c.x, C0);
@@ -113,15 +128,19 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
             }
         }
     }
-    if (frag_count != nullptr) {
-        // F = sum over pixels of the positions walked before blending stopped
-        unsigned long long s = ti.inside ? stop : 0u;
+    if (COUNT) {
+        unsigned long long c[4] = {ti.inside ? stop : 0u, c_unmasked, c_blend, c_masked};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_down_sync(0xffffffffu, c[k], o);
+        }
         __syncthreads();
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_frags, s);
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(&s_frags[k], c[k]);
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(frag_count, s_frags);
+        if (threadIdx.x < 4) atomicAdd(frag_count + threadIdx.x, s_frags[threadIdx.x]);
     }
     if (ti.inside) {
         const mg_camera &C = vt.cam[ti.v];
@@ -315,10 +334,15 @@ extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_v
     if (st != MG_OK) return st;
     const int64_t tiles = vt.tile_off[n_views];
     if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
-    render_forward_kernel<<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-        vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, cfg->bg[0],
-        cfg->bg[1], cfg->bg[2], image, final_T, n_contrib,
-        reinterpret_cast<unsigned long long *>(frag_count));
+    const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
+    if (frag_count != nullptr)
+        render_forward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T,
+            n_contrib, reinterpret_cast<unsigned long long *>(frag_count));
+    else
+        render_forward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T,
+            n_contrib, nullptr);
     return mg_host::launch_status();
 }
 

@@ -102,7 +102,7 @@ class Rasterizer:
         self.headroom = capacity_headroom
         self._buf = {}
         self.status = torch.zeros(2, dtype=torch.int64, device=self.device)   # mg_status_word
-        self.frag_count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.frag_count = torch.zeros(4, dtype=torch.int64, device=self.device)
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=self.device)
 
     # -- buffers -------------------------------------------------------------

@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 IMG_TOL = 2e-4
 GRAD_TOL = 1e-3
-EPS = 1e-3          # straddle band (relative), see the oracle's render
+EPS = 1e-4          # straddle band (relative), see the oracle's render
 
 
 @pytest.fixture(scope="module")
