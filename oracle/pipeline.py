@@ -33,7 +33,7 @@ class OracleConfig:
     mask_mode: int = MASK_GUMBEL
     given_mask: np.ndarray | None = None
     eps: float = 1e-3           # straddle band of the alpha floor / power sign (relative)
-    eps_T: float = 1e-2         # straddle band of the termination test (relative)
+    eps_T: float = 1e-3         # straddle band of the termination test (relative)
 
 
 @dataclass
