@@ -138,6 +138,9 @@ scan_kernel(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ o
 // --------------------------------------------------------------------------
 // key duplication
 // --------------------------------------------------------------------------
+// One thread per record writes small rectangles; rectangles of more than 32
+// tiles are written by the whole warp, one at a time, 32 tiles per step (the
+// near-camera splats of a scene cover thousands of tiles).
 __global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
                                  const int32_t *__restrict__ radius,
                                  const uint32_t *__restrict__ tiles,
@@ -145,28 +148,54 @@ __global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                  uint64_t capacity) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_records) return;
-    const uint32_t nt = tiles[r];
-    if (nt == 0) return;
-    const uint64_t off = offsets[r];
-    if (off + nt > capacity) return;
-    int v = 0;
-    while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= r) ++v;
-    const float4 a = *reinterpret_cast<const float4 *>(record + 12 * r);
-    const float depth = record[12 * r + 11];
-    int x0, x1, y0, y1;
-    if (!tile_rect(a.x, a.y, (float)radius[r], vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x0, x1,
-                   y0, y1))
-        return;
-    const uint64_t dbits = __float_as_uint(depth);
-    const uint64_t t0 = (uint64_t)vt.tile_off[v];
-    uint64_t k = off;
-    const uint64_t k_end = off + nt;
-    for (int ty = y0; ty <= y1; ++ty)
-        for (int tx = x0; tx <= x1 && k < k_end; ++tx, ++k) {
-            keys[k] = ((t0 + (uint64_t)ty * vt.gx[v] + tx) << 32) | dbits;
-            vals[k] = (uint32_t)r;
+    const int lane = threadIdx.x & 31;
+    bool valid = false;
+    uint64_t off = 0, dbits = 0, t0 = 0;
+    uint32_t nt = 0;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1, gx = 1;
+    if (r < n_records) {
+        nt = tiles[r];
+        off = offsets[r];
+        if (nt != 0 && off + nt <= capacity) {
+            int v = 0;
+            while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= r) ++v;
+            const float4 a = *reinterpret_cast<const float4 *>(record + 12 * r);
+            dbits = __float_as_uint(record[12 * r + 11]);
+            t0 = (uint64_t)vt.tile_off[v];
+            gx = vt.gx[v];
+            valid = tile_rect(a.x, a.y, (float)radius[r], vt.tile_w, vt.tile_h, gx, vt.gy[v], x0,
+                              x1, y0, y1);
         }
+    }
+    const bool big = valid && nt > 32u;
+    if (valid && !big) {
+        uint64_t k = off;
+        const uint64_t k_end = off + nt;
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1 && k < k_end; ++tx, ++k) {
+                keys[k] = ((t0 + (uint64_t)ty * gx + tx) << 32) | dbits;
+                vals[k] = (uint32_t)r;
+            }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, big);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint64_t o = __shfl_sync(0xffffffffu, off, src);
+        const uint64_t db = __shfl_sync(0xffffffffu, dbits, src);
+        const uint64_t tb = __shfl_sync(0xffffffffu, t0, src);
+        const uint32_t n = __shfl_sync(0xffffffffu, nt, src);
+        const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+        const int by0 = __shfl_sync(0xffffffffu, y0, src);
+        const int bgx = __shfl_sync(0xffffffffu, gx, src);
+        const uint32_t rr = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)r, src);
+        const uint32_t w = (uint32_t)(bx1 - bx0 + 1);
+        for (uint32_t k = lane; k < n; k += 32) {
+            const uint32_t ty = (uint32_t)by0 + k / w, tx = (uint32_t)bx0 + k % w;
+            keys[o + k] = ((tb + (uint64_t)ty * bgx + tx) << 32) | db;
+            vals[o + k] = rr;
+        }
+    }
 }
 
 // --------------------------------------------------------------------------

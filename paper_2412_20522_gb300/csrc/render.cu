@@ -3,13 +3,16 @@
 //
 // One CTA of 256 threads per tile, one thread per pixel.  The tile's
 // depth-sorted splats are staged through shared memory in batches of 256
-// (one 48-byte record gathered per thread), then every thread walks the batch.
+// (one 48-byte record gathered per thread, which also culls the splat against
+// the tile's eight warp strips), then every warp walks the splats that can
+// reach its strip.
 // The forward skips masked splats outright: with M_i = 0 they neither add
 // colour nor attenuate T (Eq. 3-4).  The backward walks the same lists back
 // to front from each pixel's stop index, recovers T_i = T_{i+1}/(1 - M_i
-// alpha_i), and reduces each splat's gradient over the warp with shuffles,
-// over the CTA in shared memory, then issues one vector atomic per splat and
-// tile.  Masked splats carry only dL/dM (one scalar reduction and atomic).
+// alpha_i), and reduces each splat's ten gradient sums over the warp with a
+// halving shuffle exchange, over the CTA with shared-memory atomics, then
+// issues three vector atomics per splat and tile.  Masked splats carry only
+// dL/dM (one scalar reduction and atomic).
 //
 // alpha is evaluated by the same explicitly rounded sequence in both kernels
 // so that the forward's and the backward's per-fragment decisions agree.
@@ -63,9 +66,65 @@ __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
     return ti;
 }
 
+// ---------------------------------------------------------------------------
+// Per-warp culling.  A warp's 32 pixels form a strip of the tile (2 rows of
+// 16 for 16x16 tiles).  When a batch is staged, the thread that loads splat j
+// tests the splat's alpha = 1/255 ellipse, enlarged by a margin, against each
+// strip with a separating-axis test (tile axes and the ellipse's axes; it
+// never separates shapes that overlap).  Every pixel whose FP32 alpha reaches
+// the floor lies inside the enlarged ellipse, so skipping the splat for a
+// strip it misses changes no result: both kernels still apply the per-pixel
+// alpha test, on the same set of splats.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t strip_mask(const float4 &A, const float4 &B, float x0, float y0,
+                                               int sw, int sh) {
+    const float o = B.z;
+    if (!(o >= kAlphaMin * 0.999f)) return 0u;      // alpha <= o never reaches the floor
+    // log2 of the floor relative to o, pushed outwards by 1e-3 (0.07 % in alpha)
+    const float e_thr = __log2f(kAlphaMin / o) - 1e-3f;
+    if (!(e_thr < 0.0f)) return 0xFFu;              // floor reached everywhere near the centre
+    const float r1 = sqrtf(e_thr / B.x) * 1.0001f + 0.02f;   // semi-axis along u
+    const float r2 = sqrtf(e_thr / B.y) * 1.0001f + 0.02f;   // semi-axis along u_perp
+    const float ux = A.z, uy = A.w;
+    const float aux = fabsf(ux), auy = fabsf(uy);
+    const float ex = sqrtf(r1 * r1 * ux * ux + r2 * r2 * uy * uy) + 0.02f;
+    const float ey = sqrtf(r1 * r1 * uy * uy + r2 * r2 * ux * ux) + 0.02f;
+    const float hw = 0.5f * (float)(sw - 1), hh = 0.5f * (float)(sh - 1);
+    const float cx = x0 + 0.5f * (float)sw;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int w = 0; w < kRenderThreads / 32; ++w) {
+        const float cy = y0 + (float)(w * sh) + 0.5f * (float)sh;
+        const float dx = cx - A.x, dy = cy - A.y;
+        const bool sep_x = fabsf(dx) > ex + hw;
+        const bool sep_y = fabsf(dy) > ey + hh;
+        const bool sep_u = fabsf(dx * ux + dy * uy) > r1 + hw * aux + hh * auy + 0.02f;
+        const bool sep_v = fabsf(dy * ux - dx * uy) > r2 + hw * auy + hh * aux + 0.02f;
+        if (!(sep_x || sep_y || sep_u || sep_v)) m |= 1u << w;
+    }
+    return m;
+}
+
+struct StripGeom {
+    float x0, y0;
+    int sw, sh;
+};
+
+__device__ __forceinline__ StripGeom strip_geom(const ViewTable &vt, int64_t t, const TileInfo &ti) {
+    StripGeom g;
+    const int64_t lt = t - vt.tile_off[ti.v];
+    const int gx = vt.gx[ti.v];
+    g.x0 = (float)((int)(lt % gx) * vt.tile_w);
+    g.y0 = (float)((int)(lt / gx) * vt.tile_h);
+    g.sw = vt.tile_w < 32 ? vt.tile_w : 32;
+    g.sh = 32 / g.sw;
+    return g;
+}
+
 // COUNT = true adds per-fragment counters (an untimed diagnostic variant):
 // [0] positions walked (sum of n_contrib), [1] unmasked positions walked,
 // [2] unmasked splats blended, [3] masked splats above the alpha floor.
+// Counters [1] and [3] count every walked position, culled or not.
 template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
@@ -73,11 +132,14 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                       float *__restrict__ image, float *__restrict__ final_T,
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count) {
     __shared__ float4 sA[kRenderThreads], sB[kRenderThreads], sC[kRenderThreads];
+    __shared__ uint8_t sM[kRenderThreads];
     __shared__ unsigned long long s_frags[4];
     const int64_t t = blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
+    const StripGeom sg = strip_geom(vt, t, ti);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
     const float fpx = (float)ti.px + 0.5f, fpy = (float)ti.py + 0.5f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     bool done = !ti.inside;
     uint32_t stop = end - start;
@@ -89,36 +151,56 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
         const uint32_t idx = b0 + threadIdx.x;
         if (idx < end) {
             const uint32_t r = vals[idx];
-            sA[threadIdx.x] = rec[3 * (int64_t)r];
-            sB[threadIdx.x] = rec[3 * (int64_t)r + 1];
+            const float4 A = rec[3 * (int64_t)r], B = rec[3 * (int64_t)r + 1];
+            sA[threadIdx.x] = A;
+            sB[threadIdx.x] = B;
             sC[threadIdx.x] = rec[3 * (int64_t)r + 2];
+            // masked splats neither colour nor attenuate: out of every forward list
+            sM[threadIdx.x] = (uint8_t)((B.w != 0.0f) ? strip_mask(A, B, sg.x0, sg.y0, sg.sw, sg.sh) : 0u);
         }
         __syncthreads();
         const int cnt = (int)min(end - b0, (uint32_t)kRenderThreads);
-        if (!done) {
+        if (COUNT && !done) {
+            // diagnostic counts over every position (culled or not) up to the stop
             int j = 0;
+            float Tc = T;
             for (; j < cnt; ++j) {
                 const float4 B = sB[j];
-                if (B.w == 0.0f) {                  // masked: no colour, no attenuation
-                    if (COUNT) {
-                        Frag f;
-                        frag_alpha(sA[j], B, fpx, fpy, f);
-                        c_masked += f.alpha >= kAlphaMin;
-                    }
-                    continue;
-                }
-                if (COUNT) ++c_unmasked;
                 Frag f;
                 frag_alpha(sA[j], B, fpx, fpy, f);
+                if (B.w == 0.0f) {
+                    c_masked += f.alpha >= kAlphaMin;
+                    continue;
+                }
+                ++c_unmasked;
+                if (f.alpha < kAlphaMin) continue;
+                const float tT = Tc * (1.0f - f.alpha);
+                if (tT < kTMin) {
+                    --c_unmasked;
+                    break;
+                }
+                ++c_blend;
+                Tc = tT;
+            }
+        }
+        if (__all_sync(0xffffffffu, done)) continue;
+        const int nchunks = (cnt + 31) >> 5;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int jj = (ch << 5) + lane;
+            unsigned word = __ballot_sync(0xffffffffu, jj < cnt && ((sM[jj] >> warp) & 1u));
+            while (word) {
+                const int j = (ch << 5) + __ffs(word) - 1;
+                word &= word - 1;
+                if (done) continue;
+                Frag f;
+                frag_alpha(sA[j], sB[j], fpx, fpy, f);
                 if (f.alpha < kAlphaMin) continue;
                 const float testT = T * (1.0f - f.alpha);
                 if (testT < kTMin) {
                     done = true;
                     stop = (b0 - start) + j;
-                    if (COUNT) --c_unmasked;        // the stopping splat is not walked
-                    break;
+                    continue;
                 }
-                if (COUNT) ++c_blend;
                 const float4 c = sC[j];
                 const float w = f.alpha * T;
                 C0 = fmaf(w, c.x, C0);
@@ -126,6 +208,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 C2 = fmaf(w, c.z, C2);
                 T = testT;
             }
+            if (__all_sync(0xffffffffu, done)) break;
         }
     }
     if (COUNT) {
@@ -160,6 +243,31 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Warp sum of 16 values by halving exchanges (16 shuffles instead of 80):
+// on return lane l holds the sum over the warp of v[l >> 1].
+__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane) {
+#pragma unroll
+    for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+        const bool up = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = up ? v[i] : v[i + half];
+            const float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Per splat and tile, the backward accumulates in shared memory
+//   S0 = sum dpow, S1 = sum dpow dx, S2 = sum dpow dy,
+//   S3 = sum dpow dx^2, S4 = sum dpow dx dy, S5 = sum dpow dy^2,
+//   S6..S8 = sum alpha T_i g (colour), S9 = sum dL/dM,
+// with dpow = dL/dalpha * alpha (dL/dpower of the unclamped alpha) and
+// d = pixel centre - mean; then dL/do = S0 / o, dL/dmean2d = Sigma^-1 (S1, S2),
+// dL/dconic = (-S3/2, -S4, -S5/2).
+constexpr int kAcc = 10;
+
 __global__ void __launch_bounds__(kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
@@ -168,13 +276,15 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        float *__restrict__ grad2d) {
     __shared__ float4 sA[kRenderThreads], sB[kRenderThreads], sC[kRenderThreads];
     __shared__ uint32_t sR[kRenderThreads];
-    __shared__ float sG[kRenderThreads][10];
+    __shared__ uint8_t sM[kRenderThreads];
+    __shared__ float sG[kRenderThreads][kAcc];
     __shared__ uint32_t s_maxstop;
     const int64_t t = blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
+    const StripGeom sg = strip_geom(vt, t, ti);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
     const float fpx = (float)ti.px + 0.5f, fpy = (float)ti.py + 0.5f;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
     uint32_t stop = 0;
@@ -197,6 +307,9 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     const uint32_t maxstop = min(s_maxstop, end - start);
     if (maxstop == 0) return;
     const int nb = (int)((maxstop + kRenderThreads - 1) / kRenderThreads);
+    uint32_t wstop = stop;                                     // warp's largest stop
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wstop = max(wstop, __shfl_xor_sync(0xffffffffu, wstop, o));
 
     for (int bi = nb - 1; bi >= 0; --bi) {
         const uint32_t pos0 = (uint32_t)bi * kRenderThreads;
@@ -204,90 +317,98 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             const uint32_t r = vals[start + pos0 + threadIdx.x];
+            const float4 A = rec[3 * (int64_t)r], B = rec[3 * (int64_t)r + 1];
             sR[threadIdx.x] = r;
-            sA[threadIdx.x] = rec[3 * (int64_t)r];
-            sB[threadIdx.x] = rec[3 * (int64_t)r + 1];
+            sA[threadIdx.x] = A;
+            sB[threadIdx.x] = B;
             sC[threadIdx.x] = rec[3 * (int64_t)r + 2];
+            sM[threadIdx.x] = (uint8_t)strip_mask(A, B, sg.x0, sg.y0, sg.sw, sg.sh);
         }
 #pragma unroll
-        for (int k = 0; k < 10; ++k) sG[threadIdx.x][k] = 0.0f;
+        for (int k = 0; k < kAcc; ++k) sG[threadIdx.x][k] = 0.0f;
         __syncthreads();
 
-        for (int j = cnt - 1; j >= 0; --j) {
-            const float4 B = sB[j];
-            const bool masked = B.w == 0.0f;
-            float dM = 0.0f, dmx = 0.0f, dmy = 0.0f, dca = 0.0f, dcb = 0.0f, dcc = 0.0f,
-                  dop = 0.0f, dr = 0.0f, dg = 0.0f, db = 0.0f;
-            bool contrib = false;
-            if (pos0 + j < stop) {
-                const float4 A = sA[j];
-                Frag f;
-                frag_alpha(A, B, fpx, fpy, f);
-                if (f.alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float4 c = sC[j];
-                    const float ma = masked ? 0.0f : f.alpha;
-                    const float Tj = T / (1.0f - ma);
-                    const float gcb = g0 * (c.x - b0c) + g1 * (c.y - b1c) + g2 * (c.z - b2c);
-                    dM = f.alpha * Tj * gcb;                   // Eq. 6 + Appendix A
-                    if (!masked) {
-                        const float wt = f.alpha * Tj;
-                        dr = wt * g0;
-                        dg = wt * g1;
-                        db = wt * g2;
-                        b0c = fmaf(f.alpha, c.x - b0c, b0c);
-                        b1c = fmaf(f.alpha, c.y - b1c, b1c);
-                        b2c = fmaf(f.alpha, c.z - b2c, b2c);
-                        T = Tj;
-                        if (f.araw < kAlphaMax) {
-                            const float dA = Tj * gcb;       // dL/dalpha (M = 1)
-                            dop = dA * f.G;
-                            const float dpow = dA * f.alpha;
-                            dca = -0.5f * dpow * f.dx * f.dx;
-                            dcb = -dpow * f.dx * f.dy;
-                            dcc = -0.5f * dpow * f.dy * f.dy;
-                            // Sigma^-1 d in eigen form: w_k = -2 h_k / log2(e)
-                            const float q1 = (-2.0f / kLog2e) * B.x * f.p1;
-                            const float q2 = (-2.0f / kLog2e) * B.y * f.p2;
-                            dmx = dpow * (q1 * A.z - q2 * A.w);
-                            dmy = dpow * (q1 * A.w + q2 * A.z);
+        if (pos0 < wstop) {
+            const int nchunks = (cnt + 31) >> 5;
+            for (int ch = nchunks - 1; ch >= 0; --ch) {
+                const int jj = (ch << 5) + lane;
+                unsigned word = __ballot_sync(0xffffffffu, jj < cnt && ((sM[jj] >> warp) & 1u));
+                while (word) {
+                    const int hb = 31 - __clz(word);
+                    word &= ~(1u << hb);
+                    const int j = (ch << 5) + hb;
+                    const float4 B = sB[j];
+                    const bool masked = B.w == 0.0f;
+                    float v[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] = 0.0f;
+                    bool contrib = false;
+                    if (pos0 + j < stop) {
+                        const float4 A = sA[j];
+                        Frag f;
+                        frag_alpha(A, B, fpx, fpy, f);
+                        if (f.alpha >= kAlphaMin) {
+                            contrib = true;
+                            const float4 c = sC[j];
+                            const float ma = masked ? 0.0f : f.alpha;
+                            const float Tj = __fdividef(T, 1.0f - ma);
+                            const float gcb = g0 * (c.x - b0c) + g1 * (c.y - b1c) + g2 * (c.z - b2c);
+                            v[9] = f.alpha * Tj * gcb;             // Eq. 6 + Appendix A
+                            if (!masked) {
+                                const float wt = f.alpha * Tj;
+                                v[6] = wt * g0;
+                                v[7] = wt * g1;
+                                v[8] = wt * g2;
+                                b0c = fmaf(f.alpha, c.x - b0c, b0c);
+                                b1c = fmaf(f.alpha, c.y - b1c, b1c);
+                                b2c = fmaf(f.alpha, c.z - b2c, b2c);
+                                T = Tj;
+                                if (f.araw < kAlphaMax) {
+                                    const float dpow = Tj * gcb * f.alpha;   // dL/dalpha * alpha
+                                    v[0] = dpow;
+                                    v[1] = dpow * f.dx;
+                                    v[2] = dpow * f.dy;
+                                    v[3] = v[1] * f.dx;
+                                    v[4] = v[1] * f.dy;
+                                    v[5] = v[2] * f.dy;
+                                }
+                            }
                         }
                     }
-                }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                if (masked) {
-                    dM = warp_sum(dM);
-                    if (lane == 0) atomicAdd(&sG[j][9], dM);
-                } else {
-                    dmx = warp_sum(dmx); dmy = warp_sum(dmy);
-                    dca = warp_sum(dca); dcb = warp_sum(dcb); dcc = warp_sum(dcc);
-                    dop = warp_sum(dop);
-                    dr = warp_sum(dr); dg = warp_sum(dg); db = warp_sum(db);
-                    dM = warp_sum(dM);
-                    if (lane == 0) {
-                        atomicAdd(&sG[j][0], dmx); atomicAdd(&sG[j][1], dmy);
-                        atomicAdd(&sG[j][2], dca); atomicAdd(&sG[j][3], dcb);
-                        atomicAdd(&sG[j][4], dcc); atomicAdd(&sG[j][5], dop);
-                        atomicAdd(&sG[j][6], dr); atomicAdd(&sG[j][7], dg);
-                        atomicAdd(&sG[j][8], db); atomicAdd(&sG[j][9], dM);
+                    if (__any_sync(0xffffffffu, contrib)) {
+                        if (masked) {
+                            const float dm = warp_sum(v[9]);
+                            if (lane == 0) atomicAdd(&sG[j][9], dm);
+                        } else {
+                            const float r = warp_transpose_sum16(v, lane);
+                            if ((lane & 1) == 0 && (lane >> 1) < kAcc) atomicAdd(&sG[j][lane >> 1], r);
+                        }
                     }
                 }
             }
         }
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
-            const float *s = sG[threadIdx.x];
+            const float *S = sG[threadIdx.x];
             float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[threadIdx.x];
-            if (sB[threadIdx.x].w == 0.0f) {
-                if (s[9] != 0.0f) atomicAdd(&G4[2].y, s[9]);
+            const float4 B = sB[threadIdx.x];
+            if (B.w == 0.0f) {
+                if (S[9] != 0.0f) atomicAdd(&G4[2].y, S[9]);
             } else {
-                if (s[0] != 0.0f || s[1] != 0.0f || s[2] != 0.0f || s[3] != 0.0f)
-                    atomicAdd(&G4[0], make_float4(s[0], s[1], s[2], s[3]));
-                if (s[4] != 0.0f || s[5] != 0.0f || s[6] != 0.0f || s[7] != 0.0f)
-                    atomicAdd(&G4[1], make_float4(s[4], s[5], s[6], s[7]));
-                if (s[8] != 0.0f || s[9] != 0.0f)
-                    atomicAdd(reinterpret_cast<float2 *>(&G4[2]), make_float2(s[8], s[9]));
+                const float4 A = sA[threadIdx.x];
+                // Sigma^-1 in eigen form: w_k = -2 h_k / log2(e)
+                const float w1 = (-2.0f / kLog2e) * B.x, w2 = (-2.0f / kLog2e) * B.y;
+                const float q00 = w1 * A.z * A.z + w2 * A.w * A.w;
+                const float q01 = (w1 - w2) * A.z * A.w;
+                const float q11 = w1 * A.w * A.w + w2 * A.z * A.z;
+                const float dmx = q00 * S[1] + q01 * S[2];
+                const float dmy = q01 * S[1] + q11 * S[2];
+                if (dmx != 0.0f || dmy != 0.0f || S[3] != 0.0f || S[4] != 0.0f)
+                    atomicAdd(&G4[0], make_float4(dmx, dmy, -0.5f * S[3], -S[4]));
+                if (S[5] != 0.0f || S[0] != 0.0f || S[6] != 0.0f || S[7] != 0.0f)
+                    atomicAdd(&G4[1], make_float4(-0.5f * S[5], S[0] / B.z, S[6], S[7]));
+                if (S[8] != 0.0f || S[9] != 0.0f)
+                    atomicAdd(reinterpret_cast<float2 *>(&G4[2]), make_float2(S[8], S[9]));
             }
         }
     }
