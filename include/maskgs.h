@@ -194,6 +194,24 @@ mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
                  mg_stream_t stream);
 size_t mg_bin_workspace_bytes(int64_t n_records);
 
+/* The same as mg_bin, for callers that cannot allocate device memory (a
+ * plugin whose host application owns every allocation, or code running where
+ * cudaMalloc is not allowed): no workspace argument.  The paper has no
+ * counterpart; this is a deployment convenience.
+ * Its scratch is one file-scope device array inside the library, sized for at
+ * most 2^24 records (sum of gaussian_count over the views); more records
+ * return MG_ERR_INVALID_ARG.  The array (about 64 KB) is held on every GPU
+ * that loads the library until the process exits.  The first call on each
+ * device looks up the array's device address (with that device current) and
+ * caches it; make that first call before any stream capture.  Every call
+ * shares the one array, so calls that overlap on the GPU (other streams, other
+ * threads) race: serialise them.  Nothing is allocated: no cudaMalloc, no
+ * cudaFree. */
+mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views, int32_t n_views,
+                         const mg_raster_cfg *cfg, uint32_t *offsets, uint64_t *keys,
+                         uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
+                         mg_status_word *d_status, mg_stream_t stream);
+
 /* ---- 3. sort + tile ranges (Sec. 3.1) -------------------------------------- */
 /* Stable LSD radix sort (8-bit digits, single-pass "onesweep" passes with
  * decoupled look-back) of the first *d_num_instances (key, value) pairs by

@@ -19,7 +19,7 @@ MG_MAX_VIEWS = 64
 MG_RECORD_FLOATS = 12
 MG_GRAD2D_FLOATS = 12
 
-EXPORTED = ("mg_preprocess", "mg_bin", "mg_bin_workspace_bytes", "mg_sort",
+EXPORTED = ("mg_preprocess", "mg_bin", "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
             "mg_sort_workspace_bytes", "mg_key_bits", "mg_total_tiles", "mg_render",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_read_status", "mg_status_string", "mg_version")
@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
                                _P(mg_splats), vp, vp]),
         "mg_bin": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp, vp, vp,
                         C.c_uint64, vp, vp, C.c_size_t, vp, vp]),
+        "mg_bin_noalloc": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp,
+                                vp, vp, C.c_uint64, vp, vp, vp]),
         "mg_bin_workspace_bytes": (C.c_size_t, [C.c_int64]),
         "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, vp, C.c_int64, vp,
                          C.c_size_t, _P(C.c_int32), vp, vp]),
@@ -153,6 +155,15 @@ def mg_bin(splats, views, n_views, cfg, offsets, keys, vals, capacity, d_num_ins
     _check("mg_bin", load().mg_bin(C.byref(splats), views, n_views, C.byref(cfg), ptr(offsets),
                                    ptr(keys), ptr(vals), capacity, ptr(d_num_instances),
                                    ptr(workspace), workspace_bytes, ptr(d_status), stream))
+
+
+def mg_bin_noalloc(splats, views, n_views, cfg, offsets, keys, vals, capacity, d_num_instances,
+                   d_status, stream):
+    """mg_bin for callers that cannot allocate: its scratch is a fixed array
+    inside the library (at most 2^24 records; concurrent calls race)."""
+    _check("mg_bin_noalloc", load().mg_bin_noalloc(C.byref(splats), views, n_views, C.byref(cfg),
+                                                   ptr(offsets), ptr(keys), ptr(vals), capacity,
+                                                   ptr(d_num_instances), ptr(d_status), stream))
 
 
 def mg_bin_workspace_bytes(n_records) -> int:

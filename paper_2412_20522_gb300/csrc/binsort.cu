@@ -482,3 +482,89 @@ extern "C" mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     ranges_kernel<<<sms * 4, 256, 0, s>>>(kin, d_num_instances, capacity, ranges, n_tiles_total);
     return mg_host::launch_status();
 }
+
+// --------------------------------------------------------------------------
+// mg_bin_noalloc: mg_bin without a caller-provided workspace.
+//
+// For callers that cannot allocate device memory themselves, for example a
+// plugin whose host application owns every allocation, or code that runs
+// where cudaMalloc is not permitted.  The scan's scratch (partition counter
+// and look-back words) lives in one file-scope device array instead, sized
+// for at most kNoAllocMaxRecords splat records; every GPU that loads the
+// library holds it until the process exits.  No allocation happens here.
+// --------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNoAllocMaxRecords = int64_t(1) << 24;
+constexpr int64_t kNoAllocParts = (kNoAllocMaxRecords + mg::kScanPart - 1) / mg::kScanPart + 1;
+constexpr size_t kNoAllocScratchBytes = sizeof(mg::ScanWS) + sizeof(uint64_t) * kNoAllocParts;
+constexpr int kNoAllocMaxDevices = 256;
+
+static __device__ __align__(256) unsigned char g_bin_scratch[kNoAllocScratchBytes];
+
+std::mutex g_bin_scratch_mutex;
+void *g_bin_scratch_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_bin_scratch on the current device.  In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+mg_status bin_scratch_address(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MG_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return MG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_bin_scratch_mutex);
+    if (g_bin_scratch_addr[dev] == nullptr) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess || p == nullptr)
+            return MG_ERR_CUDA;
+        g_bin_scratch_addr[dev] = p;
+    }
+    *out = g_bin_scratch_addr[dev];
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views,
+                                    int32_t n_views, const mg_raster_cfg *cfg, uint32_t *offsets,
+                                    uint64_t *keys, uint32_t *vals, uint64_t capacity,
+                                    uint64_t *d_num_instances, mg_status_word *d_status,
+                                    mg_stream_t stream) {
+    if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
+        !offsets || !d_num_instances)
+        return MG_ERR_INVALID_ARG;
+    if (capacity > 0 && (!keys || !vals)) return MG_ERR_INVALID_ARG;
+    if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    const int64_t R = vt.rec_off[n_views];
+    if (R > kNoAllocMaxRecords) return MG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats->tiles_touched) & 15u) != 0) return MG_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    st = bin_scratch_address(&scratch);
+    if (st != MG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t parts = (R + kScanPart - 1) / kScanPart;
+    ScanWS *ws = reinterpret_cast<ScanWS *>(scratch);
+    // the array keeps the previous call's contents: clear the counter and the
+    // look-back words this call uses
+    if (cudaMemsetAsync(ws, 0, sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(parts + 1), s) !=
+        cudaSuccess)
+        return MG_ERR_CUDA;
+    if (R == 0) {
+        if (cudaMemsetAsync(d_num_instances, 0, sizeof(uint64_t), s) != cudaSuccess)
+            return MG_ERR_CUDA;
+        return MG_OK;
+    }
+    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, R, offsets,
+                                                         d_num_instances, capacity, ws, parts,
+                                                         d_status);
+    if (capacity > 0)
+        duplicate_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(
+            vt, splats->record, splats->radius, splats->tiles_touched, offsets, R, keys, vals,
+            capacity);
+    return mg_host::launch_status();
+}
