@@ -155,7 +155,7 @@ def run_ours(args):
         loss, dimg = rast.l1_loss_grad(img, tgt)
         if ev is not None:
             ev["loss"][1].record(stream)
-        rast.backward(dimg, grads, stage_events=ev)
+        rast.backward(dimg, grads, stage_events=ev, count_iterations=count)
         return loss
 
     for _ in range(max(args.warmup, 3)):
@@ -195,6 +195,7 @@ def run_ours(args):
     step(count=True)
     torch.cuda.synchronize()
     counts = rast.frag_count.cpu().tolist()
+    bwd_counts = rast.bwd_count.cpu().tolist()
     flops_fwd, flops_bwd = render_flops(counts)
     K = int(rast.num_instances.item())
     so = rast.splat_outputs()
@@ -269,6 +270,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}", "instances_K": K, "fragments": {"walked": counts[0], "walked_unmasked": counts[1],
                                                   "blended": counts[2], "masked_above_floor": counts[3]},
                    "render_gflop": {"fwd": flops_fwd / 1e9, "bwd": flops_bwd / 1e9},
+                   "bwd_iterations": dict(zip(("list", "masked", "contrib_unmasked",
+                                               "contrib_masked", "contrib_lanes", "batches"),
+                                              bwd_counts)),
                    "visible": visible, "mask_on_fraction": mask_on},
         "stage_ms": stage_ms,
         "roofline": roof,

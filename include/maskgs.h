@@ -269,12 +269,17 @@ mg_status mg_l1_loss_grad(const float *image, const float *target, const mg_view
  *   dL/dalpha_i = M_i T_i g.(c_i - b_{i+1})       (0 for a masked splat)
  *   dL/dc_i     = M_i alpha_i T_i g,   g = dL/dC,
  * then through the 0.99 clamp to opacity, conic and 2D mean.
- * grad2d[R][12] is ZEROED by this call and then accumulated. */
+ * grad2d[R][12] is ZEROED by this call and then accumulated.
+ * counters (nullable): device u64[6] of profiling counters, accumulated, taken
+ * by a slower counting variant: [0] (warp, splat) iterations after culling,
+ * [1] of which masked, [2] unmasked with at least one contributing pixel,
+ * [3] masked with one, [4] contributing pixels summed over [2], [5] batches. */
 mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
                              const uint32_t *ranges, const mg_view *views,
                              int32_t n_views, const mg_raster_cfg *cfg,
                              const float *final_T, const uint32_t *n_contrib,
-                             const float *dL_dimage, float *grad2d, mg_stream_t stream);
+                             const float *dL_dimage, float *grad2d, uint64_t *counters,
+                             mg_stream_t stream);
 
 /* ---- 7. preprocess backward ------------------------------------------------- */
 /* Chain rule from grad2d through the 2D covariance (P = J W R S), the

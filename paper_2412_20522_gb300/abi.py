@@ -107,7 +107,7 @@ def load(build_if_missing: bool = True):
                            vp, vp, vp, vp, vp]),
         "mg_l1_loss_grad": (st, [vp, vp, _P(mg_view), C.c_int32, vp, vp, vp]),
         "mg_render_backward": (st, [_P(mg_splats), vp, vp, _P(mg_view), C.c_int32,
-                                    _P(mg_raster_cfg), vp, vp, vp, vp, vp]),
+                                    _P(mg_raster_cfg), vp, vp, vp, vp, vp, vp]),
         "mg_preprocess_backward": (st, [_P(mg_gaussians), _P(mg_view), C.c_int32,
                                         _P(mg_raster_cfg), _P(mg_splats), vp,
                                         _P(mg_param_grads), vp]),
@@ -205,10 +205,10 @@ def mg_l1_loss_grad(image, target, views, n_views, dL_dimage, loss, stream):
 
 
 def mg_render_backward(splats, sorted_vals, ranges, views, n_views, cfg, final_T, n_contrib,
-                       dL_dimage, grad2d, stream):
+                       dL_dimage, grad2d, counters, stream):
     _check("mg_render_backward", load().mg_render_backward(
         C.byref(splats), ptr(sorted_vals), ptr(ranges), views, n_views, C.byref(cfg),
-        ptr(final_T), ptr(n_contrib), ptr(dL_dimage), ptr(grad2d), stream))
+        ptr(final_T), ptr(n_contrib), ptr(dL_dimage), ptr(grad2d), ptr(counters), stream))
 
 
 def mg_preprocess_backward(g, views, n_views, cfg, splats, grad2d, out, stream):

@@ -268,12 +268,18 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane) {
 // dL/dconic = (-S3/2, -S4, -S5/2).
 constexpr int kAcc = 10;
 
+// COUNT = true accumulates profiling counters (an untimed variant):
+// [0] (warp, splat) list iterations, [1] of which masked, [2] unmasked with a
+// contributing lane, [3] masked with a contributing lane, [4] contributing
+// lanes over [2], [5] staged batches.
+template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                        float bg0, float bg1, float bg2, const float *__restrict__ final_T,
                        const uint32_t *__restrict__ n_contrib, const float *__restrict__ dL_dimage,
-                       float *__restrict__ grad2d) {
+                       float *__restrict__ grad2d, unsigned long long *counters) {
+    unsigned long long cnt_it = 0, cnt_m = 0, cnt_cu = 0, cnt_cm = 0, cnt_lanes = 0, cnt_b = 0;
     __shared__ float4 sA[kRenderThreads], sB[kRenderThreads], sC[kRenderThreads];
     __shared__ uint32_t sR[kRenderThreads];
     __shared__ uint8_t sM[kRenderThreads];
@@ -306,6 +312,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     __syncthreads();
     const uint32_t maxstop = min(s_maxstop, end - start);
     if (maxstop == 0) return;
+    if (COUNT) cnt_b = (maxstop + kRenderThreads - 1) / kRenderThreads;
     const int nb = (int)((maxstop + kRenderThreads - 1) / kRenderThreads);
     uint32_t wstop = stop;                                     // warp's largest stop
 #pragma unroll
@@ -375,6 +382,14 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                             }
                         }
                     }
+                    if (COUNT) {
+                        const unsigned cb = __ballot_sync(0xffffffffu, contrib);
+                        ++cnt_it;
+                        cnt_m += masked;
+                        cnt_cu += (!masked && cb);
+                        cnt_cm += (masked && cb);
+                        cnt_lanes += masked ? 0 : __popc(cb);
+                    }
                     if (__any_sync(0xffffffffu, contrib)) {
                         if (masked) {
                             const float dm = warp_sum(v[9]);
@@ -411,6 +426,14 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     atomicAdd(reinterpret_cast<float2 *>(&G4[2]), make_float2(S[8], S[9]));
             }
         }
+    }
+    if (COUNT && lane == 0) {   // per-warp counts (iteration counts are warp-uniform)
+        atomicAdd(counters + 0, cnt_it);
+        atomicAdd(counters + 1, cnt_m);
+        atomicAdd(counters + 2, cnt_cu);
+        atomicAdd(counters + 3, cnt_cm);
+        atomicAdd(counters + 4, cnt_lanes);
+        if (warp == 0) atomicAdd(counters + 5, cnt_b);
     }
 }
 
@@ -472,7 +495,7 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
                                         int32_t n_views, const mg_raster_cfg *cfg,
                                         const float *final_T, const uint32_t *n_contrib,
                                         const float *dL_dimage, float *grad2d,
-                                        mg_stream_t stream) {
+                                        uint64_t *counters, mg_stream_t stream) {
     if (!splats || !splats->record || !sorted_vals || !ranges || !final_T || !n_contrib ||
         !dL_dimage || !grad2d)
         return MG_ERR_INVALID_ARG;
@@ -488,9 +511,15 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
     if (R > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * MG_GRAD2D_FLOATS * (size_t)R, s) !=
                      cudaSuccess)
         return MG_ERR_CUDA;
-    render_backward_kernel<<<(unsigned)tiles, kRenderThreads, 0, s>>>(
-        vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, cfg->bg[0],
-        cfg->bg[1], cfg->bg[2], final_T, n_contrib, dL_dimage, grad2d);
+    const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
+    if (counters != nullptr)
+        render_backward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
+            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T, n_contrib,
+            dL_dimage, grad2d, reinterpret_cast<unsigned long long *>(counters));
+    else
+        render_backward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
+            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T, n_contrib,
+            dL_dimage, grad2d, nullptr);
     return mg_host::launch_status();
 }
 

@@ -103,6 +103,7 @@ class Rasterizer:
         self._buf = {}
         self.status = torch.zeros(2, dtype=torch.int64, device=self.device)   # mg_status_word
         self.frag_count = torch.zeros(4, dtype=torch.int64, device=self.device)
+        self.bwd_count = torch.zeros(6, dtype=torch.int64, device=self.device)
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=self.device)
 
     # -- buffers -------------------------------------------------------------
@@ -226,7 +227,8 @@ class Rasterizer:
         return loss, dimg
 
     # -- backward -------------------------------------------------------------
-    def backward(self, dL_dimage, out: dict | None = None, stage_events=None):
+    def backward(self, dL_dimage, out: dict | None = None, stage_events=None,
+                 count_iterations=False):
         """Gradients of <dL_dimage, image> w.r.t. every parameter (overwritten
         into ``out`` when given)."""
         s = self._state
@@ -234,9 +236,11 @@ class Rasterizer:
         ev = _Events(stage_events)
         grad2d = self._get("grad2d", s["R"] * abi.MG_GRAD2D_FLOATS, torch.float32)
         ev.begin("render_bwd")
+        if count_iterations:
+            self.bwd_count.zero_()
         abi.mg_render_backward(s["splats"], s["sorted_vals"], s["ranges"], s["views"], s["V"],
                                s["cfg"], self._buf["final_T"], self._buf["n_contrib"], dL_dimage,
-                               grad2d, stream)
+                               grad2d, self.bwd_count if count_iterations else None, stream)
         if out is None:
             out = {k: torch.empty_like(s["params"][k]) for k in PARAM_NAMES}
         ev.end("render_bwd")
