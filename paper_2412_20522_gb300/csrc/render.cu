@@ -1,18 +1,19 @@
 // Masked rasterisation, forward (Eq. 3-4) and backward (Eq. 6, Appendix A),
 // and the L1 render loss.
 //
-// One CTA of 256 threads per tile, one thread per pixel.  The tile's
+// One CTA of 128 threads per tile, two pixels per thread: warp w owns a
+// compact block of 64 pixels (4 rows of a 16x16 tile).  The tile's
 // depth-sorted splats are staged through shared memory in batches of 256
-// (one 48-byte record gathered per thread, which also culls the splat against
-// the tile's eight warp strips), then every warp walks the splats that can
-// reach its strip.
-// The forward skips masked splats outright: with M_i = 0 they neither add
-// colour nor attenuate T (Eq. 3-4).  The backward walks the same lists back
-// to front from each pixel's stop index, recovers T_i = T_{i+1}/(1 - M_i
-// alpha_i), and reduces each splat's ten gradient sums over the warp with a
-// halving shuffle exchange, over the CTA with shared-memory atomics, then
-// issues three vector atomics per splat and tile.  Masked splats carry only
-// dL/dM (one scalar reduction and atomic).
+// (each thread gathers two 48-byte records and culls each splat against the
+// four warp blocks), then every warp walks only the splats that can reach its
+// block, applying each to both of a thread's pixels.  The forward skips
+// masked splats outright: with M_i = 0 they neither add colour nor attenuate
+// T (Eq. 3-4).  The backward walks the same lists back to front from each
+// pixel's stop index, recovers T_i = T_{i+1}/(1 - M_i alpha_i), sums each
+// splat's ten gradient terms over a thread's two pixels, then over the warp
+// with a halving shuffle exchange, over the CTA with shared-memory atomics,
+// and issues three vector atomics per splat and tile.  Masked splats carry
+// only dL/dM (one scalar reduction and atomic).
 //
 // alpha is evaluated by the same explicitly rounded sequence in both kernels
 // so that the forward's and the backward's per-fragment decisions agree.
@@ -20,7 +21,10 @@
 
 namespace mg {
 
-constexpr int kRenderThreads = 256;
+constexpr int kRenderThreads = 128;              // threads per CTA (one tile)
+constexpr int kRenderWarps = kRenderThreads / 32;
+constexpr int kBatch = 256;                      // splats staged per batch
+constexpr int kPix = 2;                          // pixels per thread
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -46,10 +50,16 @@ __device__ __forceinline__ void frag_alpha(const float4 &A, const float4 &B, flo
     f.alpha = fminf(kAlphaMax, f.araw);
 }
 
+// Tile of the CTA and the two pixels of this thread.  Warp w owns rows
+// [w * 64/tw, (w+1) * 64/tw) of the tile; a lane's pixels are (l % tw,
+// l / tw) and the same column 32/tw rows further down, within that block.
 struct TileInfo {
-    int v, px, py;
-    bool inside;
-    int64_t pix;     // pixel index within the view
+    int v;
+    int x0, y0;          // tile origin (pixels)
+    int bh;              // rows per warp block (64 / tile_w)
+    int px[kPix], py[kPix];
+    bool inside[kPix];
+    int64_t pix[kPix];   // pixel index within the view
 };
 
 __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
@@ -57,44 +67,50 @@ __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
     ti.v = view_of_tile(vt, t);
     const int64_t lt = t - vt.tile_off[ti.v];
     const int gx = vt.gx[ti.v];
-    const int tx = (int)(lt % gx), ty = (int)(lt / gx);
-    ti.px = tx * vt.tile_w + (threadIdx.x & (vt.tile_w - 1));
-    ti.py = ty * vt.tile_h + (threadIdx.x >> vt.log2_tw);
+    ti.x0 = (int)(lt % gx) * vt.tile_w;
+    ti.y0 = (int)(lt / gx) * vt.tile_h;
+    const int tw = vt.tile_w;
+    ti.bh = (32 * kPix) / tw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const mg_camera &C = vt.cam[ti.v];
-    ti.inside = ti.px < C.width && ti.py < C.height;
-    ti.pix = (int64_t)ti.py * C.width + ti.px;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        ti.px[k] = ti.x0 + (lane & (tw - 1));
+        ti.py[k] = ti.y0 + warp * ti.bh + (lane >> vt.log2_tw) + k * (32 / tw);
+        ti.inside[k] = ti.px[k] < C.width && ti.py[k] < C.height;
+        ti.pix[k] = (int64_t)ti.py[k] * C.width + ti.px[k];
+    }
     return ti;
 }
 
 // ---------------------------------------------------------------------------
-// Per-warp culling.  A warp's 32 pixels form a strip of the tile (2 rows of
-// 16 for 16x16 tiles).  When a batch is staged, the thread that loads splat j
+// Per-warp culling.  When a batch is staged, the thread that loads splat j
 // tests the splat's alpha = 1/255 ellipse, enlarged by a margin, against each
-// strip with a separating-axis test (tile axes and the ellipse's axes; it
-// never separates shapes that overlap).  Every pixel whose FP32 alpha reaches
-// the floor lies inside the enlarged ellipse, so skipping the splat for a
-// strip it misses changes no result: both kernels still apply the per-pixel
-// alpha test, on the same set of splats.
+// warp's pixel block with a separating-axis test (tile axes and the ellipse's
+// axes; it never separates shapes that overlap).  Every pixel whose FP32
+// alpha reaches the floor lies inside the enlarged ellipse, so skipping the
+// splat for a block it misses changes no result: both kernels still apply the
+// per-pixel alpha test, on the same set of splats.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t strip_mask(const float4 &A, const float4 &B, float x0, float y0,
-                                               int sw, int sh) {
+__device__ __forceinline__ uint32_t block_mask(const float4 &A, const float4 &B, float x0,
+                                               float y0, int bw, int bh) {
     const float o = B.z;
     if (!(o >= kAlphaMin * 0.999f)) return 0u;      // alpha <= o never reaches the floor
     // log2 of the floor relative to o, pushed outwards by 1e-3 (0.07 % in alpha)
     const float e_thr = __log2f(kAlphaMin / o) - 1e-3f;
-    if (!(e_thr < 0.0f)) return 0xFFu;              // floor reached everywhere near the centre
+    if (!(e_thr < 0.0f)) return (1u << kRenderWarps) - 1u;
     const float r1 = sqrtf(e_thr / B.x) * 1.0001f + 0.02f;   // semi-axis along u
     const float r2 = sqrtf(e_thr / B.y) * 1.0001f + 0.02f;   // semi-axis along u_perp
     const float ux = A.z, uy = A.w;
     const float aux = fabsf(ux), auy = fabsf(uy);
     const float ex = sqrtf(r1 * r1 * ux * ux + r2 * r2 * uy * uy) + 0.02f;
     const float ey = sqrtf(r1 * r1 * uy * uy + r2 * r2 * ux * ux) + 0.02f;
-    const float hw = 0.5f * (float)(sw - 1), hh = 0.5f * (float)(sh - 1);
-    const float cx = x0 + 0.5f * (float)sw;
+    const float hw = 0.5f * (float)(bw - 1), hh = 0.5f * (float)(bh - 1);
+    const float cx = x0 + 0.5f * (float)bw;
     uint32_t m = 0u;
 #pragma unroll
-    for (int w = 0; w < kRenderThreads / 32; ++w) {
-        const float cy = y0 + (float)(w * sh) + 0.5f * (float)sh;
+    for (int w = 0; w < kRenderWarps; ++w) {
+        const float cy = y0 + (float)(w * bh) + 0.5f * (float)bh;
         const float dx = cx - A.x, dy = cy - A.y;
         const bool sep_x = fabsf(dx) > ex + hw;
         const bool sep_y = fabsf(dy) > ey + hh;
@@ -105,85 +121,84 @@ __device__ __forceinline__ uint32_t strip_mask(const float4 &A, const float4 &B,
     return m;
 }
 
-struct StripGeom {
-    float x0, y0;
-    int sw, sh;
-};
-
-__device__ __forceinline__ StripGeom strip_geom(const ViewTable &vt, int64_t t, const TileInfo &ti) {
-    StripGeom g;
-    const int64_t lt = t - vt.tile_off[ti.v];
-    const int gx = vt.gx[ti.v];
-    g.x0 = (float)((int)(lt % gx) * vt.tile_w);
-    g.y0 = (float)((int)(lt / gx) * vt.tile_h);
-    g.sw = vt.tile_w < 32 ? vt.tile_w : 32;
-    g.sh = 32 / g.sw;
-    return g;
-}
-
 // COUNT = true adds per-fragment counters (an untimed diagnostic variant):
 // [0] positions walked (sum of n_contrib), [1] unmasked positions walked,
 // [2] unmasked splats blended, [3] masked splats above the alpha floor.
-// Counters [1] and [3] count every walked position, culled or not.
+// They count every walked position, culled or not.
 template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, float bg0, float bg1, float bg2,
                       float *__restrict__ image, float *__restrict__ final_T,
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count) {
-    __shared__ float4 sA[kRenderThreads], sB[kRenderThreads], sC[kRenderThreads];
-    __shared__ uint8_t sM[kRenderThreads];
+    __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
+    __shared__ uint8_t sM[kBatch];
     __shared__ unsigned long long s_frags[4];
     const int64_t t = blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
-    const StripGeom sg = strip_geom(vt, t, ti);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
-    const float fpx = (float)ti.px + 0.5f, fpy = (float)ti.py + 0.5f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    bool done = !ti.inside;
-    uint32_t stop = end - start;
+    float fpx[kPix], fpy[kPix], T[kPix], C0[kPix], C1[kPix], C2[kPix];
+    bool done[kPix];
+    uint32_t stop[kPix];
     uint32_t c_unmasked = 0, c_blend = 0, c_masked = 0;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        fpx[k] = (float)ti.px[k] + 0.5f;
+        fpy[k] = (float)ti.py[k] + 0.5f;
+        T[k] = 1.0f;
+        C0[k] = C1[k] = C2[k] = 0.0f;
+        done[k] = !ti.inside[k];
+        stop[k] = end - start;
+    }
     if (threadIdx.x < 4) s_frags[threadIdx.x] = 0ull;
 
-    for (uint32_t b0 = start; b0 < end; b0 += kRenderThreads) {
-        if (__syncthreads_count(done) == kRenderThreads) break;
-        const uint32_t idx = b0 + threadIdx.x;
-        if (idx < end) {
-            const uint32_t r = vals[idx];
-            const float4 A = rec[3 * (int64_t)r], B = rec[3 * (int64_t)r + 1];
-            sA[threadIdx.x] = A;
-            sB[threadIdx.x] = B;
-            sC[threadIdx.x] = rec[3 * (int64_t)r + 2];
-            // masked splats neither colour nor attenuate: out of every forward list
-            sM[threadIdx.x] = (uint8_t)((B.w != 0.0f) ? strip_mask(A, B, sg.x0, sg.y0, sg.sw, sg.sh) : 0u);
-        }
-        __syncthreads();
-        const int cnt = (int)min(end - b0, (uint32_t)kRenderThreads);
-        if (COUNT && !done) {
-            // diagnostic counts over every position (culled or not) up to the stop
-            int j = 0;
-            float Tc = T;
-            for (; j < cnt; ++j) {
-                const float4 B = sB[j];
-                Frag f;
-                frag_alpha(sA[j], B, fpx, fpy, f);
-                if (B.w == 0.0f) {
-                    c_masked += f.alpha >= kAlphaMin;
-                    continue;
-                }
-                ++c_unmasked;
-                if (f.alpha < kAlphaMin) continue;
-                const float tT = Tc * (1.0f - f.alpha);
-                if (tT < kTMin) {
-                    --c_unmasked;
-                    break;
-                }
-                ++c_blend;
-                Tc = tT;
+    for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
+        if (__syncthreads_count(done[0] && done[1]) == kRenderThreads) break;
+#pragma unroll
+        for (int h = 0; h < kBatch / kRenderThreads; ++h) {
+            const int i = threadIdx.x + h * kRenderThreads;
+            if (b0 + i < end) {
+                const uint32_t r = vals[b0 + i];
+                const float4 A = rec[3 * (int64_t)r], B = rec[3 * (int64_t)r + 1];
+                sA[i] = A;
+                sB[i] = B;
+                sC[i] = rec[3 * (int64_t)r + 2];
+                // masked splats neither colour nor attenuate: out of every forward list
+                sM[i] = (uint8_t)((B.w != 0.0f)
+                                      ? block_mask(A, B, (float)ti.x0, (float)ti.y0, vt.tile_w, ti.bh)
+                                      : 0u);
             }
         }
-        if (__all_sync(0xffffffffu, done)) continue;
+        __syncthreads();
+        const int cnt = (int)min(end - b0, (uint32_t)kBatch);
+        if (COUNT) {
+            // diagnostic counts over every position (culled or not) up to the stop
+#pragma unroll
+            for (int k = 0; k < kPix; ++k) {
+                if (done[k]) continue;
+                float Tc = T[k];
+                for (int j = 0; j < cnt; ++j) {
+                    const float4 B = sB[j];
+                    Frag f;
+                    frag_alpha(sA[j], B, fpx[k], fpy[k], f);
+                    if (B.w == 0.0f) {
+                        c_masked += f.alpha >= kAlphaMin;
+                        continue;
+                    }
+                    ++c_unmasked;
+                    if (f.alpha < kAlphaMin) continue;
+                    const float tT = Tc * (1.0f - f.alpha);
+                    if (tT < kTMin) {
+                        --c_unmasked;
+                        break;
+                    }
+                    ++c_blend;
+                    Tc = tT;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, done[0] && done[1])) continue;
         const int nchunks = (cnt + 31) >> 5;
         for (int ch = 0; ch < nchunks; ++ch) {
             const int jj = (ch << 5) + lane;
@@ -191,49 +206,55 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
             while (word) {
                 const int j = (ch << 5) + __ffs(word) - 1;
                 word &= word - 1;
-                if (done) continue;
-                Frag f;
-                frag_alpha(sA[j], sB[j], fpx, fpy, f);
-                if (f.alpha < kAlphaMin) continue;
-                const float testT = T * (1.0f - f.alpha);
-                if (testT < kTMin) {
-                    done = true;
-                    stop = (b0 - start) + j;
-                    continue;
+                const float4 A = sA[j], B = sB[j], c = sC[j];
+#pragma unroll
+                for (int k = 0; k < kPix; ++k) {
+                    if (done[k]) continue;
+                    Frag f;
+                    frag_alpha(A, B, fpx[k], fpy[k], f);
+                    if (f.alpha < kAlphaMin) continue;
+                    const float testT = T[k] * (1.0f - f.alpha);
+                    if (testT < kTMin) {
+                        done[k] = true;
+                        stop[k] = (b0 - start) + j;
+                        continue;
+                    }
+                    const float w = f.alpha * T[k];
+                    C0[k] = fmaf(w, c.x, C0[k]);
+                    C1[k] = fmaf(w, c.y, C1[k]);
+                    C2[k] = fmaf(w, c.z, C2[k]);
+                    T[k] = testT;
                 }
-                const float4 c = sC[j];
-                const float w = f.alpha * T;
-                C0 = fmaf(w, c.x, C0);
-                C1 = fmaf(w, c.y, C1);
-                C2 = fmaf(w, c.z, C2);
-                T = testT;
             }
-            if (__all_sync(0xffffffffu, done)) break;
+            if (__all_sync(0xffffffffu, done[0] && done[1])) break;
         }
     }
     if (COUNT) {
-        unsigned long long c[4] = {ti.inside ? stop : 0u, c_unmasked, c_blend, c_masked};
+        unsigned long long c[4] = {(ti.inside[0] ? stop[0] : 0u) + (ti.inside[1] ? stop[1] : 0u),
+                                   c_unmasked, c_blend, c_masked};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_down_sync(0xffffffffu, c[k], o);
         }
         __syncthreads();
-        if ((threadIdx.x & 31) == 0)
+        if (lane == 0)
 #pragma unroll
             for (int k = 0; k < 4; ++k) atomicAdd(&s_frags[k], c[k]);
         __syncthreads();
         if (threadIdx.x < 4) atomicAdd(frag_count + threadIdx.x, s_frags[threadIdx.x]);
     }
-    if (ti.inside) {
-        const mg_camera &C = vt.cam[ti.v];
-        const int64_t HW = (int64_t)C.width * C.height;
-        float *img = image + 3 * vt.pix_off[ti.v];
-        img[ti.pix] = C0 + T * bg0;
-        img[HW + ti.pix] = C1 + T * bg1;
-        img[2 * HW + ti.pix] = C2 + T * bg2;
-        final_T[vt.pix_off[ti.v] + ti.pix] = T;
-        n_contrib[vt.pix_off[ti.v] + ti.pix] = stop;
+    const mg_camera &Cm = vt.cam[ti.v];
+    const int64_t HW = (int64_t)Cm.width * Cm.height;
+    float *img = image + 3 * vt.pix_off[ti.v];
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        if (!ti.inside[k]) continue;
+        img[ti.pix[k]] = C0[k] + T[k] * bg0;
+        img[HW + ti.pix[k]] = C1[k] + T[k] * bg1;
+        img[2 * HW + ti.pix[k]] = C2[k] + T[k] * bg2;
+        final_T[vt.pix_off[ti.v] + ti.pix[k]] = T[k];
+        n_contrib[vt.pix_off[ti.v] + ti.pix[k]] = stop[k];
     }
 }
 
@@ -270,8 +291,8 @@ constexpr int kAcc = 10;
 
 // COUNT = true accumulates profiling counters (an untimed variant):
 // [0] (warp, splat) list iterations, [1] of which masked, [2] unmasked with a
-// contributing lane, [3] masked with a contributing lane, [4] contributing
-// lanes over [2], [5] staged batches.
+// contributing pixel, [3] masked with a contributing pixel, [4] contributing
+// pixels over [2], [5] staged batches.
 template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
@@ -279,60 +300,74 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        float bg0, float bg1, float bg2, const float *__restrict__ final_T,
                        const uint32_t *__restrict__ n_contrib, const float *__restrict__ dL_dimage,
                        float *__restrict__ grad2d, unsigned long long *counters) {
-    unsigned long long cnt_it = 0, cnt_m = 0, cnt_cu = 0, cnt_cm = 0, cnt_lanes = 0, cnt_b = 0;
-    __shared__ float4 sA[kRenderThreads], sB[kRenderThreads], sC[kRenderThreads];
-    __shared__ uint32_t sR[kRenderThreads];
-    __shared__ uint8_t sM[kRenderThreads];
-    __shared__ float sG[kRenderThreads][kAcc];
+    unsigned long long cnt_it = 0, cnt_m = 0, cnt_cu = 0, cnt_cm = 0, cnt_pix = 0, cnt_b = 0;
+    __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
+    __shared__ uint32_t sR[kBatch];
+    __shared__ uint8_t sM[kBatch];
+    __shared__ float sG[kBatch][kAcc];
     __shared__ uint32_t s_maxstop;
     const int64_t t = blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
-    const StripGeom sg = strip_geom(vt, t, ti);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
-    const float fpx = (float)ti.px + 0.5f, fpy = (float)ti.py + 0.5f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-    uint32_t stop = 0;
-    if (ti.inside) {
-        const mg_camera &C = vt.cam[ti.v];
-        const int64_t HW = (int64_t)C.width * C.height;
-        const int64_t p = vt.pix_off[ti.v] + ti.pix;
-        T = final_T[p];
-        stop = n_contrib[p];
-        const float *gi = dL_dimage + 3 * vt.pix_off[ti.v];
-        g0 = gi[ti.pix];
-        g1 = gi[HW + ti.pix];
-        g2 = gi[2 * HW + ti.pix];
+    float fpx[kPix], fpy[kPix], T[kPix], g0[kPix], g1[kPix], g2[kPix], bc0[kPix], bc1[kPix],
+        bc2[kPix];
+    uint32_t stop[kPix];
+    const mg_camera &Cm = vt.cam[ti.v];
+    const int64_t HW = (int64_t)Cm.width * Cm.height;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        fpx[k] = (float)ti.px[k] + 0.5f;
+        fpy[k] = (float)ti.py[k] + 0.5f;
+        T[k] = 1.0f;
+        g0[k] = g1[k] = g2[k] = 0.0f;
+        stop[k] = 0;
+        if (ti.inside[k]) {
+            const int64_t p = vt.pix_off[ti.v] + ti.pix[k];
+            T[k] = final_T[p];
+            stop[k] = n_contrib[p];
+            const float *gi = dL_dimage + 3 * vt.pix_off[ti.v];
+            g0[k] = gi[ti.pix[k]];
+            g1[k] = gi[HW + ti.pix[k]];
+            g2[k] = gi[2 * HW + ti.pix[k]];
+        }
+        bc0[k] = bg0;                          // colour behind, background folded in
+        bc1[k] = bg1;
+        bc2[k] = bg2;
     }
-    float b0c = bg0, b1c = bg1, b2c = bg2;   // colour behind, background folded in
+    uint32_t tstop = max(stop[0], stop[1]);
     if (threadIdx.x == 0) s_maxstop = 0;
     __syncthreads();
-    atomicMax(&s_maxstop, stop);
+    atomicMax(&s_maxstop, tstop);
     __syncthreads();
     const uint32_t maxstop = min(s_maxstop, end - start);
     if (maxstop == 0) return;
-    if (COUNT) cnt_b = (maxstop + kRenderThreads - 1) / kRenderThreads;
-    const int nb = (int)((maxstop + kRenderThreads - 1) / kRenderThreads);
-    uint32_t wstop = stop;                                     // warp's largest stop
+    const int nb = (int)((maxstop + kBatch - 1) / kBatch);
+    if (COUNT) cnt_b = nb;
+    uint32_t wstop = tstop;                                    // warp's largest stop
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wstop = max(wstop, __shfl_xor_sync(0xffffffffu, wstop, o));
 
     for (int bi = nb - 1; bi >= 0; --bi) {
-        const uint32_t pos0 = (uint32_t)bi * kRenderThreads;
-        const int cnt = (int)min(maxstop - pos0, (uint32_t)kRenderThreads);
+        const uint32_t pos0 = (uint32_t)bi * kBatch;
+        const int cnt = (int)min(maxstop - pos0, (uint32_t)kBatch);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t r = vals[start + pos0 + threadIdx.x];
-            const float4 A = rec[3 * (int64_t)r], B = rec[3 * (int64_t)r + 1];
-            sR[threadIdx.x] = r;
-            sA[threadIdx.x] = A;
-            sB[threadIdx.x] = B;
-            sC[threadIdx.x] = rec[3 * (int64_t)r + 2];
-            sM[threadIdx.x] = (uint8_t)strip_mask(A, B, sg.x0, sg.y0, sg.sw, sg.sh);
-        }
 #pragma unroll
-        for (int k = 0; k < kAcc; ++k) sG[threadIdx.x][k] = 0.0f;
+        for (int h = 0; h < kBatch / kRenderThreads; ++h) {
+            const int i = threadIdx.x + h * kRenderThreads;
+            if (i < cnt) {
+                const uint32_t r = vals[start + pos0 + i];
+                const float4 A = rec[3 * (int64_t)r], B = rec[3 * (int64_t)r + 1];
+                sR[i] = r;
+                sA[i] = A;
+                sB[i] = B;
+                sC[i] = rec[3 * (int64_t)r + 2];
+                sM[i] = (uint8_t)block_mask(A, B, (float)ti.x0, (float)ti.y0, vt.tile_w, ti.bh);
+            }
+#pragma unroll
+            for (int k = 0; k < kAcc; ++k) sG[i][k] = 0.0f;
+        }
         __syncthreads();
 
         if (pos0 < wstop) {
@@ -344,53 +379,55 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     const int hb = 31 - __clz(word);
                     word &= ~(1u << hb);
                     const int j = (ch << 5) + hb;
-                    const float4 B = sB[j];
+                    const float4 A = sA[j], B = sB[j], c = sC[j];
                     const bool masked = B.w == 0.0f;
                     float v[16];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) v[k] = 0.0f;
-                    bool contrib = false;
-                    if (pos0 + j < stop) {
-                        const float4 A = sA[j];
+                    for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+                    int ncontrib = 0;
+#pragma unroll
+                    for (int k = 0; k < kPix; ++k) {
+                        if (pos0 + j >= stop[k]) continue;
                         Frag f;
-                        frag_alpha(A, B, fpx, fpy, f);
-                        if (f.alpha >= kAlphaMin) {
-                            contrib = true;
-                            const float4 c = sC[j];
-                            const float ma = masked ? 0.0f : f.alpha;
-                            const float Tj = __fdividef(T, 1.0f - ma);
-                            const float gcb = g0 * (c.x - b0c) + g1 * (c.y - b1c) + g2 * (c.z - b2c);
-                            v[9] = f.alpha * Tj * gcb;             // Eq. 6 + Appendix A
-                            if (!masked) {
-                                const float wt = f.alpha * Tj;
-                                v[6] = wt * g0;
-                                v[7] = wt * g1;
-                                v[8] = wt * g2;
-                                b0c = fmaf(f.alpha, c.x - b0c, b0c);
-                                b1c = fmaf(f.alpha, c.y - b1c, b1c);
-                                b2c = fmaf(f.alpha, c.z - b2c, b2c);
-                                T = Tj;
-                                if (f.araw < kAlphaMax) {
-                                    const float dpow = Tj * gcb * f.alpha;   // dL/dalpha * alpha
-                                    v[0] = dpow;
-                                    v[1] = dpow * f.dx;
-                                    v[2] = dpow * f.dy;
-                                    v[3] = v[1] * f.dx;
-                                    v[4] = v[1] * f.dy;
-                                    v[5] = v[2] * f.dy;
-                                }
+                        frag_alpha(A, B, fpx[k], fpy[k], f);
+                        if (f.alpha < kAlphaMin) continue;
+                        ++ncontrib;
+                        const float ma = masked ? 0.0f : f.alpha;
+                        const float Tj = __fdividef(T[k], 1.0f - ma);
+                        const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
+                                          g2[k] * (c.z - bc2[k]);
+                        v[9] += f.alpha * Tj * gcb;           // Eq. 6 + Appendix A
+                        if (!masked) {
+                            const float wt = f.alpha * Tj;
+                            v[6] += wt * g0[k];
+                            v[7] += wt * g1[k];
+                            v[8] += wt * g2[k];
+                            bc0[k] = fmaf(f.alpha, c.x - bc0[k], bc0[k]);
+                            bc1[k] = fmaf(f.alpha, c.y - bc1[k], bc1[k]);
+                            bc2[k] = fmaf(f.alpha, c.z - bc2[k], bc2[k]);
+                            T[k] = Tj;
+                            if (f.araw < kAlphaMax) {
+                                const float dpow = Tj * gcb * f.alpha;   // dL/dalpha * alpha
+                                const float pdx = dpow * f.dx, pdy = dpow * f.dy;
+                                v[0] += dpow;
+                                v[1] += pdx;
+                                v[2] += pdy;
+                                v[3] += pdx * f.dx;
+                                v[4] += pdx * f.dy;
+                                v[5] += pdy * f.dy;
                             }
                         }
                     }
                     if (COUNT) {
-                        const unsigned cb = __ballot_sync(0xffffffffu, contrib);
+                        const unsigned cb = __ballot_sync(0xffffffffu, ncontrib > 0);
+                        const int tot = __reduce_add_sync(0xffffffffu, (unsigned)ncontrib);
                         ++cnt_it;
                         cnt_m += masked;
                         cnt_cu += (!masked && cb);
                         cnt_cm += (masked && cb);
-                        cnt_lanes += masked ? 0 : __popc(cb);
+                        cnt_pix += masked ? 0 : tot;
                     }
-                    if (__any_sync(0xffffffffu, contrib)) {
+                    if (__any_sync(0xffffffffu, ncontrib > 0)) {
                         if (masked) {
                             const float dm = warp_sum(v[9]);
                             if (lane == 0) atomicAdd(&sG[j][9], dm);
@@ -403,14 +440,17 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
             }
         }
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const float *S = sG[threadIdx.x];
-            float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[threadIdx.x];
-            const float4 B = sB[threadIdx.x];
+#pragma unroll
+        for (int h = 0; h < kBatch / kRenderThreads; ++h) {
+            const int i = threadIdx.x + h * kRenderThreads;
+            if (i >= cnt) continue;
+            const float *S = sG[i];
+            float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[i];
+            const float4 B = sB[i];
             if (B.w == 0.0f) {
                 if (S[9] != 0.0f) atomicAdd(&G4[2].y, S[9]);
             } else {
-                const float4 A = sA[threadIdx.x];
+                const float4 A = sA[i];
                 // Sigma^-1 in eigen form: w_k = -2 h_k / log2(e)
                 const float w1 = (-2.0f / kLog2e) * B.x, w2 = (-2.0f / kLog2e) * B.y;
                 const float q00 = w1 * A.z * A.z + w2 * A.w * A.w;
@@ -432,7 +472,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
         atomicAdd(counters + 1, cnt_m);
         atomicAdd(counters + 2, cnt_cu);
         atomicAdd(counters + 3, cnt_cm);
-        atomicAdd(counters + 4, cnt_lanes);
+        atomicAdd(counters + 4, cnt_pix);
         if (warp == 0) atomicAdd(counters + 5, cnt_b);
     }
 }
