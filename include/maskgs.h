@@ -9,11 +9,12 @@
  *                             Gumbel-softmax over two existence scores) and
  *                             splat every Gaussian, unmasked, to a 2D
  *                             Gaussian with a view-dependent colour (Sec. 3.1)
- *   2. mg_bin                 duplicate each visible splat once per 16x16 tile
- *                             it intersects (Sec. 3.1), keyed by (tile, depth)
- *   3. mg_sort                order every tile's splats by depth (Sec. 3.1,
- *                             "the i-th Gaussian in the depth order") and find
- *                             each tile's range
+ *   2. mg_depth_order, mg_bin order the splats by depth (Sec. 3.1, "the i-th
+ *                             Gaussian in the depth order") and duplicate each
+ *                             visible splat once per 16x16 tile it intersects
+ *                             (Sec. 3.1), keyed by (tile, depth)
+ *   3. mg_sort                group the instances by tile, keeping the depth
+ *                             order, and find each tile's range
  *   4. mg_render              masked alpha blending, Eq. 3-4
  *   5. mg_l1_loss_grad        an L1 render loss and dL/dC (Eq. 8's L_render)
  *   6. mg_render_backward     the mask gradient of Eq. 6 with the background
@@ -179,17 +180,28 @@ mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, int32_t n_v
                         const mg_raster_cfg *cfg, const mg_splats *out,
                         mg_status_word *d_status, mg_stream_t stream);
 
-/* ---- 2. bin (Sec. 3.1) ---------------------------------------------------- */
-/* Exclusive scan of tiles_touched over all R records into offsets[R] (u32)
- * and the total K into *d_num_instances (device u64); then writes, for every
- * visible record r and every tile of its rectangle (row-major), the key
+/* ---- 2. depth order and bin (Sec. 3.1) ------------------------------------ */
+/* Stable radix sort of the R splat records (all views) by the float bits of
+ * their depth, records that touch no tile last: order[R] (u32 record indices).
+ * Depth ties keep record order.  keys, keys_alt, order_alt: u32[R] scratch.
+ * workspace: mg_depth_order_workspace_bytes(R) bytes, any content. */
+mg_status mg_depth_order(const mg_splats *splats, const mg_view *views, int32_t n_views,
+                         const mg_raster_cfg *cfg, uint32_t *order, uint32_t *order_alt,
+                         uint32_t *keys, uint32_t *keys_alt, void *workspace,
+                         size_t workspace_bytes, mg_status_word *d_status, mg_stream_t stream);
+size_t mg_depth_order_workspace_bytes(int64_t n_records);
+
+/* Visits the R records in `order` (nullable: record order) and writes, for
+ * position i, offsets[i] = sum_{j<i} tiles_touched[order[j]] (u32) and the
+ * total K into *d_num_instances (device u64); then, for every visible record
+ * r = order[i] and every tile of its rectangle (row-major), the key
  * (global tile id << 32) | float bits of depth and the value r at
- * offsets[r] + k.  Instances beyond `capacity` are not written and raise
+ * offsets[i] + k.  Instances beyond `capacity` are not written and raise
  * MG_ERR_CAPACITY with `required` = K.  workspace: device scratch of
  * mg_bin_workspace_bytes(R) bytes, any content. */
 mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
-                 const mg_raster_cfg *cfg, uint32_t *offsets, uint64_t *keys,
-                 uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
+                 const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
+                 uint64_t *keys, uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
                  void *workspace, size_t workspace_bytes, mg_status_word *d_status,
                  mg_stream_t stream);
 size_t mg_bin_workspace_bytes(int64_t n_records);
@@ -208,25 +220,28 @@ size_t mg_bin_workspace_bytes(int64_t n_records);
  * threads) race: serialise them.  Nothing is allocated: no cudaMalloc, no
  * cudaFree. */
 mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views, int32_t n_views,
-                         const mg_raster_cfg *cfg, uint32_t *offsets, uint64_t *keys,
-                         uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
-                         mg_status_word *d_status, mg_stream_t stream);
+                         const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
+                         uint64_t *keys, uint32_t *vals, uint64_t capacity,
+                         uint64_t *d_num_instances, mg_status_word *d_status,
+                         mg_stream_t stream);
 
 /* ---- 3. sort + tile ranges (Sec. 3.1) -------------------------------------- */
 /* Stable LSD radix sort (8-bit digits, single-pass "onesweep" passes with
  * decoupled look-back) of the first *d_num_instances (key, value) pairs by
- * the low key_bits bits of the key, then ranges[t] = [start, end) of the
+ * key bits [begin_bit, key_bits), then ranges[t] = [start, end) of the
  * instances of global tile t (n_tiles_total = sum of all views' tiles).
- * Because the instances are emitted in record order, ties in depth are
- * broken by record index.  The sorted pairs end in (keys, vals) when
+ * With instances emitted in depth order (mg_depth_order, then mg_bin), sort
+ * the tile bits only (begin_bit = 32): each tile's list then comes out ordered
+ * by (depth, record index), as a full sort (begin_bit = 0) of record-ordered
+ * instances would order it.  The sorted pairs end in (keys, vals) when
  * *result_in_alt (host int) is set to 0, else in (keys_alt, vals_alt); it is
- * known on the host from key_bits alone.  When *d_num_instances exceeds
+ * known on the host from the bit range alone.  When *d_num_instances exceeds
  * capacity (mg_bin raised MG_ERR_CAPACITY) nothing is sorted and every range
- * is empty.  workspace: mg_sort_workspace_bytes(capacity, key_bits) bytes, any
- * content.  key_bits: 33..64; capacity < 2^30. */
+ * is empty.  workspace: mg_sort_workspace_bytes(capacity, key_bits) bytes,
+ * any content.  key_bits: 33..64, begin_bit: 0..32; capacity < 2^30. */
 mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                  const uint64_t *d_num_instances, uint64_t capacity, int32_t key_bits,
-                  uint32_t *ranges, int64_t n_tiles_total, void *workspace,
+                  const uint64_t *d_num_instances, uint64_t capacity, int32_t begin_bit,
+                  int32_t key_bits, uint32_t *ranges, int64_t n_tiles_total, void *workspace,
                   size_t workspace_bytes, int32_t *result_in_alt, mg_status_word *d_status,
                   mg_stream_t stream);
 size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);

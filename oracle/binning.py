@@ -44,3 +44,10 @@ def tile_ranges(sorted_keys, n_tiles):
     start = np.searchsorted(tile, t, side="left")
     end = np.searchsorted(tile, t, side="right")
     return np.stack([start, end], axis=1).astype(np.uint32)
+
+
+def depth_order(depth_bits, visible):
+    """Records ordered by the float bits of their depth (stable: ties keep
+    record order), records outside every tile last."""
+    keys = np.where(visible, depth_bits.astype(np.uint64), np.uint64(0xFFFFFFFF))
+    return np.argsort(keys, kind="stable").astype(np.uint32)

@@ -19,7 +19,8 @@ MG_MAX_VIEWS = 64
 MG_RECORD_FLOATS = 12
 MG_GRAD2D_FLOATS = 12
 
-EXPORTED = ("mg_preprocess", "mg_bin", "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
+EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes", "mg_bin",
+            "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
             "mg_sort_workspace_bytes", "mg_key_bits", "mg_total_tiles", "mg_render",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_read_status", "mg_status_string", "mg_version")
@@ -93,13 +94,16 @@ def load(build_if_missing: bool = True):
     sig = {
         "mg_preprocess": (st, [_P(mg_gaussians), _P(mg_view), C.c_int32, _P(mg_raster_cfg),
                                _P(mg_splats), vp, vp]),
-        "mg_bin": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp, vp, vp,
+        "mg_depth_order": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp,
+                                vp, vp, vp, vp, C.c_size_t, vp, vp]),
+        "mg_depth_order_workspace_bytes": (C.c_size_t, [C.c_int64]),
+        "mg_bin": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp, vp, vp, vp,
                         C.c_uint64, vp, vp, C.c_size_t, vp, vp]),
         "mg_bin_noalloc": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp,
-                                vp, vp, C.c_uint64, vp, vp, vp]),
+                                vp, vp, vp, C.c_uint64, vp, vp, vp]),
         "mg_bin_workspace_bytes": (C.c_size_t, [C.c_int64]),
-        "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, vp, C.c_int64, vp,
-                         C.c_size_t, _P(C.c_int32), vp, vp]),
+        "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, C.c_int32, vp, C.c_int64,
+                         vp, C.c_size_t, _P(C.c_int32), vp, vp]),
         "mg_sort_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int32]),
         "mg_key_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_total_tiles": (C.c_int64, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
@@ -150,31 +154,45 @@ def mg_preprocess(g, views, n_views, cfg, out, d_status, stream):
                                                  C.byref(out), ptr(d_status), stream))
 
 
-def mg_bin(splats, views, n_views, cfg, offsets, keys, vals, capacity, d_num_instances,
+def mg_depth_order(splats, views, n_views, cfg, order, order_alt, keys, keys_alt, workspace,
+                   workspace_bytes, d_status, stream):
+    _check("mg_depth_order", load().mg_depth_order(
+        C.byref(splats), views, n_views, C.byref(cfg), ptr(order), ptr(order_alt), ptr(keys),
+        ptr(keys_alt), ptr(workspace), workspace_bytes, ptr(d_status), stream))
+
+
+def mg_depth_order_workspace_bytes(n_records) -> int:
+    return int(load().mg_depth_order_workspace_bytes(n_records))
+
+
+def mg_bin(splats, views, n_views, cfg, order, offsets, keys, vals, capacity, d_num_instances,
            workspace, workspace_bytes, d_status, stream):
-    _check("mg_bin", load().mg_bin(C.byref(splats), views, n_views, C.byref(cfg), ptr(offsets),
-                                   ptr(keys), ptr(vals), capacity, ptr(d_num_instances),
-                                   ptr(workspace), workspace_bytes, ptr(d_status), stream))
+    _check("mg_bin", load().mg_bin(C.byref(splats), views, n_views, C.byref(cfg), ptr(order),
+                                   ptr(offsets), ptr(keys), ptr(vals), capacity,
+                                   ptr(d_num_instances), ptr(workspace), workspace_bytes,
+                                   ptr(d_status), stream))
 
 
-def mg_bin_noalloc(splats, views, n_views, cfg, offsets, keys, vals, capacity, d_num_instances,
-                   d_status, stream):
+def mg_bin_noalloc(splats, views, n_views, cfg, order, offsets, keys, vals, capacity,
+                   d_num_instances, d_status, stream):
     """mg_bin for callers that cannot allocate: its scratch is a fixed array
     inside the library (at most 2^24 records; concurrent calls race)."""
     _check("mg_bin_noalloc", load().mg_bin_noalloc(C.byref(splats), views, n_views, C.byref(cfg),
-                                                   ptr(offsets), ptr(keys), ptr(vals), capacity,
-                                                   ptr(d_num_instances), ptr(d_status), stream))
+                                                   ptr(order), ptr(offsets), ptr(keys), ptr(vals),
+                                                   capacity, ptr(d_num_instances), ptr(d_status),
+                                                   stream))
 
 
 def mg_bin_workspace_bytes(n_records) -> int:
     return int(load().mg_bin_workspace_bytes(n_records))
 
 
-def mg_sort(keys, vals, keys_alt, vals_alt, d_num_instances, capacity, key_bits, ranges,
-            n_tiles_total, workspace, workspace_bytes, d_status, stream) -> int:
+def mg_sort(keys, vals, keys_alt, vals_alt, d_num_instances, capacity, begin_bit, key_bits,
+            ranges, n_tiles_total, workspace, workspace_bytes, d_status, stream) -> int:
     alt = C.c_int32(0)
     _check("mg_sort", load().mg_sort(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt),
-                                     ptr(d_num_instances), capacity, key_bits, ptr(ranges),
+                                     ptr(d_num_instances), capacity, begin_bit, key_bits,
+                                     ptr(ranges),
                                      n_tiles_total, ptr(workspace), workspace_bytes,
                                      C.byref(alt), ptr(d_status), stream))
     return int(alt.value)

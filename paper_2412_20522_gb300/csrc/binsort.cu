@@ -2,18 +2,31 @@
 // intersects the tile) and depth ordering (Sec. 3.1: Gaussians blended "in
 // the depth order").
 //
-//   scan      single-pass exclusive scan of tiles_touched (decoupled look-back)
-//   duplicate one (tile | depth) key per intersected tile, row-major per splat
-//   sort      stable LSD radix sort, 8-bit digits, one "onesweep" kernel per
-//             digit (Adinets & Merrill, "Onesweep: a faster least significant
-//             digit radix sort for GPUs", 2022): local ranking by warp
-//             match-any multi-split, global offsets by decoupled look-back
-//   ranges    [start, end) of every tile in the sorted list
+//   depth order  stable radix sort of the splat records by the float bits of
+//                their depth (4 passes over R records)
+//   scan         single-pass exclusive scan of tiles_touched, in depth order
+//                (decoupled look-back)
+//   duplicate    one (tile | depth) key per intersected tile, row-major per
+//                splat, splats in depth order
+//   sort         stable LSD radix sort of the instances on the tile bits only
+//                (key bits 32 and up; 2 passes for up to 65536 tiles): as the
+//                instances arrive in depth order, every tile's list comes out
+//                ordered by (depth, record index) -- the order a full sort of
+//                the 64-bit (tile, depth) keys of record-ordered instances
+//                gives, with a third of the traffic
+//   ranges       [start, end) of every tile in the sorted list
+//
+// The radix sort is "onesweep" (Adinets & Merrill, "Onesweep: a faster least
+// significant digit radix sort for GPUs", 2022): 8-bit digits, one kernel per
+// digit, local ranking by warp match-any multi-split, global offsets by
+// decoupled look-back.
 //
 // Every cross-block wait is bounded: after kMaxTimeoutSpins polls the kernel
 // records MG_ERR_TIMEOUT in the status word and carries on (results are then
 // invalid, but the GPU never hangs).  Partition ids come from an atomic
 // counter, so a block only ever waits on partitions held by running blocks.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace mg {
@@ -32,15 +45,6 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
 __device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
     return *reinterpret_cast<const volatile uint64_t *>(p);
 }
-
-// --------------------------------------------------------------------------
-// scan of tiles_touched
-// --------------------------------------------------------------------------
-struct ScanWS {
-    uint32_t counter;
-    uint32_t pad;
-    uint64_t status[1];   // [n_parts]
-};
 
 __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t *sm_warp,
                                                              uint64_t &total) {
@@ -69,10 +73,19 @@ __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_
     return sm_warp[warp] + inc - v;
 }
 
+// --------------------------------------------------------------------------
+// scan of tiles_touched (in the given order)
+// --------------------------------------------------------------------------
+struct ScanWS {
+    uint32_t counter;
+    uint32_t pad;
+    uint64_t status[1];   // [n_parts]
+};
+
 __global__ void __launch_bounds__(kScanThreads)
-scan_kernel(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ out,
-            uint64_t *d_total, uint64_t capacity, ScanWS *ws, int64_t n_parts,
-            mg_status_word *st) {
+scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order, int64_t n,
+            uint32_t *__restrict__ out, uint64_t *d_total, uint64_t capacity, ScanWS *ws,
+            int64_t n_parts, mg_status_word *st) {
     __shared__ uint64_t sm_warp[33];
     __shared__ uint64_t sm_prefix;
     __shared__ int64_t sm_part;
@@ -83,14 +96,15 @@ scan_kernel(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ o
     const int64_t base = part * kScanPart + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint64_t sum = 0;
-    if (base + kScanItems <= n) {
+    if (order == nullptr && base + kScanItems <= n) {
         const uint4 a = *reinterpret_cast<const uint4 *>(in + base);
         const uint4 b = *reinterpret_cast<const uint4 *>(in + base + 4);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+        for (int k = 0; k < kScanItems; ++k)
+            v[k] = (base + k < n) ? in[order ? order[base + k] : base + k] : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) sum += v[k];
@@ -138,29 +152,31 @@ scan_kernel(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ o
 // --------------------------------------------------------------------------
 // key duplication
 // --------------------------------------------------------------------------
-// One thread per record writes small rectangles; rectangles of more than 32
-// tiles are written by the whole warp, one at a time, 32 tiles per step (the
-// near-camera splats of a scene cover thousands of tiles).
+// One thread per position (record order[i], or i) writes small rectangles;
+// rectangles of more than 32 tiles are written by the whole warp, one at a
+// time, 32 tiles per step (near-camera splats cover thousands of tiles).
 __global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
                                  const int32_t *__restrict__ radius,
                                  const uint32_t *__restrict__ tiles,
+                                 const uint32_t *__restrict__ order,
                                  const uint32_t *__restrict__ offsets, int64_t n_records,
                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                  uint64_t capacity) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     bool valid = false;
     uint64_t off = 0, dbits = 0, t0 = 0;
-    uint32_t nt = 0;
+    uint32_t nt = 0, r = 0;
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1, gx = 1;
-    if (r < n_records) {
+    if (i < n_records) {
+        r = order ? order[i] : (uint32_t)i;
         nt = tiles[r];
-        off = offsets[r];
+        off = offsets[i];
         if (nt != 0 && off + nt <= capacity) {
             int v = 0;
-            while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= r) ++v;
-            const float4 a = *reinterpret_cast<const float4 *>(record + 12 * r);
-            dbits = __float_as_uint(record[12 * r + 11]);
+            while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= (int64_t)r) ++v;
+            const float4 a = *reinterpret_cast<const float4 *>(record + 12 * (int64_t)r);
+            dbits = __float_as_uint(record[12 * (int64_t)r + 11]);
             t0 = (uint64_t)vt.tile_off[v];
             gx = vt.gx[v];
             valid = tile_rect(a.x, a.y, (float)radius[r], vt.tile_w, vt.tile_h, gx, vt.gy[v], x0,
@@ -174,7 +190,7 @@ __global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
         for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1 && k < k_end; ++tx, ++k) {
                 keys[k] = ((t0 + (uint64_t)ty * gx + tx) << 32) | dbits;
-                vals[k] = (uint32_t)r;
+                vals[k] = r;
             }
     }
     unsigned todo = __ballot_sync(0xffffffffu, big);
@@ -188,7 +204,7 @@ __global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
         const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
         const int by0 = __shfl_sync(0xffffffffu, y0, src);
         const int bgx = __shfl_sync(0xffffffffu, gx, src);
-        const uint32_t rr = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)r, src);
+        const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
         const uint32_t w = (uint32_t)(bx1 - bx0 + 1);
         for (uint32_t k = lane; k < n; k += 32) {
             const uint32_t ty = (uint32_t)by0 + k / w, tx = (uint32_t)bx0 + k % w;
@@ -199,7 +215,7 @@ __global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
 }
 
 // --------------------------------------------------------------------------
-// radix sort
+// radix sort (keys of type K, 8-bit digits from begin_bit up)
 // --------------------------------------------------------------------------
 // Instances to sort: all of them, or none when they overflowed the capacity
 // (the buffers then hold an incomplete list; the status word says so).
@@ -209,14 +225,16 @@ __device__ __forceinline__ int64_t sort_count(const uint64_t *d_n, uint64_t capa
 }
 
 struct SortWS {
+    uint64_t n;                        // element count for sorts whose count is host-known
     uint32_t hist[kMaxPasses][256];    // digit counts, then exclusive offsets
     uint32_t counter[kMaxPasses];
-    uint32_t pad[8];
+    uint32_t pad[6];
     uint32_t status[1];                // [2][max_parts][256]
 };
 
-__global__ void sort_histogram_kernel(const uint64_t *__restrict__ keys, const uint64_t *d_n,
-                                      uint64_t capacity, int passes, SortWS *ws,
+template <typename K>
+__global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t *d_n,
+                                      uint64_t capacity, int begin_bit, int passes, SortWS *ws,
                                       int64_t max_parts) {
     __shared__ uint32_t h[kMaxPasses][256];
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -224,7 +242,7 @@ __global__ void sort_histogram_kernel(const uint64_t *__restrict__ keys, const u
     const int64_t n = sort_count(d_n, capacity);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = keys[i];
+        const uint64_t k = (uint64_t)keys[i] >> begin_bit;
         for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
     }
     // clear the look-back status of the first pass for the partitions in use
@@ -249,12 +267,13 @@ __global__ void sort_offsets_kernel(SortWS *ws) {
     ws->hist[p][threadIdx.x] = (uint32_t)e;
 }
 
+template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                const uint64_t *d_n, uint64_t capacity, int pass, int shift, SortWS *ws,
-                int64_t max_parts, mg_status_word *st) {
-    __shared__ uint64_t sk[kSortPart];
+onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint64_t *d_n,
+                uint64_t capacity, int pass, int shift, SortWS *ws, int64_t max_parts,
+                mg_status_word *st) {
+    __shared__ K sk[kSortPart];
     __shared__ uint32_t sv[kSortPart];
     __shared__ uint32_t whist[kSortWarps][256];
     __shared__ uint32_t dstart[256];
@@ -280,16 +299,16 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
 
         // ---- load and rank within the warp (stable: slot-major, lane-minor)
         const int64_t wbase = part * kSortPart + (int64_t)warp * (32 * kSortItems);
-        uint64_t k[kSortItems];
+        K k[kSortItems];
         uint32_t val[kSortItems], rank[kSortItems];
         int dig[kSortItems];
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             const int64_t idx = wbase + i * 32 + lane;
             const bool valid = idx < n;
-            k[i] = valid ? keys_in[idx] : 0ull;
+            k[i] = valid ? keys_in[idx] : (K)0;
             val[i] = valid ? vals_in[idx] : 0u;
-            dig[i] = valid ? (int)((k[i] >> shift) & 0xFF) : 256;
+            dig[i] = valid ? (int)(((uint64_t)k[i] >> shift) & 0xFF) : 256;
         }
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
@@ -358,8 +377,8 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
         __syncthreads();
         const int cnt = (int)(n - part * kSortPart < kSortPart ? n - part * kSortPart : kSortPart);
         for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
-            const uint64_t kk = sk[j];
-            const int64_t dst = gbase[(kk >> shift) & 0xFF] + j;
+            const K kk = sk[j];
+            const int64_t dst = gbase[((uint64_t)kk >> shift) & 0xFF] + j;
             keys_out[dst] = kk;
             vals_out[dst] = sv[j];
         }
@@ -378,6 +397,20 @@ __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const uint64_t 
     }
 }
 
+// Depth keys of the records: float bits of the depth (positive, so the bits
+// order like the values); records outside every tile go last.
+__global__ void depth_keys_kernel(const float *__restrict__ record,
+                                  const uint32_t *__restrict__ tiles, int64_t n,
+                                  uint32_t *__restrict__ keys, uint32_t *__restrict__ idx,
+                                  uint64_t *d_n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        keys[r] = tiles[r] ? __float_as_uint(record[12 * r + 11]) : 0xFFFFFFFFu;
+        idx[r] = (uint32_t)r;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = (uint64_t)n;
+}
+
 static int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -385,12 +418,78 @@ static int sm_count() {
     return n > 0 ? n : 1;
 }
 
+static int64_t sort_max_parts(uint64_t capacity) {
+    return (int64_t)((capacity + kSortPart - 1) / kSortPart) + 1;
+}
+
+static size_t sort_ws_bytes(uint64_t capacity) {
+    return sizeof(SortWS) + sizeof(uint32_t) * 2 * 256 * (size_t)sort_max_parts(capacity) + 256;
+}
+
+// Enqueue a radix sort of the first *d_n pairs by key bits [begin_bit,
+// begin_bit + 8 passes); tells whether the result is in the alt buffers.
+template <typename K>
+static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
+                            const uint64_t *d_n, uint64_t capacity, int begin_bit, int passes,
+                            SortWS *ws, mg_status_word *st, cudaStream_t s, bool *in_alt) {
+    *in_alt = (passes & 1) != 0;
+    if (cudaMemsetAsync(&ws->hist[0][0], 0, sizeof(ws->hist) + sizeof(ws->counter), s) !=
+        cudaSuccess)
+        return MG_ERR_CUDA;
+    if (capacity == 0 || passes == 0) return MG_OK;
+    const int sms = sm_count();
+    const int64_t max_parts = sort_max_parts(capacity);
+    sort_histogram_kernel<K><<<sms * 4, 256, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws,
+                                                     max_parts);
+    sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<K>, kSortThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = (int64_t)sms * per_sm < max_parts ? (int64_t)sms * per_sm : max_parts;
+    K *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        onesweep_kernel<K><<<(unsigned)grid, kSortThreads, 0, s>>>(
+            kin, vin, kout, vout, d_n, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
+        K *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+    }
+    return MG_OK;
+}
+
 }  // namespace mg
 
 using namespace mg;
 
-static int64_t sort_max_parts(uint64_t capacity) {
-    return (int64_t)((capacity + kSortPart - 1) / kSortPart) + 1;
+extern "C" size_t mg_depth_order_workspace_bytes(int64_t n_records) {
+    return sort_ws_bytes((uint64_t)(n_records > 0 ? n_records : 0));
+}
+
+extern "C" mg_status mg_depth_order(const mg_splats *splats, const mg_view *views,
+                                    int32_t n_views, const mg_raster_cfg *cfg, uint32_t *order,
+                                    uint32_t *order_alt, uint32_t *keys, uint32_t *keys_alt,
+                                    void *workspace, size_t workspace_bytes,
+                                    mg_status_word *d_status, mg_stream_t stream) {
+    if (splats == nullptr || !splats->record || !splats->tiles_touched || !workspace)
+        return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    const int64_t R = vt.rec_off[n_views];
+    if (R == 0) return MG_OK;
+    if (!order || !order_alt || !keys || !keys_alt) return MG_ERR_INVALID_ARG;
+    if (R > (int64_t)kValMask) return MG_ERR_INVALID_ARG;
+    if (workspace_bytes < mg_depth_order_workspace_bytes(R)) return MG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    SortWS *ws = reinterpret_cast<SortWS *>(workspace);
+    depth_keys_kernel<<<sm_count() * 4, 256, 0, s>>>(splats->record, splats->tiles_touched, R,
+                                                      keys, order, &ws->n);
+    bool in_alt = false;
+    // 4 passes (an even number): the result is back in (keys, order)
+    st = radix_sort<uint32_t>(keys, order, keys_alt, order_alt, &ws->n, (uint64_t)R, 0, 4, ws,
+                              d_status, s, &in_alt);
+    if (st != MG_OK) return st;
+    return mg_host::launch_status();
 }
 
 extern "C" size_t mg_bin_workspace_bytes(int64_t n_records) {
@@ -400,14 +499,14 @@ extern "C" size_t mg_bin_workspace_bytes(int64_t n_records) {
 
 extern "C" size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits) {
     (void)key_bits;
-    return sizeof(SortWS) + sizeof(uint32_t) * 2 * 256 * (size_t)sort_max_parts(capacity) + 256;
+    return sort_ws_bytes(capacity);
 }
 
 extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
-                            const mg_raster_cfg *cfg, uint32_t *offsets, uint64_t *keys,
-                            uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
-                            void *workspace, size_t workspace_bytes, mg_status_word *d_status,
-                            mg_stream_t stream) {
+                            const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
+                            uint64_t *keys, uint32_t *vals, uint64_t capacity,
+                            uint64_t *d_num_instances, void *workspace, size_t workspace_bytes,
+                            mg_status_word *d_status, mg_stream_t stream) {
     if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
         !offsets || !d_num_instances || !workspace)
         return MG_ERR_INVALID_ARG;
@@ -430,56 +529,44 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
             return MG_ERR_CUDA;
         return MG_OK;
     }
-    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, R, offsets,
+    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, order, R, offsets,
                                                          d_num_instances, capacity, ws, parts,
                                                          d_status);
     if (capacity > 0)
         duplicate_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(
-            vt, splats->record, splats->radius, splats->tiles_touched, offsets, R, keys, vals,
-            capacity);
+            vt, splats->record, splats->radius, splats->tiles_touched, order, offsets, R, keys,
+            vals, capacity);
     return mg_host::launch_status();
 }
 
 extern "C" mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                              uint32_t *vals_alt, const uint64_t *d_num_instances,
-                             uint64_t capacity, int32_t key_bits, uint32_t *ranges,
-                             int64_t n_tiles_total, void *workspace, size_t workspace_bytes,
-                             int32_t *result_in_alt, mg_status_word *d_status,
-                             mg_stream_t stream) {
+                             uint64_t capacity, int32_t begin_bit, int32_t key_bits,
+                             uint32_t *ranges, int64_t n_tiles_total, void *workspace,
+                             size_t workspace_bytes, int32_t *result_in_alt,
+                             mg_status_word *d_status, mg_stream_t stream) {
     if (!keys || !vals || !keys_alt || !vals_alt || !d_num_instances || !ranges || !workspace ||
-        !result_in_alt || key_bits < 33 || key_bits > 64 || n_tiles_total <= 0)
+        !result_in_alt || key_bits < 33 || key_bits > 64 || begin_bit < 0 || begin_bit > 32 ||
+        n_tiles_total <= 0)
         return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
     if (workspace_bytes < mg_sort_workspace_bytes(capacity, key_bits)) return MG_ERR_INVALID_ARG;
     if ((n_tiles_total >> 32) != 0) return MG_ERR_INVALID_ARG;
-    const int passes = (key_bits + 7) / 8;
-    *result_in_alt = passes & 1;
+    const int passes = (key_bits - begin_bit + 7) / 8;
+    if (passes > kMaxPasses) return MG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     SortWS *ws = reinterpret_cast<SortWS *>(workspace);
-    const int64_t max_parts = sort_max_parts(capacity);
-    if (cudaMemsetAsync(ws, 0, offsetof(SortWS, status), s) != cudaSuccess) return MG_ERR_CUDA;
     if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) !=
         cudaSuccess)
         return MG_ERR_CUDA;
-    if (capacity == 0) return MG_OK;
-    const int sms = sm_count();
-    sort_histogram_kernel<<<sms * 4, 256, 0, s>>>(keys, d_num_instances, capacity, passes, ws,
-                                                  max_parts);
-    sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kSortThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    const int64_t grid = (int64_t)sms * per_sm < max_parts ? (int64_t)sms * per_sm : max_parts;
-    uint64_t *kin = keys, *kout = keys_alt;
-    uint32_t *vin = vals, *vout = vals_alt;
-    for (int p = 0; p < passes; ++p) {
-        onesweep_kernel<<<(unsigned)grid, kSortThreads, 0, s>>>(kin, vin, kout, vout,
-                                                                d_num_instances, capacity, p,
-                                                                8 * p, ws, max_parts, d_status);
-        uint64_t *tk = kin; kin = kout; kout = tk;
-        uint32_t *tv = vin; vin = vout; vout = tv;
-    }
-    ranges_kernel<<<sms * 4, 256, 0, s>>>(kin, d_num_instances, capacity, ranges, n_tiles_total);
+    bool in_alt = false;
+    mg_status st = radix_sort<uint64_t>(keys, vals, keys_alt, vals_alt, d_num_instances, capacity,
+                                        begin_bit, passes, ws, d_status, s, &in_alt);
+    if (st != MG_OK) return st;
+    *result_in_alt = in_alt ? 1 : 0;
+    if (capacity == 0) return mg_host::launch_status();
+    ranges_kernel<<<sm_count() * 4, 256, 0, s>>>(in_alt ? keys_alt : keys, d_num_instances,
+                                                 capacity, ranges, n_tiles_total);
     return mg_host::launch_status();
 }
 
@@ -493,8 +580,6 @@ extern "C" mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
 // for at most kNoAllocMaxRecords splat records; every GPU that loads the
 // library holds it until the process exits.  No allocation happens here.
 // --------------------------------------------------------------------------
-#include <mutex>
-
 namespace {
 
 constexpr int64_t kNoAllocMaxRecords = int64_t(1) << 24;
@@ -528,10 +613,10 @@ mg_status bin_scratch_address(void **out) {
 }  // namespace
 
 extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views,
-                                    int32_t n_views, const mg_raster_cfg *cfg, uint32_t *offsets,
-                                    uint64_t *keys, uint32_t *vals, uint64_t capacity,
-                                    uint64_t *d_num_instances, mg_status_word *d_status,
-                                    mg_stream_t stream) {
+                                    int32_t n_views, const mg_raster_cfg *cfg,
+                                    const uint32_t *order, uint32_t *offsets, uint64_t *keys,
+                                    uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
+                                    mg_status_word *d_status, mg_stream_t stream) {
     if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
         !offsets || !d_num_instances)
         return MG_ERR_INVALID_ARG;
@@ -559,12 +644,12 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
             return MG_ERR_CUDA;
         return MG_OK;
     }
-    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, R, offsets,
+    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, order, R, offsets,
                                                          d_num_instances, capacity, ws, parts,
                                                          d_status);
     if (capacity > 0)
         duplicate_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(
-            vt, splats->record, splats->radius, splats->tiles_touched, offsets, R, keys, vals,
-            capacity);
+            vt, splats->record, splats->radius, splats->tiles_touched, order, offsets, R, keys,
+            vals, capacity);
     return mg_host::launch_status();
 }

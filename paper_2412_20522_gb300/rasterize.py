@@ -157,18 +157,24 @@ class Rasterizer:
         ev.begin("preprocess")
         abi.mg_preprocess(g, views, V, ccfg, splats, self.status, stream)
         ev.end("preprocess")
+        # depth order of the records, then instances in that order
+        order = self._get("order", R, torch.int32)
+        dws = self._get("depth_ws", abi.mg_depth_order_workspace_bytes(R), torch.uint8)
+        ev.begin("bin")
+        abi.mg_depth_order(splats, views, V, ccfg, order, self._get("order_alt", R, torch.int32),
+                           self._get("dkeys", R, torch.int32), self._get("dkeys_alt", R, torch.int32),
+                           dws, dws.numel(), self.status, stream)
         offsets = self._get("offsets", R, torch.int32)
         bin_ws = self._get("bin_ws", abi.mg_bin_workspace_bytes(R), torch.uint8)
         if self.capacity <= 0:
             # size the instance buffers from this step's own count
-            abi.mg_bin(splats, views, V, ccfg, offsets, None, None, 0, self.num_instances,
+            abi.mg_bin(splats, views, V, ccfg, order, offsets, None, None, 0, self.num_instances,
                        bin_ws, bin_ws.numel(), self.status, stream)
             k = int(self.num_instances.item())
             self.capacity = max(int(k * self.headroom), 1024)
             self.status.zero_()
         self._ensure_sort_buffers(self.capacity, key_bits)
-        ev.begin("bin")
-        abi.mg_bin(splats, views, V, ccfg, offsets, self._buf["keys"], self._buf["vals"],
+        abi.mg_bin(splats, views, V, ccfg, order, offsets, self._buf["keys"], self._buf["vals"],
                    self.capacity, self.num_instances, bin_ws, bin_ws.numel(), self.status, stream)
         ev.end("bin")
         if check:
@@ -177,16 +183,17 @@ class Rasterizer:
                 self.capacity = int(st.required * self.headroom) + 1024
                 self._ensure_sort_buffers(self.capacity, key_bits)
                 self.status.zero_()
-                abi.mg_bin(splats, views, V, ccfg, offsets, self._buf["keys"], self._buf["vals"],
-                           self.capacity, self.num_instances, bin_ws, bin_ws.numel(),
-                           self.status, stream)
+                abi.mg_bin(splats, views, V, ccfg, order, offsets, self._buf["keys"],
+                           self._buf["vals"], self.capacity, self.num_instances, bin_ws,
+                           bin_ws.numel(), self.status, stream)
             elif st.status != abi.MG_OK:
                 raise abi.MaskgsError("mg_bin", st.status)
         ranges_buf = self._get("ranges", 2 * tiles, torch.int32)
         sort_ws = self._buf["sort_ws"]
         ev.begin("sort")
+        # instances arrive in depth order: a stable sort on the tile bits suffices
         alt = abi.mg_sort(self._buf["keys"], self._buf["vals"], self._buf["keys_alt"],
-                          self._buf["vals_alt"], self.num_instances, self.capacity, key_bits,
+                          self._buf["vals_alt"], self.num_instances, self.capacity, 32, key_bits,
                           ranges_buf, tiles, sort_ws, sort_ws.numel(), self.status, stream)
         ev.end("sort")
         sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
@@ -199,9 +206,10 @@ class Rasterizer:
         abi.mg_render(splats, sorted_vals, ranges_buf, views, V, ccfg, image, final_T, n_contrib,
                       self.frag_count if count_fragments else None, stream)
         ev.end("render")
-        # kernels of ours per forward: preprocess; scan + duplicate; histogram,
-        # offsets, one per digit pass, ranges; render
-        self._fwd_launches = 1 + 2 + 3 + (key_bits + 7) // 8 + 1
+        # kernels of ours per forward: preprocess; depth keys, histogram,
+        # offsets, 4 digit passes; scan, duplicate; histogram, offsets, one per
+        # tile digit pass, ranges; render
+        self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits - 32 + 7) // 8 + 1
         self._state = dict(g=g, views=views, V=V, cfg=ccfg, splats=splats, R=R, n=n, pix=pix,
                            sorted_vals=sorted_vals, ranges=ranges_buf, tiles=tiles,
                            sh_degree=sh_degree, params=params, cams=cams)
@@ -257,7 +265,7 @@ class Rasterizer:
     def splat_outputs(self):
         s = self._state
         R, n = s["R"], s["n"]
-        return dict(record=self._buf["record"][:R * 12].view(R, 12),
+        return dict(record=self._buf["record"][:R * 12].view(R, 12), order=self._buf["order"][:R],
                     tiles=self._buf["tiles"][:R], radius=self._buf["radius"][:R],
                     clamp=self._buf["clamp"][:R], mask=self._buf["mask"][:n],
                     mask_soft=self._buf["mask_soft"][:n], offsets=self._buf["offsets"][:R],

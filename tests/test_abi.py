@@ -39,7 +39,8 @@ def test_binding_names_match_header():
     assert sorted(abi.EXPORTED) == _declared()
     for n in _declared():
         if n not in ("mg_status_string", "mg_version", "mg_bin_workspace_bytes",
-                     "mg_sort_workspace_bytes", "mg_key_bits", "mg_total_tiles"):
+                     "mg_sort_workspace_bytes", "mg_key_bits", "mg_total_tiles",
+                     "mg_depth_order_workspace_bytes"):
             assert callable(getattr(abi, n))
 
 
@@ -79,6 +80,6 @@ def test_bad_arguments_rejected_on_host(lib):
                        None, None)
     assert st == abi.MG_ERR_INVALID_ARG
     alt = C.c_int32(0)
-    st = lib.mg_sort(None, None, None, None, None, 0, 20, None, 1, None, 0, C.byref(alt), None,
+    st = lib.mg_sort(None, None, None, None, None, 0, 32, 20, None, 1, None, 0, C.byref(alt), None,
                      None)
     assert st == abi.MG_ERR_INVALID_ARG

@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from gpu_helpers import rel_l2, to_device
-from oracle import pipeline
+from oracle import binning, pipeline
 from paper_2412_20522_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +33,8 @@ def test_scene_scale_single_view():
     assert np.array_equal(so["mask"].cpu().numpy(), M)
     assert np.array_equal(so["tiles"].cpu().numpy().view(np.uint32), v.fp32["tiles"])
     assert np.array_equal(so["radius"].cpu().numpy(), v.fp32["radius"])
+    order = binning.depth_order(v.fp32["depth_bits"], v.fp32["visible"])
+    assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order)
     K = int(so["num_instances"].item())
     assert K == v.K
     keys = rast.sorted_keys().cpu().numpy().view(np.uint64)[:K]

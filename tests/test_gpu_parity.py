@@ -16,7 +16,7 @@ import pytest
 import torch
 
 from gpu_helpers import rel_l2, split_views, to_device
-from oracle import pipeline
+from oracle import binning, pipeline
 from paper_2412_20522_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -55,10 +55,17 @@ def _oracle(g, cams, cfg_kw=None, tile=(16, 16)):
 def _check_discrete(rast, views, M, cams):
     so = rast.splat_outputs()
     assert np.array_equal(so["mask"].cpu().numpy(), M), "sampled masks differ"
+    # depth order of all records (all views), and the scan in that order
+    tiles_all = np.concatenate([v.fp32["tiles"] for v in views]).astype(np.int64)
+    order = binning.depth_order(np.concatenate([v.fp32["depth_bits"] for v in views]),
+                                np.concatenate([v.fp32["visible"] for v in views]))
+    assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order), "depth order differs"
+    exp_off = np.concatenate([[0], np.cumsum(tiles_all[order])[:-1]]) if order.size else order
+    assert np.array_equal(so["offsets"].cpu().numpy().view(np.uint32).astype(np.int64), exp_off), \
+        "scan offsets differ"
     rec = so["record"].cpu().numpy()
     tiles = so["tiles"].cpu().numpy().view(np.uint32)
     radius = so["radius"].cpu().numpy()
-    offs = so["offsets"].cpu().numpy().view(np.uint32)
     K_gpu = int(so["num_instances"].item())
     R0 = 0
     T0 = 0
@@ -76,8 +83,6 @@ def _check_discrete(rast, views, M, cams):
         assert np.array_equal(r[vis, 0].view(np.uint32), fp["px"][vis].view(np.uint32))
         assert np.array_equal(r[vis, 1].view(np.uint32), fp["py"][vis].view(np.uint32))
         assert np.array_equal(r[vis, 11].view(np.uint32), fp["depth_bits"][vis])
-        assert np.array_equal(offs[R0:R0 + n].astype(np.uint64),
-                              v.offsets.astype(np.uint64) + np.uint64(K0)), "scan offsets differ"
         nt = v.ranges.shape[0]
         # the oracle's keys are per view: shift its tile ids by the view's tile offset
         okeys = v.sorted_keys + (np.uint64(T0) << np.uint64(32))

@@ -21,8 +21,9 @@ def _splat(g, cams):
     return rast
 
 
-def _bin(abi, rast, noalloc):
+def _bin(abi, rast, noalloc, ordered=True):
     s = rast._state
+    order = rast.splat_outputs()["order"] if ordered else None
     R = s["R"]
     dev = rast.device
     cap = rast.capacity
@@ -33,12 +34,12 @@ def _bin(abi, rast, noalloc):
     status = torch.zeros(2, dtype=torch.int64, device=dev)
     stream = rast._stream()
     if noalloc:
-        abi.mg_bin_noalloc(s["splats"], s["views"], s["V"], s["cfg"], offsets, keys, vals, cap, n,
-                           status, stream)
+        abi.mg_bin_noalloc(s["splats"], s["views"], s["V"], s["cfg"], order, offsets, keys, vals,
+                           cap, n, status, stream)
     else:
         ws = torch.empty(abi.mg_bin_workspace_bytes(R), dtype=torch.uint8, device=dev)
-        abi.mg_bin(s["splats"], s["views"], s["V"], s["cfg"], offsets, keys, vals, cap, n, ws,
-                   ws.numel(), status, stream)
+        abi.mg_bin(s["splats"], s["views"], s["V"], s["cfg"], order, offsets, keys, vals, cap, n,
+                   ws, ws.numel(), status, stream)
     torch.cuda.synchronize()
     k = int(n.item())
     assert int(status[0].item()) == 0
@@ -55,14 +56,15 @@ def test_noalloc_matches_workspace_binning_twice(which):
         cams = [scenes.ring_camera(0.0, 4.0, 300, 200, 230.0),
                 scenes.ring_camera(1.0, 4.0, 200, 150, 180.0)]
     rast = _splat(g, cams)
-    ref = _bin(abi, rast, noalloc=False)
-    assert ref[1] > 0
-    for _ in range(2):
-        got = _bin(abi, rast, noalloc=True)
-        assert got[1] == ref[1]
-        assert np.array_equal(got[0], ref[0])
-        assert np.array_equal(got[2], ref[2])
-        assert np.array_equal(got[3], ref[3])
+    for ordered in (True, False):
+        ref = _bin(abi, rast, noalloc=False, ordered=ordered)
+        assert ref[1] > 0
+        for _ in range(2):
+            got = _bin(abi, rast, noalloc=True, ordered=ordered)
+            assert got[1] == ref[1]
+            assert np.array_equal(got[0], ref[0])
+            assert np.array_equal(got[2], ref[2])
+            assert np.array_equal(got[3], ref[3])
 
 
 def test_noalloc_rejects_more_records_than_its_array_holds():
@@ -77,8 +79,8 @@ def test_noalloc_rejects_more_records_than_its_array_holds():
     big = make_views(cams, [(0, (1 << 24) + 1)])
     # the size check comes first: nothing is launched for an oversized request
     with pytest.raises(abi.MaskgsError) as e:
-        abi.mg_bin_noalloc(s["splats"], big, 1, RasterConfig().c(), offsets, None, None, 0, n,
-                           None, rast._stream())
+        abi.mg_bin_noalloc(s["splats"], big, 1, RasterConfig().c(), None, offsets, None, None, 0,
+                           n, None, rast._stream())
     assert e.value.status == abi.MG_ERR_INVALID_ARG
-    assert abi.load().mg_bin_noalloc(None, ok, 1, RasterConfig().c(), None, None, None, 0, None,
-                                     None, None) == abi.MG_ERR_INVALID_ARG
+    assert abi.load().mg_bin_noalloc(None, ok, 1, RasterConfig().c(), None, None, None, None, 0,
+                                     None, None, None) == abi.MG_ERR_INVALID_ARG
