@@ -2,8 +2,8 @@
 // splat of every Gaussian (Sec. 3.1) for every view.
 //
 // One thread per Gaussian; the attributes are read once and reused for all
-// views that see the Gaussian.  The SH block of a warp's 32 Gaussians is
-// staged through shared memory with 128-bit coalesced loads.
+// views that see the Gaussian.  SH rows (the bulk of the bytes) are read only
+// for Gaussians visible in some view, with 128-bit loads.
 //
 // Decisions (cull, radius, tile rectangle, depth key, mask) use a fixed
 // sequence of correctly rounded FP32 operations (__fadd_rn, __fmul_rn, ...),
@@ -20,33 +20,6 @@ constexpr int kPreThreads = 128;
 
 template <int ROW>
 struct StageStride { static constexpr int value = (ROW % 2 == 0) ? ROW + 1 : ROW; };
-
-// Copy rows [row0, row0 + nrows) of a row-major [*, ROW] array to shared
-// memory with an odd row stride (conflict-free per-lane reads).
-template <int ROW>
-__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int64_t row0, int nrows,
-                                           float *sm, int lane) {
-    constexpr int S = StageStride<ROW>::value;
-    const float *base = src + row0 * ROW;
-    const int total = nrows * ROW;
-    int done = 0;
-    if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
-        const float4 *b4 = reinterpret_cast<const float4 *>(base);
-        const int n4 = total >> 2;
-        for (int q = lane; q < n4; q += 32) {
-            const float4 v = __ldg(b4 + q);
-            const float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int f = 4 * q + k;
-                sm[(f / ROW) * S + (f % ROW)] = e[k];
-            }
-        }
-        done = n4 << 2;
-    }
-    for (int f = done + lane; f < total; f += 32) sm[(f / ROW) * S + (f % ROW)] = __ldg(base + f);
-    __syncwarp();
-}
 
 struct Splat32 {
     // decision-path quantities
@@ -165,20 +138,36 @@ __device__ __forceinline__ void eigen2(const Splat32 &S, float &uxo, float &uyo,
     }
 }
 
+// sum_k Y_k sh[i][k][ch] for the three channels, streaming the Gaussian's SH
+// row from global memory (128-bit loads when the row is 16-byte aligned).
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const float *__restrict__ sh, int64_t i, const float *Y,
+                                          float acc[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int ROW = 3 * K;
+    if constexpr (ROW % 4 == 0) {
+        const float4 *row = reinterpret_cast<const float4 *>(sh) + i * (ROW / 4);
+#pragma unroll
+        for (int q = 0; q < ROW / 4; ++q) {
+            const float4 v = __ldg(row + q);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[(4 * q + u) % 3] = fmaf(Y[(4 * q + u) / 3], e[u], acc[(4 * q + u) % 3]);
+        }
+    } else {
+        const float *row = sh + i * ROW;
+#pragma unroll
+        for (int f = 0; f < ROW; ++f) acc[f % 3] = fmaf(Y[f / 3], __ldg(row + f), acc[f % 3]);
+    }
+}
+
+// The SH rows are read only for Gaussians that are visible in a view, one
+// row per lane with 128-bit loads (no row of an invisible Gaussian is read).
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int ROW = 3 * K;
-    constexpr int S_ = StageStride<ROW>::value;
-    __shared__ float sm_sh[kPreThreads / 32][32 * S_];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t gw0 = ((int64_t)blockIdx.x * kPreThreads) + warp * 32;
-    if (gw0 >= g.n) return;
-    const int nrows = (int)(g.n - gw0 < 32 ? g.n - gw0 : 32);
-    stage_rows<ROW>(g.sh, gw0, nrows, sm_sh[warp], lane);
-    const int64_t i = gw0 + lane;
-    if (lane >= nrows) return;
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
+    if (i >= g.n) return;
 
     // --- mask sample (Sec. 3.3): Gumbel-max over the two existence scores
     float Mf = 1.0f;
@@ -205,7 +194,6 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
     const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
     const float q[4] = {q4.x, q4.y, q4.z, q4.w};
     const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
-    const float *shr = sm_sh[warp] + lane * S_;
 
     for (int v = 0; v < vt.n_views; ++v) {
         if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
@@ -229,18 +217,15 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         dx *= inv; dy *= inv; dz *= inv;
         float Y[16];
         sh_basis(DEG, dx, dy, dz, Y);
-        float rgb[3];
+        float rgb[3] = {0.5f, 0.5f, 0.5f};
+        sh_colour<DEG>(g.sh, i, Y, rgb);
         uint8_t cl = 0;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.5f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], shr[3 * k + ch], acc);
-            if (acc < 0.0f) {
+            if (rgb[ch] < 0.0f) {
                 cl |= (uint8_t)(1u << ch);
-                acc = 0.0f;
+                rgb[ch] = 0.0f;
             }
-            rgb[ch] = acc;
         }
         out.clamp[r] = cl;
         float4 *rec = reinterpret_cast<float4 *>(out.record) + 3 * r;
@@ -433,6 +418,9 @@ __device__ __forceinline__ void cov_backward(const CovState<F> &S, const mg_came
     if (!clampy) dL_dt[1] += (float)(-dJ12 * fy * itz2);
 }
 
+// dL/dsh accumulates over views in a per-warp shared-memory tile (one row
+// per lane, odd row stride) and leaves with coalesced 128-bit stores; SH rows
+// are read only for Gaussians visible in some view.
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats sp,
@@ -440,123 +428,155 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int ROW = 3 * K;
     constexpr int S_ = StageStride<ROW>::value;
-    __shared__ float sm_sh[kPreThreads / 32][32 * S_];
+    __shared__ float sm_dsh[kPreThreads / 32][32 * S_];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw0 = ((int64_t)blockIdx.x * kPreThreads) + warp * 32;
     if (gw0 >= g.n) return;
     const int nrows = (int)(g.n - gw0 < 32 ? g.n - gw0 : 32);
-    stage_rows<ROW>(g.sh, gw0, nrows, sm_sh[warp], lane);
+    float *dsh = sm_dsh[warp];
+    for (int f = lane; f < 32 * S_; f += 32) dsh[f] = 0.0f;
+    __syncwarp();
     const int64_t i = gw0 + lane;
-    if (lane >= nrows) return;
-    const float *shr = sm_sh[warp] + lane * S_;
+    if (lane < nrows) {
+        float *drow = dsh + lane * S_;
+        const float x = __ldg(g.means + 3 * i), y = __ldg(g.means + 3 * i + 1),
+                    z = __ldg(g.means + 3 * i + 2);
+        const float ls[3] = {__ldg(g.log_scales + 3 * i), __ldg(g.log_scales + 3 * i + 1),
+                             __ldg(g.log_scales + 3 * i + 2)};
+        const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
+        const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+        const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
 
-    const float x = __ldg(g.means + 3 * i), y = __ldg(g.means + 3 * i + 1),
-                z = __ldg(g.means + 3 * i + 2);
-    const float ls[3] = {__ldg(g.log_scales + 3 * i), __ldg(g.log_scales + 3 * i + 1),
-                         __ldg(g.log_scales + 3 * i + 2)};
-    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
-    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
-    const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
+        float d_mean[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0}, d_op = 0.0f,
+              d_M = 0.0f;
+        for (int v = 0; v < vt.n_views; ++v) {
+            if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
+            const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
+            if (sp.radius[r] == 0) continue;
+            const float4 *G4 = reinterpret_cast<const float4 *>(grad2d) + 3 * r;
+            const float4 g0 = G4[0], g1 = G4[1], g2 = G4[2];
+            // g0 = (dmx, dmy, dca, dcb), g1 = (dcc, dop, dr, dg), g2 = (db, dM, -, -)
+            d_M += g2.y;
+            d_op += g1.y;
+            const mg_camera &C = vt.cam[v];
+            Splat32 S;
+            splat_fp32(C, vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z, ls, q, S);
+            const float *V = C.viewmat;
+            float dL_dt[3] = {0, 0, 0};   // camera-space centre
 
-    float d_mean[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0}, d_op = 0.0f,
-          d_M = 0.0f;
-    float d_sh[ROW];
+            // ---- colour: rgb_c = max(0, sum_k Y_k sh_kc + 0.5)
+            {
+                const float vx = x - C.cam_pos[0], vy = y - C.cam_pos[1], vz = z - C.cam_pos[2];
+                const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+                const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
+                float Y[16];
+                sh_basis(DEG, dx, dy, dz, Y);
+                const uint8_t cl = sp.clamp[r];
+                const float grgb[3] = {(cl & 1) ? 0.0f : g1.z, (cl & 2) ? 0.0f : g1.w,
+                                       (cl & 4) ? 0.0f : g2.x};
 #pragma unroll
-    for (int k = 0; k < ROW; ++k) d_sh[k] = 0.0f;
-
-    for (int v = 0; v < vt.n_views; ++v) {
-        if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
-        const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
-        if (sp.radius[r] == 0) continue;
-        const float4 *G4 = reinterpret_cast<const float4 *>(grad2d) + 3 * r;
-        const float4 g0 = G4[0], g1 = G4[1], g2 = G4[2];
-        // g0 = (dmx, dmy, dca, dcb), g1 = (dcc, dop, dr, dg), g2 = (db, dM, -, -)
-        d_M += g2.y;
-        d_op += g1.y;
-        const mg_camera &C = vt.cam[v];
-        Splat32 S;
-        splat_fp32(C, vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z, ls, q, S);
-        const float *V = C.viewmat;
-        float dL_dt[3] = {0, 0, 0};   // camera-space centre
-
-        // ---- colour: rgb_c = max(0, sum_k Y_k sh_kc + 0.5)
-        {
-            const float vx = x - C.cam_pos[0], vy = y - C.cam_pos[1], vz = z - C.cam_pos[2];
-            const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-            const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
-            float Y[16];
-            sh_basis(DEG, dx, dy, dz, Y);
-            const uint8_t cl = sp.clamp[r];
-            const float grgb[3] = {(cl & 1) ? 0.0f : g1.z, (cl & 2) ? 0.0f : g1.w,
-                                   (cl & 4) ? 0.0f : g2.x};
+                for (int k = 0; k < K; ++k)
 #pragma unroll
-            for (int k = 0; k < K; ++k)
+                    for (int ch = 0; ch < 3; ++ch) drow[3 * k + ch] = fmaf(Y[k], grgb[ch], drow[3 * k + ch]);
+                if (DEG > 0) {
+                    // t_k = sum_c grgb_c sh_kc, streamed from the SH row
+                    float t[16];
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) d_sh[3 * k + ch] = fmaf(Y[k], grgb[ch], d_sh[3 * k + ch]);
-            if (DEG > 0) {
-                float Yx[16], Yy[16], Yz[16];
-                sh_basis_grad(DEG, dx, dy, dz, Yx, Yy, Yz);
-                float gd[3] = {0, 0, 0};
+                    for (int k = 0; k < 16; ++k) t[k] = 0.0f;
+                    if constexpr (ROW % 4 == 0) {
+                        const float4 *row = reinterpret_cast<const float4 *>(g.sh) + i * (ROW / 4);
 #pragma unroll
-                for (int k = 1; k < K; ++k) {
-                    const float t = grgb[0] * shr[3 * k] + grgb[1] * shr[3 * k + 1] +
-                                    grgb[2] * shr[3 * k + 2];
-                    gd[0] = fmaf(t, Yx[k], gd[0]);
-                    gd[1] = fmaf(t, Yy[k], gd[1]);
-                    gd[2] = fmaf(t, Yz[k], gd[2]);
+                        for (int qq = 0; qq < ROW / 4; ++qq) {
+                            const float4 sv = __ldg(row + qq);
+                            const float e[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                t[(4 * qq + u) / 3] = fmaf(grgb[(4 * qq + u) % 3], e[u], t[(4 * qq + u) / 3]);
+                        }
+                    } else {
+                        const float *row = g.sh + i * ROW;
+#pragma unroll
+                        for (int f = 0; f < ROW; ++f) t[f / 3] = fmaf(grgb[f % 3], __ldg(row + f), t[f / 3]);
+                    }
+                    float Yx[16], Yy[16], Yz[16];
+                    sh_basis_grad(DEG, dx, dy, dz, Yx, Yy, Yz);
+                    float gd[3] = {0, 0, 0};
+#pragma unroll
+                    for (int k = 1; k < K; ++k) {
+                        gd[0] = fmaf(t[k], Yx[k], gd[0]);
+                        gd[1] = fmaf(t[k], Yy[k], gd[1]);
+                        gd[2] = fmaf(t[k], Yz[k], gd[2]);
+                    }
+                    // through dir = v / |v|
+                    const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+                    d_mean[0] += (gd[0] - dot * dx) * inv;
+                    d_mean[1] += (gd[1] - dot * dy) * inv;
+                    d_mean[2] += (gd[2] - dot * dz) * inv;
                 }
-                // through dir = v / |v|
-                const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
-                d_mean[0] += (gd[0] - dot * dx) * inv;
-                d_mean[1] += (gd[1] - dot * dy) * inv;
-                d_mean[2] += (gd[2] - dot * dz) * inv;
             }
-        }
 
-        // ---- 2D mean: px = fx tx/tz + cx, py = fy ty/tz + cy
-        {
-            const float itz = 1.0f / S.tzs;
-            dL_dt[0] += g0.x * C.fx * itz;
-            dL_dt[1] += g0.y * C.fy * itz;
-            dL_dt[2] -= (g0.x * C.fx * S.ux + g0.y * C.fy * S.uy) * itz;
-        }
+            // ---- 2D mean: px = fx tx/tz + cx, py = fy ty/tz + cy
+            {
+                const float itz = 1.0f / S.tzs;
+                dL_dt[0] += g0.x * C.fx * itz;
+                dL_dt[1] += g0.y * C.fy * itz;
+                dL_dt[2] -= (g0.x * C.fx * S.ux + g0.y * C.fy * S.uy) * itz;
+            }
 
-        // ---- conic -> Sigma_bar -> P = J W R S -> scales, rotation, J
-        float ux, uy, l1, l2;
-        eigen2(S, ux, uy, l1, l2);
-        if (l1 > kFp64Condition * l2) {
-            // needle splat: the FP32 factor cannot resolve its thin direction
-            CovState<double> D;
-            cov_state_fp64(C, x, y, z, ls, q, S.clampx, S.clampy, D);
-            cov_backward<double>(D, C, S.clampx, S.clampy, g0.z, g0.w, g1.x, d_ls, d_q, dL_dt);
-        } else {
-            CovState<float> F;
-            cov_state_fp32(S, ux, uy, l1, l2, F);
-            cov_backward<float>(F, C, S.clampx, S.clampy, g0.z, g0.w, g1.x, d_ls, d_q, dL_dt);
-        }
-        // t = W p + t_cam  =>  dp += W^T dt
+            // ---- conic -> Sigma_bar -> P = J W R S -> scales, rotation, J
+            float ux, uy, l1, l2;
+            eigen2(S, ux, uy, l1, l2);
+            if (l1 > kFp64Condition * l2) {
+                // needle splat: the FP32 factor cannot resolve its thin direction
+                CovState<double> D;
+                cov_state_fp64(C, x, y, z, ls, q, S.clampx, S.clampy, D);
+                cov_backward<double>(D, C, S.clampx, S.clampy, g0.z, g0.w, g1.x, d_ls, d_q, dL_dt);
+            } else {
+                CovState<float> F;
+                cov_state_fp32(S, ux, uy, l1, l2, F);
+                cov_backward<float>(F, C, S.clampx, S.clampy, g0.z, g0.w, g1.x, d_ls, d_q, dL_dt);
+            }
+            // t = W p + t_cam  =>  dp += W^T dt
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            d_mean[k] += V[k] * dL_dt[0] + V[4 + k] * dL_dt[1] + V[8 + k] * dL_dt[2];
-    }
+            for (int k = 0; k < 3; ++k)
+                d_mean[k] += V[k] * dL_dt[0] + V[4 + k] * dL_dt[1] + V[8 + k] * dL_dt[2];
+        }
 
-    out.means[3 * i] = d_mean[0];
-    out.means[3 * i + 1] = d_mean[1];
-    out.means[3 * i + 2] = d_mean[2];
-    out.log_scales[3 * i] = d_ls[0];
-    out.log_scales[3 * i + 1] = d_ls[1];
-    out.log_scales[3 * i + 2] = d_ls[2];
-    reinterpret_cast<float4 *>(out.quats)[i] = make_float4(d_q[0], d_q[1], d_q[2], d_q[3]);
-    out.opacity_logit[i] = d_op * op * (1.0f - op);
-    float *dsh = out.sh + (int64_t)ROW * i;
-#pragma unroll
-    for (int k = 0; k < ROW; ++k) dsh[k] = d_sh[k];
-    float dl0 = 0.0f;
-    if (cfg.mask_mode == MG_MASK_GUMBEL) {
-        const float y0 = sp.mask_soft[i];
-        dl0 = d_M * y0 * (1.0f - y0) / cfg.tau;
+        out.means[3 * i] = d_mean[0];
+        out.means[3 * i + 1] = d_mean[1];
+        out.means[3 * i + 2] = d_mean[2];
+        out.log_scales[3 * i] = d_ls[0];
+        out.log_scales[3 * i + 1] = d_ls[1];
+        out.log_scales[3 * i + 2] = d_ls[2];
+        reinterpret_cast<float4 *>(out.quats)[i] = make_float4(d_q[0], d_q[1], d_q[2], d_q[3]);
+        out.opacity_logit[i] = d_op * op * (1.0f - op);
+        float dl0 = 0.0f;
+        if (cfg.mask_mode == MG_MASK_GUMBEL) {
+            const float y0 = sp.mask_soft[i];
+            dl0 = d_M * y0 * (1.0f - y0) / cfg.tau;
+        }
+        reinterpret_cast<float2 *>(out.mask_logits)[i] = make_float2(dl0, -dl0);
     }
-    reinterpret_cast<float2 *>(out.mask_logits)[i] = make_float2(dl0, -dl0);
+    __syncwarp();
+    // ---- the warp's dL/dsh rows are contiguous in global memory
+    float *dst = out.sh + gw0 * ROW;
+    const int total = nrows * ROW;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        const int n4 = total >> 2;
+        for (int qq = lane; qq < n4; qq += 32) {
+            float e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = 4 * qq + u;
+                e[u] = dsh[(f / ROW) * S_ + (f % ROW)];
+            }
+            d4[qq] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+        done = n4 << 2;
+    }
+    for (int f = done + lane; f < total; f += 32) dst[f] = dsh[(f / ROW) * S_ + (f % ROW)];
 }
 
 }  // namespace mg
