@@ -194,14 +194,13 @@ size_t mg_depth_order_workspace_bytes(int64_t n_records);
 /* Visits the R records in `order` (nullable: record order) and writes, for
  * position i, offsets[i] = sum_{j<i} tiles_touched[order[j]] (u32) and the
  * total K into *d_num_instances (device u64); then, for every visible record
- * r = order[i] and every tile of its rectangle (row-major), the key
- * (global tile id << 32) | float bits of depth and the value r at
- * offsets[i] + k.  Instances beyond `capacity` are not written and raise
+ * r = order[i] and every tile of its rectangle (row-major), the key = global
+ * tile id (u32) and the value r at offsets[i] + k.  Instances beyond `capacity` are not written and raise
  * MG_ERR_CAPACITY with `required` = K.  workspace: device scratch of
  * mg_bin_workspace_bytes(R) bytes, any content. */
 mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
                  const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
-                 uint64_t *keys, uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
+                 uint32_t *keys, uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
                  void *workspace, size_t workspace_bytes, mg_status_word *d_status,
                  mg_stream_t stream);
 size_t mg_bin_workspace_bytes(int64_t n_records);
@@ -221,32 +220,31 @@ size_t mg_bin_workspace_bytes(int64_t n_records);
  * cudaFree. */
 mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views, int32_t n_views,
                          const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
-                         uint64_t *keys, uint32_t *vals, uint64_t capacity,
+                         uint32_t *keys, uint32_t *vals, uint64_t capacity,
                          uint64_t *d_num_instances, mg_status_word *d_status,
                          mg_stream_t stream);
 
 /* ---- 3. sort + tile ranges (Sec. 3.1) -------------------------------------- */
 /* Stable LSD radix sort (8-bit digits, single-pass "onesweep" passes with
- * decoupled look-back) of the first *d_num_instances (key, value) pairs by
- * key bits [begin_bit, key_bits), then ranges[t] = [start, end) of the
- * instances of global tile t (n_tiles_total = sum of all views' tiles).
- * With instances emitted in depth order (mg_depth_order, then mg_bin), sort
- * the tile bits only (begin_bit = 32): each tile's list then comes out ordered
- * by (depth, record index), as a full sort (begin_bit = 0) of record-ordered
- * instances would order it.  The sorted pairs end in (keys, vals) when
- * *result_in_alt (host int) is set to 0, else in (keys_alt, vals_alt); it is
- * known on the host from the bit range alone.  When *d_num_instances exceeds
- * capacity (mg_bin raised MG_ERR_CAPACITY) nothing is sorted and every range
- * is empty.  workspace: mg_sort_workspace_bytes(capacity, key_bits) bytes,
- * any content.  key_bits: 33..64, begin_bit: 0..32; capacity < 2^30. */
-mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                  const uint64_t *d_num_instances, uint64_t capacity, int32_t begin_bit,
-                  int32_t key_bits, uint32_t *ranges, int64_t n_tiles_total, void *workspace,
+ * decoupled look-back) of the first *d_num_instances (tile id, value) pairs by
+ * the low key_bits bits of the tile id (mg_tile_bits), then ranges[t] =
+ * [start, end) of the instances of global tile t (n_tiles_total = sum of all
+ * views' tiles).  With the instances emitted in depth order (mg_depth_order,
+ * then mg_bin), each tile's list comes out ordered by (depth, record index).
+ * The sorted pairs end in (keys, vals) when *result_in_alt (host int) is set
+ * to 0, else in (keys_alt, vals_alt); it is known on the host from key_bits
+ * alone.  When *d_num_instances exceeds capacity (mg_bin raised
+ * MG_ERR_CAPACITY) nothing is sorted and every range is empty.  workspace:
+ * mg_sort_workspace_bytes(capacity, key_bits) bytes, any content.  key_bits:
+ * 1..32 with n_tiles_total <= 2^key_bits; capacity < 2^30. */
+mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                  const uint64_t *d_num_instances, uint64_t capacity, int32_t key_bits,
+                  uint32_t *ranges, int64_t n_tiles_total, void *workspace,
                   size_t workspace_bytes, int32_t *result_in_alt, mg_status_word *d_status,
                   mg_stream_t stream);
 size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);
-/* Number of key bits for a set of views: ceil(log2(n_tiles_total)) + 32. */
-int32_t mg_key_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
+/* Bits of a global tile id for a set of views: ceil(log2(n_tiles_total)), >= 1. */
+int32_t mg_tile_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
 int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
 
 /* ---- 4. render forward (Eq. 3-4) -------------------------------------------- */

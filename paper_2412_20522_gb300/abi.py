@@ -21,7 +21,7 @@ MG_GRAD2D_FLOATS = 12
 
 EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes", "mg_bin",
             "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
-            "mg_sort_workspace_bytes", "mg_key_bits", "mg_total_tiles", "mg_render",
+            "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_read_status", "mg_status_string", "mg_version")
 
@@ -102,10 +102,10 @@ def load(build_if_missing: bool = True):
         "mg_bin_noalloc": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp,
                                 vp, vp, vp, C.c_uint64, vp, vp, vp]),
         "mg_bin_workspace_bytes": (C.c_size_t, [C.c_int64]),
-        "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, C.c_int32, vp, C.c_int64,
-                         vp, C.c_size_t, _P(C.c_int32), vp, vp]),
+        "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, vp, C.c_int64, vp,
+                         C.c_size_t, _P(C.c_int32), vp, vp]),
         "mg_sort_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int32]),
-        "mg_key_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
+        "mg_tile_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_total_tiles": (C.c_int64, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_render": (st, [_P(mg_splats), vp, vp, _P(mg_view), C.c_int32, _P(mg_raster_cfg),
                            vp, vp, vp, vp, vp]),
@@ -187,12 +187,11 @@ def mg_bin_workspace_bytes(n_records) -> int:
     return int(load().mg_bin_workspace_bytes(n_records))
 
 
-def mg_sort(keys, vals, keys_alt, vals_alt, d_num_instances, capacity, begin_bit, key_bits,
-            ranges, n_tiles_total, workspace, workspace_bytes, d_status, stream) -> int:
+def mg_sort(keys, vals, keys_alt, vals_alt, d_num_instances, capacity, key_bits, ranges,
+            n_tiles_total, workspace, workspace_bytes, d_status, stream) -> int:
     alt = C.c_int32(0)
     _check("mg_sort", load().mg_sort(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt),
-                                     ptr(d_num_instances), capacity, begin_bit, key_bits,
-                                     ptr(ranges),
+                                     ptr(d_num_instances), capacity, key_bits, ptr(ranges),
                                      n_tiles_total, ptr(workspace), workspace_bytes,
                                      C.byref(alt), ptr(d_status), stream))
     return int(alt.value)
@@ -202,8 +201,8 @@ def mg_sort_workspace_bytes(capacity, key_bits) -> int:
     return int(load().mg_sort_workspace_bytes(capacity, key_bits))
 
 
-def mg_key_bits(views, n_views, cfg) -> int:
-    return int(load().mg_key_bits(views, n_views, C.byref(cfg)))
+def mg_tile_bits(views, n_views, cfg) -> int:
+    return int(load().mg_tile_bits(views, n_views, C.byref(cfg)))
 
 
 def mg_total_tiles(views, n_views, cfg) -> int:

@@ -52,12 +52,12 @@ int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cf
     return vt.tile_off[n_views];
 }
 
-int32_t mg_key_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg) {
+int32_t mg_tile_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg) {
     const int64_t t = mg_total_tiles(views, n_views, cfg);
     if (t <= 0) return -1;
     int b = 0;
     while ((int64_t(1) << b) < t) ++b;
-    return 32 + (b > 0 ? b : 1);
+    return b > 0 ? b : 1;
 }
 
 mg_status mg_read_status(const mg_status_word *d_status, mg_status_word *h_out,

@@ -6,14 +6,14 @@
 //                their depth (4 passes over R records)
 //   scan         single-pass exclusive scan of tiles_touched, in depth order
 //                (decoupled look-back)
-//   duplicate    one (tile | depth) key per intersected tile, row-major per
-//                splat, splats in depth order
-//   sort         stable LSD radix sort of the instances on the tile bits only
-//                (key bits 32 and up; 2 passes for up to 65536 tiles): as the
-//                instances arrive in depth order, every tile's list comes out
-//                ordered by (depth, record index) -- the order a full sort of
-//                the 64-bit (tile, depth) keys of record-ordered instances
-//                gives, with a third of the traffic
+//   duplicate    one tile-id key per intersected tile, row-major per splat,
+//                splats in depth order
+//   sort         stable LSD radix sort of the instances by tile id (2 passes
+//                for up to 65536 tiles): as the instances arrive in depth
+//                order, every tile's list comes out ordered by (depth, record
+//                index) -- the order a full sort of 64-bit (tile, depth) keys
+//                of record-ordered instances gives, with a quarter of the
+//                traffic
 //   ranges       [start, end) of every tile in the sorted list
 //
 // The radix sort is "onesweep" (Adinets & Merrill, "Onesweep: a faster least
@@ -152,64 +152,64 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 // --------------------------------------------------------------------------
 // key duplication
 // --------------------------------------------------------------------------
-// One thread per position (record order[i], or i) writes small rectangles;
-// rectangles of more than 32 tiles are written by the whole warp, one at a
-// time, 32 tiles per step (near-camera splats cover thousands of tiles).
-__global__ void duplicate_kernel(ViewTable vt, const float *__restrict__ record,
-                                 const int32_t *__restrict__ radius,
-                                 const uint32_t *__restrict__ tiles,
-                                 const uint32_t *__restrict__ order,
-                                 const uint32_t *__restrict__ offsets, int64_t n_records,
-                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                 uint64_t capacity) {
+// A warp's 32 positions own one contiguous range of instance slots (their
+// offsets are consecutive).  The warp writes that range 32 slots at a time,
+// fully coalesced: slot p belongs to the last lane L with offsets[L] <= p
+// (binary search over the lanes by shuffles), and is tile m = p - offsets[L]
+// of L's rectangle, row-major.
+__global__ void __launch_bounds__(256)
+duplicate_kernel(ViewTable vt, const float *__restrict__ record,
+                 const int32_t *__restrict__ radius, const uint32_t *__restrict__ tiles,
+                 const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
+                 int64_t n_records, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                 uint64_t capacity) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    bool valid = false;
-    uint64_t off = 0, dbits = 0, t0 = 0;
-    uint32_t nt = 0, r = 0;
-    int x0 = 0, x1 = -1, y0 = 0, y1 = -1, gx = 1;
+    const int64_t w0 = i - lane;
+    if (w0 >= n_records) return;                       // whole warp past the end
+    uint32_t r = 0, nt = 0, off, tbase = 0, gx = 1, x0 = 0, y0 = 0, w = 1;
     if (i < n_records) {
         r = order ? order[i] : (uint32_t)i;
-        nt = tiles[r];
         off = offsets[i];
-        if (nt != 0 && off + nt <= capacity) {
+        nt = tiles[r];
+        if (nt != 0) {
             int v = 0;
             while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= (int64_t)r) ++v;
-            const float4 a = *reinterpret_cast<const float4 *>(record + 12 * (int64_t)r);
-            dbits = __float_as_uint(record[12 * (int64_t)r + 11]);
-            t0 = (uint64_t)vt.tile_off[v];
-            gx = vt.gx[v];
-            valid = tile_rect(a.x, a.y, (float)radius[r], vt.tile_w, vt.tile_h, gx, vt.gy[v], x0,
-                              x1, y0, y1);
-        }
-    }
-    const bool big = valid && nt > 32u;
-    if (valid && !big) {
-        uint64_t k = off;
-        const uint64_t k_end = off + nt;
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1 && k < k_end; ++tx, ++k) {
-                keys[k] = ((t0 + (uint64_t)ty * gx + tx) << 32) | dbits;
-                vals[k] = r;
+            const float2 m = *reinterpret_cast<const float2 *>(record + 12 * (int64_t)r);
+            int ix0, ix1, iy0, iy1;
+            if (tile_rect(m.x, m.y, (float)radius[r], vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v],
+                          ix0, ix1, iy0, iy1)) {
+                gx = (uint32_t)vt.gx[v];
+                tbase = (uint32_t)vt.tile_off[v];
+                x0 = (uint32_t)ix0;
+                y0 = (uint32_t)iy0;
+                w = (uint32_t)(ix1 - ix0 + 1);
             }
+        }
+    } else {
+        off = offsets[n_records - 1] + tiles[order ? order[n_records - 1] : (uint32_t)(n_records - 1)];
     }
-    unsigned todo = __ballot_sync(0xffffffffu, big);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint64_t o = __shfl_sync(0xffffffffu, off, src);
-        const uint64_t db = __shfl_sync(0xffffffffu, dbits, src);
-        const uint64_t tb = __shfl_sync(0xffffffffu, t0, src);
-        const uint32_t n = __shfl_sync(0xffffffffu, nt, src);
-        const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
-        const int by0 = __shfl_sync(0xffffffffu, y0, src);
-        const int bgx = __shfl_sync(0xffffffffu, gx, src);
-        const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
-        const uint32_t w = (uint32_t)(bx1 - bx0 + 1);
-        for (uint32_t k = lane; k < n; k += 32) {
-            const uint32_t ty = (uint32_t)by0 + k / w, tx = (uint32_t)bx0 + k % w;
-            keys[o + k] = ((tb + (uint64_t)ty * bgx + tx) << 32) | db;
-            vals[o + k] = rr;
+    const uint64_t begin = __shfl_sync(0xffffffffu, off, 0);
+    const uint64_t end = (uint64_t)__shfl_sync(0xffffffffu, off + nt, 31);
+    const uint64_t stop = end < capacity ? end : capacity;
+    for (uint64_t base = begin; base < stop; base += 32) {   // warp-uniform trip count
+        const uint64_t p = base + lane;
+        const uint32_t pp = (uint32_t)p;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t oc = __shfl_sync(0xffffffffu, off, L + step);
+            if (oc <= pp) L += step;
+        }
+        const uint32_t m = pp - __shfl_sync(0xffffffffu, off, L);
+        const uint32_t wl = __shfl_sync(0xffffffffu, w, L);
+        const uint32_t key = __shfl_sync(0xffffffffu, tbase, L) +
+                             (__shfl_sync(0xffffffffu, y0, L) + m / wl) * __shfl_sync(0xffffffffu, gx, L) +
+                             __shfl_sync(0xffffffffu, x0, L) + m % wl;
+        const uint32_t rr = __shfl_sync(0xffffffffu, r, L);
+        if (p < stop) {
+            keys[p] = key;
+            vals[p] = rr;
         }
     }
 }
@@ -240,15 +240,21 @@ __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = sort_count(d_n, capacity);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = (uint64_t)keys[i] >> begin_bit;
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u < n) {
+                const uint64_t k = (uint64_t)keys[i0 + u] >> begin_bit;
+                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+            }
+        }
     }
     // clear the look-back status of the first pass for the partitions in use
     const int64_t parts = (n + kSortPart - 1) / kSortPart;
     const int64_t lim = min(parts, max_parts) * 256;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += stride)
+    const int64_t stride1 = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += stride1)
         ws->status[i] = 0u;
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
@@ -385,15 +391,24 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
     }
 }
 
-__global__ void ranges_kernel(const uint64_t *__restrict__ keys, const uint64_t *d_n,
+__global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint64_t *d_n,
                               uint64_t capacity, uint32_t *__restrict__ ranges, int64_t n_tiles) {
     const int64_t n = sort_count(d_n, capacity);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t t = (int64_t)(keys[i] >> 32);
-        if (t >= n_tiles) continue;
-        if (i == 0 || (int64_t)(keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
-        if (i == n - 1 || (int64_t)(keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+        uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u;
+            if (i >= n) break;
+            const uint32_t t = keys[i];
+            const uint32_t next = i + 1 < n ? keys[i + 1] : 0xFFFFFFFFu;
+            if ((int64_t)t < n_tiles) {
+                if (i == 0 || prev != t) ranges[2 * (int64_t)t] = (uint32_t)i;
+                if (i == n - 1 || next != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
+            }
+            prev = t;
+        }
     }
 }
 
@@ -439,8 +454,9 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     if (capacity == 0 || passes == 0) return MG_OK;
     const int sms = sm_count();
     const int64_t max_parts = sort_max_parts(capacity);
-    sort_histogram_kernel<K><<<sms * 4, 256, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws,
-                                                     max_parts);
+    const int64_t hblocks = (int64_t)((capacity + 1023) / 1024);
+    sort_histogram_kernel<K><<<(unsigned)(hblocks < 65535 ? hblocks : 65535), 256, 0, s>>>(
+        keys, d_n, capacity, begin_bit, passes, ws, max_parts);
     sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<K>, kSortThreads, 0);
@@ -504,7 +520,7 @@ extern "C" size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits) {
 
 extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
                             const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
-                            uint64_t *keys, uint32_t *vals, uint64_t capacity,
+                            uint32_t *keys, uint32_t *vals, uint64_t capacity,
                             uint64_t *d_num_instances, void *workspace, size_t workspace_bytes,
                             mg_status_word *d_status, mg_stream_t stream) {
     if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
@@ -539,34 +555,35 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
     return mg_host::launch_status();
 }
 
-extern "C" mg_status mg_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
                              uint32_t *vals_alt, const uint64_t *d_num_instances,
-                             uint64_t capacity, int32_t begin_bit, int32_t key_bits,
-                             uint32_t *ranges, int64_t n_tiles_total, void *workspace,
-                             size_t workspace_bytes, int32_t *result_in_alt,
-                             mg_status_word *d_status, mg_stream_t stream) {
+                             uint64_t capacity, int32_t key_bits, uint32_t *ranges,
+                             int64_t n_tiles_total, void *workspace, size_t workspace_bytes,
+                             int32_t *result_in_alt, mg_status_word *d_status,
+                             mg_stream_t stream) {
     if (!keys || !vals || !keys_alt || !vals_alt || !d_num_instances || !ranges || !workspace ||
-        !result_in_alt || key_bits < 33 || key_bits > 64 || begin_bit < 0 || begin_bit > 32 ||
-        n_tiles_total <= 0)
+        !result_in_alt || key_bits < 1 || key_bits > 32 || n_tiles_total <= 0)
         return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
     if (workspace_bytes < mg_sort_workspace_bytes(capacity, key_bits)) return MG_ERR_INVALID_ARG;
-    if ((n_tiles_total >> 32) != 0) return MG_ERR_INVALID_ARG;
-    const int passes = (key_bits - begin_bit + 7) / 8;
-    if (passes > kMaxPasses) return MG_ERR_INVALID_ARG;
+    if ((n_tiles_total >> 32) != 0 || (key_bits < 32 && (n_tiles_total >> key_bits) > 1) ||
+        (key_bits < 32 && (n_tiles_total > (int64_t(1) << key_bits))))
+        return MG_ERR_INVALID_ARG;
+    const int passes = (key_bits + 7) / 8;
     cudaStream_t s = (cudaStream_t)stream;
     SortWS *ws = reinterpret_cast<SortWS *>(workspace);
     if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) !=
         cudaSuccess)
         return MG_ERR_CUDA;
     bool in_alt = false;
-    mg_status st = radix_sort<uint64_t>(keys, vals, keys_alt, vals_alt, d_num_instances, capacity,
-                                        begin_bit, passes, ws, d_status, s, &in_alt);
+    mg_status st = radix_sort<uint32_t>(keys, vals, keys_alt, vals_alt, d_num_instances, capacity,
+                                        0, passes, ws, d_status, s, &in_alt);
     if (st != MG_OK) return st;
     *result_in_alt = in_alt ? 1 : 0;
     if (capacity == 0) return mg_host::launch_status();
-    ranges_kernel<<<sm_count() * 4, 256, 0, s>>>(in_alt ? keys_alt : keys, d_num_instances,
-                                                 capacity, ranges, n_tiles_total);
+    const int64_t rblocks = (int64_t)((capacity + 1023) / 1024);
+    ranges_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), 256, 0, s>>>(
+        in_alt ? keys_alt : keys, d_num_instances, capacity, ranges, n_tiles_total);
     return mg_host::launch_status();
 }
 
@@ -614,7 +631,7 @@ mg_status bin_scratch_address(void **out) {
 
 extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views,
                                     int32_t n_views, const mg_raster_cfg *cfg,
-                                    const uint32_t *order, uint32_t *offsets, uint64_t *keys,
+                                    const uint32_t *order, uint32_t *offsets, uint32_t *keys,
                                     uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
                                     mg_status_word *d_status, mg_stream_t stream) {
     if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||

@@ -485,11 +485,21 @@ __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ imag
     const int64_t o = 3 * vt.pix_off[v];
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float d = image[o + i] - target[o + i];
-        grad[o + i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
-        acc += fabsf(d);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+        float a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = i0 + u < n ? image[o + i0 + u] : 0.0f;
+            b[u] = i0 + u < n ? target[o + i0 + u] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u >= n) break;
+            const float d = a[u] - b[u];
+            grad[o + i0 + u] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+            acc += fabsf(d);
+        }
     }
     acc = warp_sum(acc);
     __shared__ float s[32];
@@ -573,7 +583,10 @@ extern "C" mg_status mg_l1_loss_grad(const float *image, const float *target,
     ViewTable vt;
     mg_status st = mg_host::build_view_table(views, n_views, &cfg, &vt);
     if (st != MG_OK) return st;
-    const dim3 grid(152, (unsigned)n_views);
+    int64_t most = 0;
+    for (int v = 0; v < n_views; ++v) most = max(most, 3 * (vt.pix_off[v + 1] - vt.pix_off[v]));
+    const int64_t bx = (most + 1023) / 1024;
+    const dim3 grid((unsigned)(bx < 2048 ? (bx > 0 ? bx : 1) : 2048), (unsigned)n_views);
     l1_loss_grad_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(vt, image, target, dL_dimage,
                                                                loss);
     return mg_host::launch_status();

@@ -128,9 +128,9 @@ class Rasterizer:
         return s
 
     def _ensure_sort_buffers(self, cap, key_bits):
-        self._get("keys", cap, torch.int64)
+        self._get("keys", cap, torch.int32)
         self._get("vals", cap, torch.int32)
-        self._get("keys_alt", cap, torch.int64)
+        self._get("keys_alt", cap, torch.int32)
         self._get("vals_alt", cap, torch.int32)
         self._get("sort_ws", abi.mg_sort_workspace_bytes(cap, key_bits), torch.uint8)
 
@@ -149,7 +149,7 @@ class Rasterizer:
         R = sum(int(r[1]) for r in ranges)
         pix = sum(int(c.width) * int(c.height) for c in cams)
         tiles = abi.mg_total_tiles(views, V, ccfg)
-        key_bits = abi.mg_key_bits(views, V, ccfg)
+        key_bits = abi.mg_tile_bits(views, V, ccfg)
         stream = self._stream()
         ev = _Events(stage_events)
         self.status.zero_()
@@ -191,9 +191,9 @@ class Rasterizer:
         ranges_buf = self._get("ranges", 2 * tiles, torch.int32)
         sort_ws = self._buf["sort_ws"]
         ev.begin("sort")
-        # instances arrive in depth order: a stable sort on the tile bits suffices
+        # instances arrive in depth order: a stable sort by tile id suffices
         alt = abi.mg_sort(self._buf["keys"], self._buf["vals"], self._buf["keys_alt"],
-                          self._buf["vals_alt"], self.num_instances, self.capacity, 32, key_bits,
+                          self._buf["vals_alt"], self.num_instances, self.capacity, key_bits,
                           ranges_buf, tiles, sort_ws, sort_ws.numel(), self.status, stream)
         ev.end("sort")
         sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
@@ -209,7 +209,7 @@ class Rasterizer:
         # kernels of ours per forward: preprocess; depth keys, histogram,
         # offsets, 4 digit passes; scan, duplicate; histogram, offsets, one per
         # tile digit pass, ranges; render
-        self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits - 32 + 7) // 8 + 1
+        self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1
         self._state = dict(g=g, views=views, V=V, cfg=ccfg, splats=splats, R=R, n=n, pix=pix,
                            sorted_vals=sorted_vals, ranges=ranges_buf, tiles=tiles,
                            sh_degree=sh_degree, params=params, cams=cams)

@@ -39,7 +39,7 @@ def test_binding_names_match_header():
     assert sorted(abi.EXPORTED) == _declared()
     for n in _declared():
         if n not in ("mg_status_string", "mg_version", "mg_bin_workspace_bytes",
-                     "mg_sort_workspace_bytes", "mg_key_bits", "mg_total_tiles",
+                     "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles",
                      "mg_depth_order_workspace_bytes"):
             assert callable(getattr(abi, n))
 
@@ -53,7 +53,7 @@ def test_host_only_helpers(lib):
     views = make_views([cam, cam], [(0, 10), (0, 10)])
     cfg = RasterConfig().c()
     assert abi.mg_total_tiles(views, 2, cfg) == 2 * 98 * 65
-    assert abi.mg_key_bits(views, 2, cfg) == 32 + 14
+    assert abi.mg_tile_bits(views, 2, cfg) == 14
     cfg.tile_w, cfg.tile_h = 8, 32
     assert abi.mg_total_tiles(views, 1, cfg) == 195 * 33
     cfg.tile_w = 12
@@ -80,6 +80,6 @@ def test_bad_arguments_rejected_on_host(lib):
                        None, None)
     assert st == abi.MG_ERR_INVALID_ARG
     alt = C.c_int32(0)
-    st = lib.mg_sort(None, None, None, None, None, 0, 32, 20, None, 1, None, 0, C.byref(alt), None,
+    st = lib.mg_sort(None, None, None, None, None, 0, 20, None, 1, None, 0, C.byref(alt), None,
                      None)
     assert st == abi.MG_ERR_INVALID_ARG

@@ -37,9 +37,9 @@ def test_scene_scale_single_view():
     assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order)
     K = int(so["num_instances"].item())
     assert K == v.K
-    keys = rast.sorted_keys().cpu().numpy().view(np.uint64)[:K]
+    keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:K]
     vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:K]
-    assert np.array_equal(keys, v.sorted_keys)
+    assert np.array_equal(keys.astype(np.uint64), v.sorted_keys >> np.uint64(32))
     assert np.array_equal(vals, v.sorted_vals)
     rng = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
     nonempty = v.ranges[:, 1] > v.ranges[:, 0]

@@ -72,7 +72,7 @@ def _check_discrete(rast, views, M, cams):
     K0 = 0
     ranges = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
     vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:K_gpu]
-    keys = rast.sorted_keys().cpu().numpy().view(np.uint64)[:K_gpu]
+    keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:K_gpu]
     for v, cam in zip(views, cams):
         n = v.fp32["tiles"].shape[0]
         fp = v.fp32
@@ -84,9 +84,9 @@ def _check_discrete(rast, views, M, cams):
         assert np.array_equal(r[vis, 1].view(np.uint32), fp["py"][vis].view(np.uint32))
         assert np.array_equal(r[vis, 11].view(np.uint32), fp["depth_bits"][vis])
         nt = v.ranges.shape[0]
-        # the oracle's keys are per view: shift its tile ids by the view's tile offset
-        okeys = v.sorted_keys + (np.uint64(T0) << np.uint64(32))
-        assert np.array_equal(keys[K0:K0 + v.K], okeys), "sorted keys differ"
+        # instance keys are global tile ids: the oracle's tile of view v plus T0
+        otiles = (v.sorted_keys >> np.uint64(32)).astype(np.int64) + T0
+        assert np.array_equal(keys[K0:K0 + v.K].astype(np.int64), otiles), "sorted tiles differ"
         assert np.array_equal(vals[K0:K0 + v.K], v.sorted_vals.astype(np.uint32) + R0), "sorted values differ"
         gr = ranges[T0:T0 + nt].astype(np.int64)
         orr = v.ranges.astype(np.int64)

@@ -28,7 +28,7 @@ def _bin(abi, rast, noalloc, ordered=True):
     dev = rast.device
     cap = rast.capacity
     offsets = torch.full((R,), -1, dtype=torch.int32, device=dev)
-    keys = torch.full((cap,), -1, dtype=torch.int64, device=dev)
+    keys = torch.full((cap,), -1, dtype=torch.int32, device=dev)
     vals = torch.full((cap,), -1, dtype=torch.int32, device=dev)
     n = torch.zeros(1, dtype=torch.int64, device=dev)
     status = torch.zeros(2, dtype=torch.int64, device=dev)
