@@ -232,6 +232,9 @@ struct SortWS {
     uint32_t status[1];                // [2][max_parts][256]
 };
 
+// Digit counts of every pass in one read of the keys: a few blocks per SM,
+// each with a shared-memory histogram flushed once (the flush contends on the
+// same 256 counters per pass, so the grid stays small).
 template <typename K>
 __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t *d_n,
                                       uint64_t capacity, int begin_bit, int passes, SortWS *ws,
@@ -240,22 +243,35 @@ __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = sort_count(d_n, capacity);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    if (sizeof(K) == 4) {
+        // 4 keys per 128-bit load
+        const int64_t n4 = n >> 2;
+        const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
+        for (int64_t q = t; q < n4; q += nt) {
+            const uint4 v = k4[q];
+            const uint32_t e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (i0 + u < n) {
-                const uint64_t k = (uint64_t)keys[i0 + u] >> begin_bit;
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t k = (uint64_t)e[u] >> begin_bit;
                 for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
             }
+        }
+        for (int64_t i = (n4 << 2) + t; i < n; i += nt) {
+            const uint64_t k = (uint64_t)keys[i] >> begin_bit;
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+        }
+    } else {
+        for (int64_t i = t; i < n; i += nt) {
+            const uint64_t k = (uint64_t)keys[i] >> begin_bit;
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
         }
     }
     // clear the look-back status of the first pass for the partitions in use
     const int64_t parts = (n + kSortPart - 1) / kSortPart;
     const int64_t lim = min(parts, max_parts) * 256;
-    const int64_t stride1 = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += stride1)
-        ws->status[i] = 0u;
+    for (int64_t i = t; i < lim; i += nt) ws->status[i] = 0u;
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
         const uint32_t c = (&h[0][0])[i];
@@ -454,9 +470,10 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     if (capacity == 0 || passes == 0) return MG_OK;
     const int sms = sm_count();
     const int64_t max_parts = sort_max_parts(capacity);
-    const int64_t hblocks = (int64_t)((capacity + 1023) / 1024);
-    sort_histogram_kernel<K><<<(unsigned)(hblocks < 65535 ? hblocks : 65535), 256, 0, s>>>(
-        keys, d_n, capacity, begin_bit, passes, ws, max_parts);
+    const int64_t hblocks = (int64_t)((capacity + 4095) / 4096);
+    const int64_t hcap = (int64_t)sms * 2;
+    sort_histogram_kernel<K><<<(unsigned)(hblocks < hcap ? (hblocks > 0 ? hblocks : 1) : hcap),
+                               512, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws, max_parts);
     sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<K>, kSortThreads, 0);

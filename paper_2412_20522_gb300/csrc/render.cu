@@ -294,7 +294,7 @@ constexpr int kAcc = 10;
 // contributing pixel, [3] masked with a contributing pixel, [4] contributing
 // pixels over [2], [5] staged batches.
 template <bool COUNT>
-__global__ void __launch_bounds__(kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, 6)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                        float bg0, float bg1, float bg2, const float *__restrict__ final_T,
@@ -379,42 +379,49 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     const int hb = 31 - __clz(word);
                     word &= ~(1u << hb);
                     const int j = (ch << 5) + hb;
-                    const float4 A = sA[j], B = sB[j], c = sC[j];
+                    const float4 A = sA[j], B = sB[j];
                     const bool masked = B.w == 0.0f;
+                    // alpha of both pixels first: independent, so they interleave
+                    Frag f[kPix];
+                    bool on[kPix];
+#pragma unroll
+                    for (int k = 0; k < kPix; ++k) {
+                        frag_alpha(A, B, fpx[k], fpy[k], f[k]);
+                        on[k] = pos0 + j < stop[k] && f[k].alpha >= kAlphaMin;
+                    }
+                    const int ncontrib = (int)on[0] + (int)on[1];
+                    if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) continue;
+                    const float4 c = sC[j];
                     float v[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-                    int ncontrib = 0;
 #pragma unroll
                     for (int k = 0; k < kPix; ++k) {
-                        if (pos0 + j >= stop[k]) continue;
-                        Frag f;
-                        frag_alpha(A, B, fpx[k], fpy[k], f);
-                        if (f.alpha < kAlphaMin) continue;
-                        ++ncontrib;
-                        const float ma = masked ? 0.0f : f.alpha;
+                        if (!on[k]) continue;
+                        const float alpha = f[k].alpha;
+                        const float ma = masked ? 0.0f : alpha;
                         const float Tj = __fdividef(T[k], 1.0f - ma);
                         const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
                                           g2[k] * (c.z - bc2[k]);
-                        v[9] += f.alpha * Tj * gcb;           // Eq. 6 + Appendix A
+                        v[9] += alpha * Tj * gcb;               // Eq. 6 + Appendix A
                         if (!masked) {
-                            const float wt = f.alpha * Tj;
+                            const float wt = alpha * Tj;
                             v[6] += wt * g0[k];
                             v[7] += wt * g1[k];
                             v[8] += wt * g2[k];
-                            bc0[k] = fmaf(f.alpha, c.x - bc0[k], bc0[k]);
-                            bc1[k] = fmaf(f.alpha, c.y - bc1[k], bc1[k]);
-                            bc2[k] = fmaf(f.alpha, c.z - bc2[k], bc2[k]);
+                            bc0[k] = fmaf(alpha, c.x - bc0[k], bc0[k]);
+                            bc1[k] = fmaf(alpha, c.y - bc1[k], bc1[k]);
+                            bc2[k] = fmaf(alpha, c.z - bc2[k], bc2[k]);
                             T[k] = Tj;
-                            if (f.araw < kAlphaMax) {
-                                const float dpow = Tj * gcb * f.alpha;   // dL/dalpha * alpha
-                                const float pdx = dpow * f.dx, pdy = dpow * f.dy;
+                            if (f[k].araw < kAlphaMax) {
+                                const float dpow = Tj * gcb * alpha;    // dL/dalpha * alpha
+                                const float pdx = dpow * f[k].dx, pdy = dpow * f[k].dy;
                                 v[0] += dpow;
                                 v[1] += pdx;
                                 v[2] += pdy;
-                                v[3] += pdx * f.dx;
-                                v[4] += pdx * f.dy;
-                                v[5] += pdy * f.dy;
+                                v[3] += pdx * f[k].dx;
+                                v[4] += pdx * f[k].dy;
+                                v[5] += pdy * f[k].dy;
                             }
                         }
                     }
