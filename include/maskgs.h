@@ -139,7 +139,9 @@ typedef struct {
  *   record[R][12] FP32 render record: mean2d x, y; major axis ux, uy of the
  *     2D covariance; h1 = -log2(e)/(2 lambda_1), h2 = -log2(e)/(2 lambda_2)
  *     (so that o exp(-1/2 d^T Sigma^-1 d) = o exp2(h1 (d.u)^2 + h2 (d.u_perp)^2));
- *     opacity o; mask M as 0.0/1.0; r, g, b; depth tz.
+ *     o if M = 1, -o if M = 0 (opacity o > 0, the mask in the sign);
+ *     e_min, a skip threshold just below log2(1/(255 o)) for the exponent
+ *     (1 if o < 1/255: the splat never reaches the floor); r, g, b; depth tz.
  *   tiles_touched[R] u32 (0 = culled), radius[R] i32 (pixels, 0 = culled),
  *   clamp[R] u8 (bit c: colour channel c was clamped at 0).
  * Per-Gaussian (n):

@@ -230,7 +230,10 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         out.clamp[r] = cl;
         float4 *rec = reinterpret_cast<float4 *>(out.record) + 3 * r;
         rec[0] = make_float4(S.px, S.py, ux, uy);
-        rec[1] = make_float4(-0.5f * kLog2e / l1, -0.5f * kLog2e / l2, op, Mf);
+        // mask in the sign of the opacity; e_min just below log2(1/(255 o)) (a
+        // splat with o under the floor never reaches it: e_min = 1 > any e)
+        const float e_min = op >= kAlphaMin ? __log2f(kAlphaMin / op) - 1e-3f : 1.0f;
+        rec[1] = make_float4(-0.5f * kLog2e / l1, -0.5f * kLog2e / l2, Mf != 0.0f ? op : -op, e_min);
         rec[2] = make_float4(rgb[0], rgb[1], rgb[2], S.tz);
     }
 }

@@ -21,10 +21,13 @@
 
 namespace mg {
 
-constexpr int kRenderThreads = 128;              // threads per CTA (one tile)
+#ifndef MG_RENDER_PIX
+#define MG_RENDER_PIX 2
+#endif
+constexpr int kPix = MG_RENDER_PIX;              // pixels per thread
+constexpr int kRenderThreads = 256 / kPix;       // threads per CTA (one 256-pixel tile)
 constexpr int kRenderWarps = kRenderThreads / 32;
 constexpr int kBatch = 256;                      // splats staged per batch
-constexpr int kPix = 2;                          // pixels per thread
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -33,26 +36,35 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 struct Frag {
-    float dx, dy, p1, p2, G, araw, alpha;
+    float dx, dy, p1, p2, e, G, araw, alpha;
+    bool on;             // alpha reaches the 1/255 floor
 };
 
-// alpha = min(0.99, o 2^(h1 p1^2 + h2 p2^2)), p1 = d.u, p2 = d.u_perp,
-// d = pixel centre - mean.  A = (mx, my, ux, uy), B = (h1, h2, o, M).
+// alpha = min(0.99, o 2^e), e = h1 p1^2 + h2 p2^2, p1 = d.u, p2 = d.u_perp,
+// d = pixel centre - mean.  A = (mx, my, ux, uy), B = (h1, h2, +-o, e_min):
+// the sign of B.z is the mask (negative = masked), and e_min (stored by the
+// preprocess, just below log2(1/(255 o))) lets both kernels skip the exp of
+// fragments whose alpha is certainly under the floor; the alpha test itself
+// still decides every other fragment, identically in both kernels.
 __device__ __forceinline__ void frag_alpha(const float4 &A, const float4 &B, float fpx, float fpy,
                                            Frag &f) {
     f.dx = __fsub_rn(fpx, A.x);
     f.dy = __fsub_rn(fpy, A.y);
     f.p1 = __fmaf_rn(f.dy, A.w, __fmul_rn(f.dx, A.z));
     f.p2 = __fmaf_rn(f.dy, A.z, -__fmul_rn(f.dx, A.w));
-    const float e = __fmaf_rn(__fmul_rn(B.x, f.p1), f.p1, __fmul_rn(__fmul_rn(B.y, f.p2), f.p2));
-    f.G = ex2_approx(e);
-    f.araw = __fmul_rn(B.z, f.G);
-    f.alpha = fminf(kAlphaMax, f.araw);
+    f.e = __fmaf_rn(__fmul_rn(B.x, f.p1), f.p1, __fmul_rn(__fmul_rn(B.y, f.p2), f.p2));
+    f.on = false;
+    if (f.e >= B.w) {
+        f.G = ex2_approx(f.e);
+        f.araw = __fmul_rn(fabsf(B.z), f.G);
+        f.alpha = fminf(kAlphaMax, f.araw);
+        f.on = f.alpha >= kAlphaMin;
+    }
 }
 
-// Tile of the CTA and the two pixels of this thread.  Warp w owns rows
-// [w * 64/tw, (w+1) * 64/tw) of the tile; a lane's pixels are (l % tw,
-// l / tw) and the same column 32/tw rows further down, within that block.
+// Tile of the CTA and the kPix pixels of this thread.  Warp w owns rows
+// [w * bh, (w+1) * bh) of the tile, bh = 32 kPix / tw; a lane's pixels are
+// (l % tw, l / tw) and the same column 32/tw, 2*32/tw, ... rows further down.
 struct TileInfo {
     int v;
     int x0, y0;          // tile origin (pixels)
@@ -94,11 +106,10 @@ __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t block_mask(const float4 &A, const float4 &B, float x0,
                                                float y0, int bw, int bh) {
-    const float o = B.z;
-    if (!(o >= kAlphaMin * 0.999f)) return 0u;      // alpha <= o never reaches the floor
-    // log2 of the floor relative to o, pushed outwards by 1e-3 (0.07 % in alpha)
-    const float e_thr = __log2f(kAlphaMin / o) - 1e-3f;
-    if (!(e_thr < 0.0f)) return (1u << kRenderWarps) - 1u;
+    // e_min < 0 is the stored skip threshold (already pushed outwards by
+    // 1e-3 in log2 alpha); e_min > 0 marks a splat that never reaches the floor
+    const float e_thr = B.w;
+    if (!(e_thr < 0.0f)) return 0u;
     const float r1 = sqrtf(e_thr / B.x) * 1.0001f + 0.02f;   // semi-axis along u
     const float r2 = sqrtf(e_thr / B.y) * 1.0001f + 0.02f;   // semi-axis along u_perp
     const float ux = A.z, uy = A.w;
@@ -119,6 +130,13 @@ __device__ __forceinline__ uint32_t block_mask(const float4 &A, const float4 &B,
         if (!(sep_x || sep_y || sep_u || sep_v)) m |= 1u << w;
     }
     return m;
+}
+
+__device__ __forceinline__ bool all_done(const bool *done) {
+    bool a = true;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) a = a && done[k];
+    return a;
 }
 
 // COUNT = true adds per-fragment counters (an untimed diagnostic variant):
@@ -154,7 +172,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
     if (threadIdx.x < 4) s_frags[threadIdx.x] = 0ull;
 
     for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
-        if (__syncthreads_count(done[0] && done[1]) == kRenderThreads) break;
+        if (__syncthreads_count(all_done(done)) == kRenderThreads) break;
 #pragma unroll
         for (int h = 0; h < kBatch / kRenderThreads; ++h) {
             const int i = threadIdx.x + h * kRenderThreads;
@@ -165,7 +183,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 sB[i] = B;
                 sC[i] = rec[3 * (int64_t)r + 2];
                 // masked splats neither colour nor attenuate: out of every forward list
-                sM[i] = (uint8_t)((B.w != 0.0f)
+                sM[i] = (uint8_t)((B.z > 0.0f)
                                       ? block_mask(A, B, (float)ti.x0, (float)ti.y0, vt.tile_w, ti.bh)
                                       : 0u);
             }
@@ -182,12 +200,12 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                     const float4 B = sB[j];
                     Frag f;
                     frag_alpha(sA[j], B, fpx[k], fpy[k], f);
-                    if (B.w == 0.0f) {
-                        c_masked += f.alpha >= kAlphaMin;
+                    if (B.z < 0.0f) {
+                        c_masked += f.on;
                         continue;
                     }
                     ++c_unmasked;
-                    if (f.alpha < kAlphaMin) continue;
+                    if (!f.on) continue;
                     const float tT = Tc * (1.0f - f.alpha);
                     if (tT < kTMin) {
                         --c_unmasked;
@@ -198,7 +216,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 }
             }
         }
-        if (__all_sync(0xffffffffu, done[0] && done[1])) continue;
+        if (__all_sync(0xffffffffu, all_done(done))) continue;
         const int nchunks = (cnt + 31) >> 5;
         for (int ch = 0; ch < nchunks; ++ch) {
             const int jj = (ch << 5) + lane;
@@ -212,7 +230,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                     if (done[k]) continue;
                     Frag f;
                     frag_alpha(A, B, fpx[k], fpy[k], f);
-                    if (f.alpha < kAlphaMin) continue;
+                    if (!f.on) continue;
                     const float testT = T[k] * (1.0f - f.alpha);
                     if (testT < kTMin) {
                         done[k] = true;
@@ -226,12 +244,14 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                     T[k] = testT;
                 }
             }
-            if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+            if (__all_sync(0xffffffffu, all_done(done))) break;
         }
     }
     if (COUNT) {
-        unsigned long long c[4] = {(ti.inside[0] ? stop[0] : 0u) + (ti.inside[1] ? stop[1] : 0u),
-                                   c_unmasked, c_blend, c_masked};
+        unsigned long long walked = 0;
+#pragma unroll
+        for (int k = 0; k < kPix; ++k) walked += ti.inside[k] ? stop[k] : 0u;
+        unsigned long long c[4] = {walked, c_unmasked, c_blend, c_masked};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -294,7 +314,7 @@ constexpr int kAcc = 10;
 // contributing pixel, [3] masked with a contributing pixel, [4] contributing
 // pixels over [2], [5] staged batches.
 template <bool COUNT>
-__global__ void __launch_bounds__(kRenderThreads, 6)
+__global__ void __launch_bounds__(kRenderThreads, 768 / kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                        float bg0, float bg1, float bg2, const float *__restrict__ final_T,
@@ -336,7 +356,9 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
         bc1[k] = bg1;
         bc2[k] = bg2;
     }
-    uint32_t tstop = max(stop[0], stop[1]);
+    uint32_t tstop = 0;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) tstop = max(tstop, stop[k]);
     if (threadIdx.x == 0) s_maxstop = 0;
     __syncthreads();
     atomicMax(&s_maxstop, tstop);
@@ -380,16 +402,18 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     word &= ~(1u << hb);
                     const int j = (ch << 5) + hb;
                     const float4 A = sA[j], B = sB[j];
-                    const bool masked = B.w == 0.0f;
-                    // alpha of both pixels first: independent, so they interleave
+                    const bool masked = B.z < 0.0f;
+                    // alpha of every pixel first: independent, so they interleave
                     Frag f[kPix];
                     bool on[kPix];
 #pragma unroll
                     for (int k = 0; k < kPix; ++k) {
                         frag_alpha(A, B, fpx[k], fpy[k], f[k]);
-                        on[k] = pos0 + j < stop[k] && f[k].alpha >= kAlphaMin;
+                        on[k] = pos0 + j < stop[k] && f[k].on;
                     }
-                    const int ncontrib = (int)on[0] + (int)on[1];
+                    int ncontrib = 0;
+#pragma unroll
+                    for (int k = 0; k < kPix; ++k) ncontrib += (int)on[k];
                     if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) continue;
                     const float4 c = sC[j];
                     float v[16];
@@ -454,7 +478,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
             const float *S = sG[i];
             float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[i];
             const float4 B = sB[i];
-            if (B.w == 0.0f) {
+            if (B.z < 0.0f) {
                 if (S[9] != 0.0f) atomicAdd(&G4[2].y, S[9]);
             } else {
                 const float4 A = sA[i];
@@ -468,7 +492,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                 if (dmx != 0.0f || dmy != 0.0f || S[3] != 0.0f || S[4] != 0.0f)
                     atomicAdd(&G4[0], make_float4(dmx, dmy, -0.5f * S[3], -S[4]));
                 if (S[5] != 0.0f || S[0] != 0.0f || S[6] != 0.0f || S[7] != 0.0f)
-                    atomicAdd(&G4[1], make_float4(-0.5f * S[5], S[0] / B.z, S[6], S[7]));
+                    atomicAdd(&G4[1], make_float4(-0.5f * S[5], S[0] / fabsf(B.z), S[6], S[7]));
                 if (S[8] != 0.0f || S[9] != 0.0f)
                     atomicAdd(reinterpret_cast<float2 *>(&G4[2]), make_float2(S[8], S[9]));
             }
