@@ -91,6 +91,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+PROFILE_KERNEL = {"render_bwd": ("render_backward", "render.cu"),
+                  "render": ("render_forward", "render.cu"),
+                  "sort": ("onesweep", "binsort.cu"),
+                  "preprocess": ("preprocess", "preprocess.cu"),
+                  "preprocess_bwd": ("preprocess_backward", "preprocess.cu")}
+
+
+def _profiled_traffic(stage):
+    """DRAM bytes per launch from the committed ncu summary of the stage's
+    kernel, if that summary was taken on the current source (else None)."""
+    import hashlib
+    import re
+    if stage not in PROFILE_KERNEL:
+        return None
+    label, src = PROFILE_KERNEL[stage]
+    path = os.path.join(ROOT, "profiles", f"{label}_scene_1p2M_1557x1038.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"sha256\[:16\] at capture: `([0-9a-f]+)`", text)
+    t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+    cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2412_20522_gb300", "csrc", src), "rb")
+                         .read()).hexdigest()[:16]
+    if not m or not t or m.group(1) != cur:
+        return None
+    return int(t.group(1))
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -249,7 +277,8 @@ def run_ours(args):
     if dom in ("render", "render_bwd"):
         achieved = (flops_fwd if dom == "render" else flops_bwd) / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": _profiled_traffic(dom),
                 "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)"}
     else:
         bytes_per = {"sort": K * 152, "preprocess": g.n * 244 + visible * 60,
@@ -257,7 +286,7 @@ def run_ours(args):
         achieved = bytes_per / (stage_ms[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved,
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": _profiled_traffic(dom),
                 "peak_source": peak_src}
 
     line = {
