@@ -310,6 +310,8 @@ def run_ours(args):
         "gpu_launches": gpu_launches_per_step * args.steps,
         "clocks": clk,
     }
+    if not args.no_forms:
+        line["forms"] = run_forms(dev, g, cams, target, ms, W * H)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(steps=1)
     if clk is not None and clk["samples"] < 3:
@@ -318,6 +320,131 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _device_params(g, dev, storage=None):
+    import torch
+    from paper_2412_20522_gb300.rasterize import PARAM_NAMES, STORED
+    p = {k: torch.as_tensor(np.ascontiguousarray(getattr(g, k))).to(dev) for k in PARAM_NAMES}
+    if storage is not None:
+        for k in STORED:
+            p[k] = p[k].to(storage)
+    return p
+
+
+def _concat_scenes(scs):
+    from paper_2412_20522_gb300 import scenes
+    cat = {k: np.concatenate([getattr(s, k) for s in scs]) for k in
+           ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")}
+    return scenes.Gaussians(**cat, sh_degree=scs[0].sh_degree)
+
+
+def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
+    """The batched and reduced-storage forms, each against the plain FP32
+    single-view form measured above (same GPU, same run)."""
+    import torch
+    from paper_2412_20522_gb300 import scenes
+    from paper_2412_20522_gb300.autotune import GraphStep, autotune_tile, time_step
+    from paper_2412_20522_gb300.rasterize import RasterConfig
+
+    forms = {"plain_fp32_single_view": {"ms_per_step": plain_ms,
+                                        "mpix_per_s": plain_pix / 1e6 / (plain_ms * 1e-3)}}
+
+    # multi-view batch: 8 ring cameras, one shared mask sample, summed
+    # gradients, one captured launch sequence, autotuned tile shape
+    cams8 = [scenes.ring_camera(2 * math.pi * k / 8, 4.0, 1557, 1038, 1150.0) for k in range(8)]
+    p = _device_params(g, dev)
+    tgt8 = torch.as_tensor(np.concatenate([target.reshape(-1)] * 8)).to(dev)
+    tile = autotune_tile(p, cams8, tgt8, steps=3)
+    gs = GraphStep(p, cams8, RasterConfig(tile_w=tile[0], tile_h=tile[1]), tgt8)
+    ms = time_step(gs.replay, steps=steps)
+    pix = 8 * 1557 * 1038
+    forms["multiview_graph"] = {"views": 8, "tile": f"{tile[0]}x{tile[1]}", "ms_per_step": ms,
+                                "mpix_per_s": pix / 1e6 / (ms * 1e-3),
+                                "status": gs.status()}
+    del gs, p
+    torch.cuda.empty_cache()
+
+    # precision variant: 3M Gaussians, 4 views at 1957x1297, BF16 / FP16 storage
+    g3 = scenes.cluster_gaussians(3_000_000, seed=2024125)
+    f4 = 1150.0 * 1957 / 1557
+    cams4 = [scenes.ring_camera(2 * math.pi * k / 4, 4.0, 1957, 1297, f4) for k in range(4)]
+    tgt4 = torch.as_tensor(np.concatenate(
+        [scenes.target_image(1297, 1957, seed=2024126 + k).reshape(-1) for k in range(4)])).to(dev)
+    for name, dt in (("precision_bf16", torch.bfloat16), ("precision_fp16", torch.float16),
+                     ("precision_fp32", None)):
+        p = _device_params(g3, dev, dt)
+        gs = GraphStep(p, cams4, RasterConfig(), tgt4)
+        ms = time_step(gs.replay, steps=max(3, steps // 2))
+        forms[name] = {"gaussians": g3.n, "views": 4, "ms_per_step": ms,
+                       "mpix_per_s": 4 * 1957 * 1297 / 1e6 / (ms * 1e-3), "status": gs.status()}
+        del gs, p
+        torch.cuda.empty_cache()
+    try:
+        forms["precision_error_vs_fp64_crop64"] = precision_crop_errors(dev, g3, cams4[0])
+    except Exception as exc:          # report, do not lose the line
+        forms["precision_error_vs_fp64_crop64"] = {"error": repr(exc)[:200]}
+    del g3
+
+    # uneven batch: 6 scenes, one camera each, BF16 storage, one launch sequence
+    sizes = [150_000, 400_000, 800_000, 1_200_000, 2_000_000, 3_000_000]
+    res = [(779, 519), (1039, 692), (1297, 865), (1557, 1038), (1751, 1167), (1957, 1297)]
+    scs = [scenes.cluster_gaussians(n, seed=2024130 + k) for k, n in enumerate(sizes)]
+    camsu = [scenes.ring_camera(0.5 * k, 4.0, w, h, 1150.0 * w / 1557) for k, (w, h) in enumerate(res)]
+    tgtu = torch.as_tensor(np.concatenate(
+        [scenes.target_image(h, w, seed=2024140 + k).reshape(-1) for k, (w, h) in enumerate(res)])).to(dev)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    ranges = [(int(o), n) for o, n in zip(offs, sizes)]
+    p = _device_params(_concat_scenes(scs), dev, torch.bfloat16)
+    gs = GraphStep(p, camsu, RasterConfig(), tgtu, view_ranges=ranges)
+    ms = time_step(gs.replay, steps=max(3, steps // 2))
+    pix = sum(w * h for w, h in res)
+    per_scene = []
+    del gs, p
+    torch.cuda.empty_cache()
+    for k, sc in enumerate(scs):
+        pk = _device_params(sc, dev, torch.bfloat16)
+        w, h = res[k]
+        tk = torch.as_tensor(scenes.target_image(h, w, seed=2024140 + k)).to(dev).reshape(-1)
+        gk = GraphStep(pk, [camsu[k]], RasterConfig(), tk)
+        mk = time_step(gk.replay, steps=max(3, steps // 2))
+        per_scene.append({"gaussians": sizes[k], "resolution": f"{w}x{h}", "ms_per_step": mk,
+                          "mpix_per_s": w * h / 1e6 / (mk * 1e-3)})
+        del gk, pk
+        torch.cuda.empty_cache()
+    forms["uneven_batch_bf16"] = {"scenes": len(sizes), "ms_per_step": ms,
+                                  "mpix_per_s": pix / 1e6 / (ms * 1e-3), "per_scene": per_scene}
+    return forms
+
+
+def precision_crop_errors(dev, g, cam):
+    """Per-output error of BF16 / FP16 storage against the FP64 oracle on the
+    FP32 parameters, on the centre 64x64 crop of the view."""
+    import torch
+    from oracle import pipeline
+    from paper_2412_20522_gb300 import scenes
+    from paper_2412_20522_gb300.rasterize import PARAM_NAMES, RasterConfig, Rasterizer
+    crop = _crop_camera(cam, 64, 64)
+    tgt = scenes.target_image(64, 64, seed=2024127)
+    ref = pipeline.forward_backward_l1(g, [crop], [tgt], pipeline.OracleConfig())
+    v = ref["views"][0]
+    out = {}
+    for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16), ("fp32", None)):
+        p = _device_params(g, dev, dt)
+        rast = Rasterizer(dev)
+        img = rast.forward(p, [crop], RasterConfig())
+        d = torch.as_tensor(ref["dL_dimages"][0].astype(np.float32)).to(dev).reshape(-1)
+        grads = rast.backward(d)
+        torch.cuda.synchronize()
+        e = {"image_max_abs": float(np.abs(img.cpu().numpy().reshape(3, 64, 64) - v.out["image"]).max())}
+        for k in PARAM_NAMES:
+            a = grads[k].cpu().numpy().astype(np.float64).ravel()
+            b = ref["grads"][k].ravel()
+            nb = np.linalg.norm(b)
+            e[f"d_{k}_rel_l2"] = float(np.linalg.norm(a - b) / nb) if nb > 0 else 0.0
+        out[name] = e
+        del p, rast
+    return out
 
 
 def _crop_camera(cam, cw, ch):
@@ -381,6 +508,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the multi-view, reduced-storage and scene-batch forms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

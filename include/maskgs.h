@@ -67,7 +67,7 @@ typedef enum {
 } mg_status;
 
 enum { MG_MASK_GUMBEL = 0, MG_MASK_ALL_ONES = 1, MG_MASK_GIVEN = 2 };
-enum { MG_DTYPE_F32 = 0 };
+enum { MG_DTYPE_F32 = 0, MG_DTYPE_BF16 = 1, MG_DTYPE_F16 = 2 };
 enum { MG_MAX_VIEWS = 64, MG_RECORD_FLOATS = 12, MG_GRAD2D_FLOATS = 12 };
 
 /* Device status word.  Zero it before a step; kernels only ever raise it.
@@ -80,24 +80,27 @@ typedef struct {
 } mg_status_word;
 
 /* Gaussian parameters (Sec. 3.1: centre p, opacity o, scales s, rotation q,
- * SH; Sec. 3.3: two mask scores).  Device arrays, FP32:
- *   means[n][3]; log_scales[n][3] (s = exp(log_scales));
+ * SH; Sec. 3.3: two mask scores).  Device arrays:
+ *   means[n][3] FP32; log_scales[n][3] (s = exp(log_scales));
  *   quats[n][4] as (w, x, y, z), normalised inside;
  *   opacity_logit[n] (o = sigmoid(opacity_logit));
  *   sh[n][(sh_degree+1)^2][3], real SH with the Condon-Shortley phase,
  *     basis order l = 0..D, m = -l..l, colour = sum_k Y_k(dir) sh[k] + 0.5,
  *     clamped at 0; dir = normalise(p - cam_pos);
- *   mask_logits[n][2], index 0 = "present". */
+ *   mask_logits[n][2] FP32, index 0 = "present".
+ * dtype is the storage of log_scales, quats, opacity_logit and sh: FP32, BF16
+ * or FP16 (unpacked to FP32 on load; every computation is FP32).  Alignment:
+ * sh 16 bytes, quats one row (16 or 8 bytes). */
 typedef struct {
     int64_t n;
     int32_t sh_degree;       /* 0..3 */
-    int32_t dtype;           /* MG_DTYPE_F32 */
-    const float *means;
-    const float *log_scales;
-    const float *quats;
-    const float *opacity_logit;
-    const float *sh;
-    const float *mask_logits;
+    int32_t dtype;           /* MG_DTYPE_F32, MG_DTYPE_BF16 or MG_DTYPE_F16 */
+    const void *means;
+    const void *log_scales;
+    const void *quats;
+    const void *opacity_logit;
+    const void *sh;
+    const void *mask_logits;
 } mg_gaussians;
 
 /* Pinhole camera with OpenCV axes (x right, y down, z forward).

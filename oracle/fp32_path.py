@@ -135,10 +135,11 @@ def exp32(x):
 # Mask sample (Sec. 3.3): Gumbel-max over the two existence scores.
 # ---------------------------------------------------------------------------
 
-def gumbel_uniforms(n, seed, it):
+def gumbel_uniforms(n, seed, it, index_offset=0):
     """The two uniforms u_0, u_1 of Gaussian i: Philox4x32-10 with
-    counter (i, iter_lo, iter_hi, 0) and key (seed_lo, seed_hi)."""
-    i = np.arange(n, dtype=np.uint64).astype(np.uint32)
+    counter (i, iter_lo, iter_hi, 0) and key (seed_lo, seed_hi); i counts from
+    ``index_offset`` (the Gaussian's index in a batch of scenes)."""
+    i = (np.arange(n, dtype=np.uint64) + np.uint64(index_offset)).astype(np.uint32)
     it = int(it)
     seed = int(seed)
     x = philox4x32_10(i, np.full(n, it & 0xFFFFFFFF, np.uint32),
@@ -152,11 +153,11 @@ def gumbel32(u):
     return -log32(-log32(u))
 
 
-def sample_mask(mask_logits, seed, it):
+def sample_mask(mask_logits, seed, it, index_offset=0):
     """Hard Gumbel-max sample M_i = [l_0 + g_0 >= l_1 + g_1] (index 0 = present,
     ties to 'present'), decided in FP32.  Returns (M uint8, margin f32, u0, u1)."""
     l = np.asarray(mask_logits, dtype=np.float32)
-    u0, u1 = gumbel_uniforms(l.shape[0], seed, it)
+    u0, u1 = gumbel_uniforms(l.shape[0], seed, it, index_offset)
     a0 = l[:, 0] + gumbel32(u0)
     a1 = l[:, 1] + gumbel32(u1)
     d = a0 - a1

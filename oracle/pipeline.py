@@ -34,6 +34,7 @@ class OracleConfig:
     given_mask: np.ndarray | None = None
     eps: float = 1e-3           # straddle band of the alpha floor / power sign (relative)
     eps_T: float = 1e-3         # straddle band of the termination test (relative)
+    index_offset: int = 0       # index of the first Gaussian in a batch of scenes (noise counter)
 
 
 @dataclass
@@ -63,7 +64,8 @@ def sample_masks(g, cfg: OracleConfig):
         return np.ones(n, np.uint8), None
     if cfg.mask_mode == MASK_GIVEN:
         return np.asarray(cfg.given_mask, dtype=np.uint8).copy(), None
-    M, margin, u0, u1 = fp32_path.sample_mask(g.mask_logits, cfg.seed, cfg.iteration)
+    M, margin, u0, u1 = fp32_path.sample_mask(g.mask_logits, cfg.seed, cfg.iteration,
+                                              cfg.index_offset)
     return M, dict(margin=margin, u0=u0, u1=u1)
 
 

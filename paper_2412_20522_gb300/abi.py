@@ -14,7 +14,7 @@ from . import build as _build
 
 MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_CAPACITY, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = range(6)
 MG_MASK_GUMBEL, MG_MASK_ALL_ONES, MG_MASK_GIVEN = 0, 1, 2
-MG_DTYPE_F32 = 0
+MG_DTYPE_F32, MG_DTYPE_BF16, MG_DTYPE_F16 = 0, 1, 2
 MG_MAX_VIEWS = 64
 MG_RECORD_FLOATS = 12
 MG_GRAD2D_FLOATS = 12

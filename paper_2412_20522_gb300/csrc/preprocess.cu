@@ -12,6 +12,10 @@
 // det by Cauchy-Binet, eigenvalue gap as a sum of squares.  The splat is
 // stored in eigen form (major axis u, h_k = -log2(e) / (2 lambda_k)), which
 // stays accurate in FP32 for needle-shaped splats whose conic entries cancel.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <string.h>
+
 #include "internal.cuh"
 
 namespace mg {
@@ -20,6 +24,62 @@ constexpr int kPreThreads = 128;
 
 template <int ROW>
 struct StageStride { static constexpr int value = (ROW % 2 == 0) ? ROW + 1 : ROW; };
+
+// ---------------------------------------------------------------------------
+// Attribute storage: log-scales, quaternions, opacity logits and SH are read
+// as FP32, BF16 or FP16 (ST) and unpacked to FP32 exactly; means and mask
+// scores are always FP32.  Every computation is FP32 after the load.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+template <typename ST>
+__device__ __forceinline__ float ld_attr(const void *base, int64_t i) {
+    if constexpr (sizeof(ST) == 4) {
+        return __ldg(reinterpret_cast<const float *>(base) + i);
+    } else {
+        const unsigned short u = __ldg(reinterpret_cast<const unsigned short *>(base) + i);
+        ST v;
+        memcpy(&v, &u, 2);
+        return to_f32(v);
+    }
+}
+
+template <typename ST>
+__device__ __forceinline__ void ld_quat(const void *base, int64_t i, float q[4]) {
+    if constexpr (sizeof(ST) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(base) + i);
+        q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+    } else {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(base) + i);
+        ST e[4];
+        memcpy(e, &v, 8);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = to_f32(e[k]);
+    }
+}
+
+// Calls f(index, value) for the ROW values of SH row i, with 128-bit loads
+// when rows are 16-byte multiples.
+template <typename ST, int ROW, typename Fn>
+__device__ __forceinline__ void for_sh_row(const void *sh, int64_t i, Fn &&f) {
+    constexpr int PER = 16 / (int)sizeof(ST);
+    if constexpr ((ROW * sizeof(ST)) % 16 == 0) {
+        const uint4 *row = reinterpret_cast<const uint4 *>(sh) + i * (ROW / PER);
+#pragma unroll
+        for (int q = 0; q < ROW / PER; ++q) {
+            const uint4 v = __ldg(row + q);
+            ST e[PER];
+            memcpy(e, &v, 16);
+#pragma unroll
+            for (int u = 0; u < PER; ++u) f(q * PER + u, to_f32(e[u]));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < ROW; ++k) f(k, ld_attr<ST>(sh, i * ROW + k));
+    }
+}
 
 struct Splat32 {
     // decision-path quantities
@@ -139,31 +199,17 @@ __device__ __forceinline__ void eigen2(const Splat32 &S, float &uxo, float &uyo,
 }
 
 // sum_k Y_k sh[i][k][ch] for the three channels, streaming the Gaussian's SH
-// row from global memory (128-bit loads when the row is 16-byte aligned).
-template <int DEG>
-__device__ __forceinline__ void sh_colour(const float *__restrict__ sh, int64_t i, const float *Y,
+// row from global memory.
+template <int DEG, typename ST>
+__device__ __forceinline__ void sh_colour(const void *sh, int64_t i, const float *Y,
                                           float acc[3]) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int ROW = 3 * K;
-    if constexpr (ROW % 4 == 0) {
-        const float4 *row = reinterpret_cast<const float4 *>(sh) + i * (ROW / 4);
-#pragma unroll
-        for (int q = 0; q < ROW / 4; ++q) {
-            const float4 v = __ldg(row + q);
-            const float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[(4 * q + u) % 3] = fmaf(Y[(4 * q + u) / 3], e[u], acc[(4 * q + u) % 3]);
-        }
-    } else {
-        const float *row = sh + i * ROW;
-#pragma unroll
-        for (int f = 0; f < ROW; ++f) acc[f % 3] = fmaf(Y[f / 3], __ldg(row + f), acc[f % 3]);
-    }
+    constexpr int ROW = 3 * (DEG + 1) * (DEG + 1);
+    for_sh_row<ST, ROW>(sh, i, [&](int e, float v) { acc[e % 3] = fmaf(Y[e / 3], v, acc[e % 3]); });
 }
 
 // The SH rows are read only for Gaussians that are visible in a view, one
 // row per lane with 128-bit loads (no row of an invisible Gaussian is read).
-template <int DEG>
+template <int DEG, typename ST>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out) {
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
@@ -175,7 +221,7 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         const uint4 x = philox4x32_10(
             make_uint4((uint32_t)i, (uint32_t)cfg.iteration, (uint32_t)(cfg.iteration >> 32), 0u),
             make_uint2((uint32_t)cfg.seed, (uint32_t)(cfg.seed >> 32)));
-        const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);
+        const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);  // FP32
         const float g0 = -log32(-log32(uniform24(x.x)));
         const float g1 = -log32(-log32(uniform24(x.y)));
         const float d = sb(ad(l.x, g0), ad(l.y, g1));
@@ -187,13 +233,14 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
     }
     out.mask[i] = Mf != 0.0f;
 
-    const float x = __ldg(g.means + 3 * i), y = __ldg(g.means + 3 * i + 1),
-                z = __ldg(g.means + 3 * i + 2);
-    const float ls[3] = {__ldg(g.log_scales + 3 * i), __ldg(g.log_scales + 3 * i + 1),
-                         __ldg(g.log_scales + 3 * i + 2)};
-    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
-    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
-    const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
+    const float *means = reinterpret_cast<const float *>(g.means);
+    const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
+                z = __ldg(means + 3 * i + 2);
+    const float ls[3] = {ld_attr<ST>(g.log_scales, 3 * i), ld_attr<ST>(g.log_scales, 3 * i + 1),
+                         ld_attr<ST>(g.log_scales, 3 * i + 2)};
+    float q[4];
+    ld_quat<ST>(g.quats, i, q);
+    const float op = 1.0f / (1.0f + __expf(-ld_attr<ST>(g.opacity_logit, i)));
 
     for (int v = 0; v < vt.n_views; ++v) {
         if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
@@ -218,7 +265,7 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         float Y[16];
         sh_basis(DEG, dx, dy, dz, Y);
         float rgb[3] = {0.5f, 0.5f, 0.5f};
-        sh_colour<DEG>(g.sh, i, Y, rgb);
+        sh_colour<DEG, ST>(g.sh, i, Y, rgb);
         uint8_t cl = 0;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -424,7 +471,7 @@ __device__ __forceinline__ void cov_backward(const CovState<F> &S, const mg_came
 // dL/dsh accumulates over views in a per-warp shared-memory tile (one row
 // per lane, odd row stride) and leaves with coalesced 128-bit stores; SH rows
 // are read only for Gaussians visible in some view.
-template <int DEG>
+template <int DEG, typename ST>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats sp,
                            const float *__restrict__ grad2d, mg_param_grads out) {
@@ -442,13 +489,14 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
     const int64_t i = gw0 + lane;
     if (lane < nrows) {
         float *drow = dsh + lane * S_;
-        const float x = __ldg(g.means + 3 * i), y = __ldg(g.means + 3 * i + 1),
-                    z = __ldg(g.means + 3 * i + 2);
-        const float ls[3] = {__ldg(g.log_scales + 3 * i), __ldg(g.log_scales + 3 * i + 1),
-                             __ldg(g.log_scales + 3 * i + 2)};
-        const float4 q4 = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
-        const float q[4] = {q4.x, q4.y, q4.z, q4.w};
-        const float op = 1.0f / (1.0f + __expf(-__ldg(g.opacity_logit + i)));
+        const float *means = reinterpret_cast<const float *>(g.means);
+        const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
+                    z = __ldg(means + 3 * i + 2);
+        const float ls[3] = {ld_attr<ST>(g.log_scales, 3 * i), ld_attr<ST>(g.log_scales, 3 * i + 1),
+                             ld_attr<ST>(g.log_scales, 3 * i + 2)};
+        float q[4];
+        ld_quat<ST>(g.quats, i, q);
+        const float op = 1.0f / (1.0f + __expf(-ld_attr<ST>(g.opacity_logit, i)));
 
         float d_mean[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0}, d_op = 0.0f,
               d_M = 0.0f;
@@ -486,21 +534,9 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
                     float t[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) t[k] = 0.0f;
-                    if constexpr (ROW % 4 == 0) {
-                        const float4 *row = reinterpret_cast<const float4 *>(g.sh) + i * (ROW / 4);
-#pragma unroll
-                        for (int qq = 0; qq < ROW / 4; ++qq) {
-                            const float4 sv = __ldg(row + qq);
-                            const float e[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                t[(4 * qq + u) / 3] = fmaf(grgb[(4 * qq + u) % 3], e[u], t[(4 * qq + u) / 3]);
-                        }
-                    } else {
-                        const float *row = g.sh + i * ROW;
-#pragma unroll
-                        for (int f = 0; f < ROW; ++f) t[f / 3] = fmaf(grgb[f % 3], __ldg(row + f), t[f / 3]);
-                    }
+                    for_sh_row<ST, ROW>(g.sh, i, [&](int e, float v) {
+                        t[e / 3] = fmaf(grgb[e % 3], v, t[e / 3]);
+                    });
                     float Yx[16], Yy[16], Yz[16];
                     sh_basis_grad(DEG, dx, dy, dz, Yx, Yy, Yz);
                     float gd[3] = {0, 0, 0};
@@ -588,16 +624,49 @@ using namespace mg;
 
 static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+static size_t attr_bytes(int32_t dtype) { return dtype == MG_DTYPE_F32 ? 4 : 2; }
+
 static mg_status check_gaussians(const mg_gaussians *g) {
     if (g == nullptr || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3 ||
-        g->dtype != MG_DTYPE_F32)
+        (g->dtype != MG_DTYPE_F32 && g->dtype != MG_DTYPE_BF16 && g->dtype != MG_DTYPE_F16))
         return MG_ERR_INVALID_ARG;
     if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->sh ||
                      !g->mask_logits))
         return MG_ERR_INVALID_ARG;
-    if (!aligned(g->quats, 16) || !aligned(g->mask_logits, 8)) return MG_ERR_INVALID_ARG;
+    const size_t eb = attr_bytes(g->dtype);
+    if (!aligned(g->quats, 4 * eb) || !aligned(g->mask_logits, 8) || !aligned(g->sh, 16) ||
+        !aligned(g->means, 4) || !aligned(g->log_scales, eb) || !aligned(g->opacity_logit, eb))
+        return MG_ERR_INVALID_ARG;
     if (g->n >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
     return MG_OK;
+}
+
+template <int DEG>
+static void launch_preprocess(int32_t dtype, dim3 grid, cudaStream_t s, const ViewTable &vt,
+                              const mg_gaussians &g, const mg_raster_cfg &cfg,
+                              const mg_splats &out) {
+    if (dtype == MG_DTYPE_BF16)
+        preprocess_kernel<DEG, __nv_bfloat16><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, out);
+    else if (dtype == MG_DTYPE_F16)
+        preprocess_kernel<DEG, __half><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, out);
+    else
+        preprocess_kernel<DEG, float><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, out);
+}
+
+template <int DEG>
+static void launch_preprocess_backward(int32_t dtype, dim3 grid, cudaStream_t s,
+                                       const ViewTable &vt, const mg_gaussians &g,
+                                       const mg_raster_cfg &cfg, const mg_splats &sp,
+                                       const float *grad2d, const mg_param_grads &out) {
+    if (dtype == MG_DTYPE_BF16)
+        preprocess_backward_kernel<DEG, __nv_bfloat16><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, sp,
+                                                                                   grad2d, out);
+    else if (dtype == MG_DTYPE_F16)
+        preprocess_backward_kernel<DEG, __half><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, sp, grad2d,
+                                                                            out);
+    else
+        preprocess_backward_kernel<DEG, float><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, sp, grad2d,
+                                                                           out);
 }
 
 static mg_status check_views(const mg_gaussians *g, const mg_view *views, int32_t n_views,
@@ -628,10 +697,10 @@ extern "C" mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, 
     const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
     cudaStream_t s = (cudaStream_t)stream;
     switch (g->sh_degree) {
-        case 0: preprocess_kernel<0><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
-        case 1: preprocess_kernel<1><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
-        case 2: preprocess_kernel<2><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
-        default: preprocess_kernel<3><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *out); break;
+        case 0: launch_preprocess<0>(g->dtype, grid, s, vt, *g, *cfg, *out); break;
+        case 1: launch_preprocess<1>(g->dtype, grid, s, vt, *g, *cfg, *out); break;
+        case 2: launch_preprocess<2>(g->dtype, grid, s, vt, *g, *cfg, *out); break;
+        default: launch_preprocess<3>(g->dtype, grid, s, vt, *g, *cfg, *out); break;
     }
     return mg_host::launch_status();
 }
@@ -654,10 +723,10 @@ extern "C" mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view
     const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
     cudaStream_t s = (cudaStream_t)stream;
     switch (g->sh_degree) {
-        case 0: preprocess_backward_kernel<0><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
-        case 1: preprocess_backward_kernel<1><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
-        case 2: preprocess_backward_kernel<2><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
-        default: preprocess_backward_kernel<3><<<grid, kPreThreads, 0, s>>>(vt, *g, *cfg, *splats, grad2d, *out); break;
+        case 0: launch_preprocess_backward<0>(g->dtype, grid, s, vt, *g, *cfg, *splats, grad2d, *out); break;
+        case 1: launch_preprocess_backward<1>(g->dtype, grid, s, vt, *g, *cfg, *splats, grad2d, *out); break;
+        case 2: launch_preprocess_backward<2>(g->dtype, grid, s, vt, *g, *cfg, *splats, grad2d, *out); break;
+        default: launch_preprocess_backward<3>(g->dtype, grid, s, vt, *g, *cfg, *splats, grad2d, *out); break;
     }
     return mg_host::launch_status();
 }

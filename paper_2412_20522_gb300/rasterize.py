@@ -64,15 +64,26 @@ def make_views(cams, ranges=None):
     return arr
 
 
+_STORAGE = {torch.float32: abi.MG_DTYPE_F32, torch.bfloat16: abi.MG_DTYPE_BF16,
+            torch.float16: abi.MG_DTYPE_F16}
+STORED = ("log_scales", "quats", "opacity_logit", "sh")
+
+
 def _gaussians_struct(p: dict, sh_degree: int) -> abi.mg_gaussians:
+    """Means and mask logits are FP32; log-scales, quaternions, opacity logits
+    and SH share one storage type (FP32, BF16 or FP16)."""
     g = abi.mg_gaussians()
     g.n = int(p["means"].shape[0])
     g.sh_degree = int(sh_degree)
-    g.dtype = abi.MG_DTYPE_F32
+    st = p["sh"].dtype
+    if st not in _STORAGE:
+        raise ValueError(f"unsupported attribute storage {st}")
+    g.dtype = _STORAGE[st]
     for name in PARAM_NAMES:
         t = p[name]
-        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
-            raise ValueError(f"{name}: contiguous float32 CUDA tensor required")
+        want = st if name in STORED else torch.float32
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: contiguous {want} CUDA tensor required")
         setattr(g, name, t.data_ptr())
     return g
 
@@ -250,7 +261,8 @@ class Rasterizer:
                                s["cfg"], self._buf["final_T"], self._buf["n_contrib"], dL_dimage,
                                grad2d, self.bwd_count if count_iterations else None, stream)
         if out is None:
-            out = {k: torch.empty_like(s["params"][k]) for k in PARAM_NAMES}
+            out = {k: torch.empty(s["params"][k].shape, dtype=torch.float32, device=self.device)
+                   for k in PARAM_NAMES}
         ev.end("render_bwd")
         pg = abi.mg_param_grads()
         for k in PARAM_NAMES:
@@ -296,8 +308,10 @@ class MaskedRasterize(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dimg):
         out = ctx.rast.backward(dimg.contiguous())
-        return (out["means"], out["log_scales"], out["quats"], out["opacity_logit"], out["sh"],
-                out["mask_logits"], None, None, None)
+        p = ctx.rast._state["params"]
+        # gradients are computed in FP32; autograd wants the parameters' dtype
+        g = [out[k].to(p[k].dtype) for k in PARAM_NAMES]
+        return (*g, None, None, None)
 
 
 def rasterize(params: dict, cams, cfg: RasterConfig, rast: Rasterizer | None = None):

@@ -1,0 +1,119 @@
+"""Batched forms: a CUDA-graph replay of the whole step equals the eager step
+bit for bit; an uneven batch of scenes (disjoint Gaussian ranges, one camera
+each, mixed resolutions) in one launch sequence matches the oracle per scene;
+the tile-shape autotuner picks a measured shape and caches it."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import rel_l2, to_device
+from oracle import pipeline
+from paper_2412_20522_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def test_graph_replay_equals_eager_step():
+    from paper_2412_20522_gb300.autotune import GraphStep
+    from paper_2412_20522_gb300.rasterize import PARAM_NAMES, RasterConfig, Rasterizer
+    g = scenes.cluster_gaussians(30_000, seed=3, centre_radius=1.5, reject_radius=2.0,
+                                 log_scale_mu=-4.0, log_scale_sigma=0.5)
+    cams = [scenes.ring_camera(2 * math.pi * k / 4, 4.0, 160, 120, 130.0) for k in range(4)]
+    tgt = torch.cat([torch.as_tensor(scenes.target_image(c.height, c.width, seed=k)).reshape(-1)
+                     for k, c in enumerate(cams)]).cuda()
+    p = to_device(g)
+    cfg = RasterConfig(bg=(0.1, 0.2, 0.3), seed=9, iteration=4)
+    gs = GraphStep(p, cams, cfg, tgt)
+    gs.replay()
+    gs.replay()
+    torch.cuda.synchronize()
+    assert gs.status() == 0
+    rast = Rasterizer()
+    img = rast.forward(p, cams, cfg)
+    loss, dimg = rast.l1_loss_grad(img, tgt)
+    grads = rast.backward(dimg)
+    torch.cuda.synchronize()
+    assert torch.equal(img, gs.image)
+    for k in PARAM_NAMES:
+        # atomics may reorder FP32 sums: equal up to rounding
+        assert rel_l2(gs.grads[k].cpu().numpy(), grads[k].cpu().numpy()) < 1e-5, k
+    assert abs(float(loss) - float(gs.loss)) < 1e-6
+
+
+def _tile_lists(rast, t0, nt, r0):
+    so = rast.splat_outputs()
+    rng = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)[t0:t0 + nt]
+    vals = so["sorted_vals"].cpu().numpy().view(np.uint32)
+    return [vals[s:e].astype(np.int64) - r0 for s, e in rng]
+
+
+def test_uneven_scene_batch_matches_oracle_per_scene():
+    from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
+    sizes = [1500, 4000, 9000]
+    sc = [scenes.cluster_gaussians(n, seed=40 + k, centre_radius=1.5, reject_radius=2.0,
+                                   log_scale_mu=-4.0, log_scale_sigma=0.5)
+          for k, n in enumerate(sizes)]
+    cams = [scenes.ring_camera(0.7 * k, 4.0, w, h, 0.8 * w)
+            for k, (w, h) in enumerate([(72, 48), (100, 75), (131, 97)])]
+    cat = {k: np.concatenate([getattr(s, k) for s in sc]) for k in
+           ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")}
+    gall = scenes.Gaussians(**cat, sh_degree=3)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    ranges = [(int(o), n) for o, n in zip(offs, sizes)]
+    cfg = RasterConfig(bg=(0.3, 0.3, 0.3), seed=77, iteration=2)
+    rast = Rasterizer()
+    img = rast.forward(to_device(gall), cams, cfg, view_ranges=ranges)
+    tg = [scenes.target_image(c.height, c.width, seed=60 + k) for k, c in enumerate(cams)]
+    torch.cuda.synchronize()
+    gimg = img.cpu().numpy()
+    so = rast.splat_outputs()
+    mask = so["mask"].cpu().numpy()
+    po = 0
+    t0 = 0
+    dimgs = []
+    orc = []
+    for k, (s, cam) in enumerate(zip(sc, cams)):
+        ocfg = pipeline.OracleConfig(bg=cfg.bg, seed=cfg.seed, iteration=cfg.iteration,
+                                     index_offset=int(offs[k]), eps=1e-4)
+        views, M, minfo = pipeline.forward(s, [cam], ocfg)
+        v = views[0]
+        assert np.array_equal(mask[offs[k]:offs[k] + sizes[k]], M)
+        gx, gy = v.fp32["grid"]
+        lists = _tile_lists(rast, t0, gx * gy, int(offs[k]))
+        for t, lst in enumerate(lists):
+            s0, e0 = v.ranges[t]
+            assert np.array_equal(lst, v.sorted_vals[s0:e0].astype(np.int64)), (k, t)
+        n = 3 * cam.width * cam.height
+        im = gimg[po:po + n].reshape(3, cam.height, cam.width)
+        straddle = (v.out["flags"] & 11) != 0
+        d = np.abs(im - v.out["image"]).max(0)
+        assert not ((d > 2e-4) & ~straddle).any()
+        _, dg = pipeline.l1_loss_grad(v.out["image"], tg[k])
+        dg = dg * (~straddle)[None]
+        dimgs.append(dg)
+        orc.append((s, cam, ocfg, views, M, minfo, dg))
+        po += n
+        t0 += gx * gy
+    flat = np.concatenate([d.reshape(-1) for d in dimgs]).astype(np.float32)
+    out = rast.backward(torch.as_tensor(flat).cuda())
+    torch.cuda.synchronize()
+    for k, (s, cam, ocfg, views, M, minfo, dg) in enumerate(orc):
+        grads, _ = pipeline.backward(s, [cam], ocfg, views, M, minfo, [dg])
+        sl = slice(int(offs[k]), int(offs[k]) + sizes[k])
+        for name in ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits"):
+            e = rel_l2(out[name][sl].cpu().numpy(), grads[name])
+            assert e < 1e-3, (k, name, e)
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    from paper_2412_20522_gb300 import autotune
+    monkeypatch.setenv("MASKGS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    g, cams, tgt = scenes.tiny_workload(8000)
+    p = to_device(g)
+    t = torch.as_tensor(tgt).cuda().reshape(-1)
+    best = autotune.autotune_tile(p, cams, t, steps=2)
+    assert best in autotune.TILE_SHAPES
+    assert (tmp_path / "tune.json").exists()
+    assert autotune.autotune_tile(p, cams, t, steps=2) == best      # from the cache
