@@ -1,7 +1,9 @@
 """Attribute storage in BF16 / FP16 (log-scales, quaternions, opacity logits,
 SH; means and mask scores stay FP32): values are unpacked to FP32 exactly, so
 the step must be bit-identical to the FP32 step on the unpacked values, and
-match the oracle on them like any FP32 run."""
+match the oracle on them like any FP32 run.  (Gradients are summed by float
+atomics whose order varies from run to run, so they are compared to a
+rounding-level tolerance; every forward output is compared bitwise.)"""
 import numpy as np
 import pytest
 import torch
@@ -12,6 +14,7 @@ from paper_2412_20522_gb300 import scenes
 pytestmark = pytest.mark.gpu
 
 STORED = ("log_scales", "quats", "opacity_logit", "sh")
+GRADS = ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")
 
 
 def _step(params, cams, tgt):
@@ -38,7 +41,12 @@ def test_half_storage_is_bit_identical_to_fp32_of_unpacked(dt):
     a = _step(packed, cams, tgt)
     b = _step(unpacked, cams, tgt)
     for k in a:
-        assert torch.equal(a[k], b[k]), k
+        if k in GRADS:
+            scale = float(b[k].abs().max()) + 1e-30
+            err = float((a[k] - b[k]).abs().max()) / scale
+            assert err < 1e-5, (k, err)
+        else:
+            assert torch.equal(a[k], b[k]), k
     # and storage changed the inputs: the FP32 originals give another image
     c = _step(p32, cams, tgt)
     assert not torch.equal(a["image"], c["image"])
