@@ -66,7 +66,27 @@ typedef enum {
     MG_ERR_UNSUPPORTED = 5
 } mg_status;
 
-enum { MG_MASK_GUMBEL = 0, MG_MASK_ALL_ONES = 1, MG_MASK_GIVEN = 2 };
+/* Mask modes (mg_raster_cfg.mask_mode):
+ *   MG_MASK_GUMBEL    M_i sampled by Gumbel-max over the two scores, gradient
+ *                     by the straight-through Gumbel-softmax (Sec. 3.3);
+ *   MG_MASK_ALL_ONES  M_i = 1 (plain 3DGS, Eq. 1-2);
+ *   MG_MASK_GIVEN     M_i read from given_mask;
+ *   MG_MASK_STE       the deterministic ablation of Sec. 4.3 ("Effect of
+ *                     Gumbel Softmax"): M_i = [l_0 - l_1 > ste_logit], i.e.
+ *                     sigmoid(l_0 - l_1) above a threshold, with the
+ *                     straight-through gradient of sigmoid(l_0 - l_1).
+ * Mask application (mg_raster_cfg.mask_apply):
+ *   MG_APPLY_RASTER   masked rasterisation, Eq. 3-4 (the method);
+ *   MG_APPLY_OPACITY  the ablation of Sec. 4.3 ("Effect of Masked
+ *                     Rasterization"): the splat's opacity is M_i o_i and it
+ *                     blends as in Eq. 1-2, so a masked splat (alpha 0) is
+ *                     filtered and receives no gradient; dL/dM_i = o_i dL/do'.
+ * Mask loss (mg_raster_cfg.mask_loss), weighted by lambda_m (Eq. 8):
+ *   MG_MASK_LOSS_L2   L_m = (sum_i M_i / N)^2 (Eq. 7);
+ *   MG_MASK_LOSS_L1   L_m = sum_i M_i / N (the L1 form of Appendix C). */
+enum { MG_MASK_GUMBEL = 0, MG_MASK_ALL_ONES = 1, MG_MASK_GIVEN = 2, MG_MASK_STE = 3 };
+enum { MG_APPLY_RASTER = 0, MG_APPLY_OPACITY = 1 };
+enum { MG_MASK_LOSS_L2 = 0, MG_MASK_LOSS_L1 = 1 };
 enum { MG_DTYPE_F32 = 0, MG_DTYPE_BF16 = 1, MG_DTYPE_F16 = 2 };
 enum { MG_MAX_VIEWS = 64, MG_RECORD_FLOATS = 12, MG_GRAD2D_FLOATS = 12 };
 
@@ -126,16 +146,22 @@ typedef struct {
  * Gumbel noise: u_k from Philox4x32-10 (Salmon et al., SC'11) with counter
  * (i, iteration_lo, iteration_hi, 0) and key (seed_lo, seed_hi), outputs 0 and
  * 1 mapped to (2 (x >> 9) + 1) 2^-24.  mask_mode MG_MASK_GIVEN reads
- * given_mask[n] (device, 0/1 bytes). */
+ * given_mask[n] (device, 0/1 bytes).  A view's scene is its Gaussian range:
+ * views with equal ranges are views of one scene, and L_m is summed over the
+ * distinct ranges, each over its own N = gaussian_count. */
 typedef struct {
     int32_t tile_w, tile_h;
     float bg[3];
     float tau;               /* Gumbel-softmax temperature, > 0 */
     uint64_t seed;
     uint64_t iteration;
-    int32_t mask_mode;
-    int32_t reserved;
+    int32_t mask_mode;       /* MG_MASK_* */
+    int32_t mask_apply;      /* MG_APPLY_* */
     const uint8_t *given_mask;
+    float lambda_m;          /* weight of L_m in L = L_render + lambda_m L_m (Eq. 8); 0 = off */
+    int32_t mask_loss;       /* MG_MASK_LOSS_* */
+    float ste_logit;         /* MG_MASK_STE threshold on l_0 - l_1 (FP32 comparison) */
+    int32_t reserved;        /* 0 */
 } mg_raster_cfg;
 
 /* Per-view preprocess outputs (R = sum_v gaussian_count_v records):
@@ -147,9 +173,15 @@ typedef struct {
  *     (1 if o < 1/255: the splat never reaches the floor); r, g, b; depth tz.
  *   tiles_touched[R] u32 (0 = culled), radius[R] i32 (pixels, 0 = culled),
  *   clamp[R] u8 (bit c: colour channel c was clamped at 0).
+ *   With MG_APPLY_OPACITY the stored opacity is M o (+0 for a masked splat,
+ *   e_min = 1).
  * Per-Gaussian (n):
  *   mask[n] u8 sampled M_i; mask_soft[n] f32 soft sample y_0 of the
- *   Gumbel-softmax (1 for all-ones / given masks). */
+ *   Gumbel-softmax (sigmoid(l_0 - l_1) for MG_MASK_STE, 1 for all-ones /
+ *   given masks).
+ * Per view (n_views), nullable: mask_count[v] u32 = sum of M_i over view v's
+ *   Gaussian range (written by mg_preprocess; needed by mg_mask_loss and by
+ *   mg_preprocess_backward when lambda_m != 0). */
 typedef struct {
     float *record;
     uint32_t *tiles_touched;
@@ -157,6 +189,7 @@ typedef struct {
     uint8_t *clamp;
     uint8_t *mask;
     float *mask_soft;
+    uint32_t *mask_count;
 } mg_splats;
 
 /* Gradients w.r.t. the per-view splats, grad2d[R][12] FP32:
@@ -303,13 +336,65 @@ mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_val
 /* Chain rule from grad2d through the 2D covariance (P = J W R S), the
  * quaternion normalisation, the scale exponential, the projection and the
  * SH colour (zero for clamped channels) to every parameter, summed over
- * views; mask_logits receive dL/dM y_0 (1 - y_0) / tau and its negative
- * (straight-through Gumbel-softmax, Sec. 3.3) for MG_MASK_GUMBEL, zero
- * otherwise.  Outputs are overwritten. */
+ * views.  dL/dM_i is the sum over views of grad2d's dM (MG_APPLY_RASTER) or
+ * o_i times the sum of dL/do' (MG_APPLY_OPACITY, where opacity_logit receives
+ * M_i dL/do' sigma'), plus lambda_m dL_m/dM_i of the Gaussian's scene (first
+ * view whose range holds i): 2 count / N^2 (L2) or 1 / N (L1), from
+ * splats->mask_count.  mask_logits receive dL/dM y_0 (1 - y_0) / tau and its
+ * negative (straight-through Gumbel-softmax, Sec. 3.3) for MG_MASK_GUMBEL,
+ * dL/dM p (1 - p) and its negative with p = sigmoid(l_0 - l_1) for
+ * MG_MASK_STE, zero otherwise.  Outputs are overwritten. */
 mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view *views,
                                  int32_t n_views, const mg_raster_cfg *cfg,
                                  const mg_splats *splats, const float *grad2d,
                                  const mg_param_grads *out, mg_stream_t stream);
+
+/* ---- 8. mask loss (Sec. 3.5, Eq. 7-8) ----------------------------------------- */
+/* *loss (device f32) += lambda_m * sum over scenes of L_m, from
+ * splats->mask_count (a scene = a distinct Gaussian range among the views,
+ * N = its gaussian_count; empty ranges add nothing).  The gradient is added
+ * by mg_preprocess_backward.  One tiny kernel; the caller zeroes *loss. */
+mg_status mg_mask_loss(const mg_splats *splats, const mg_view *views, int32_t n_views,
+                       const mg_raster_cfg *cfg, float *loss, mg_stream_t stream);
+
+/* ---- 9. pruning (Sec. 3.5) ------------------------------------------------------- */
+/* Draws n_draws (1..1024) independent masks per Gaussian and keeps the
+ * Gaussians sampled present at least once: keep[i] = OR_d [l_0 + g_0 >=
+ * l_1 + g_1] (u8 0/1), draw d with Philox counter (i, iteration_lo,
+ * iteration_hi, d + 1) and key (seed_lo, seed_hi) -- disjoint from the
+ * training draws (last counter word 0) -- and the same FP32 decision as
+ * mg_preprocess.  The paper draws 10 times.  g->mask_logits is read (FP32). */
+mg_status mg_prune_sample(const mg_gaussians *g, uint64_t seed, uint64_t iteration,
+                          int32_t n_draws, uint8_t *keep, mg_stream_t stream);
+
+/* Writable Gaussian arrays, laid out as in mg_gaussians with the same dtype. */
+typedef struct {
+    void *means;
+    void *log_scales;
+    void *quats;
+    void *opacity_logit;
+    void *sh;
+    void *mask_logits;
+} mg_gaussian_arrays;
+
+/* Stream compaction of every attribute array of src to dst (rows with
+ * keep[i] != 0, order kept; dst has room for src->n rows and must not
+ * overlap src): *d_n_kept (device i64) = number kept, new_index[i] (device
+ * i32, nullable) = row of i in dst or -1.  Single-pass scan with decoupled
+ * look-back; a wait that gives up raises MG_ERR_TIMEOUT in d_status.
+ * workspace: mg_compact_workspace_bytes(n) bytes, any content. */
+mg_status mg_compact(const mg_gaussians *src, const uint8_t *keep, const mg_gaussian_arrays *dst,
+                     int32_t *new_index, int64_t *d_n_kept, void *workspace,
+                     size_t workspace_bytes, mg_status_word *d_status, mg_stream_t stream);
+size_t mg_compact_workspace_bytes(int64_t n);
+
+/* ---- 10. inference render (Sec. 4.2, rendering speed) ----------------------- */
+/* Forward-only blend of splats made with MG_MASK_ALL_ONES (a pruned model
+ * renders every Gaussian it keeps; masked records, if any, are skipped):
+ * image[3][H][W] per view, as mg_render, without final_T and n_contrib. */
+mg_status mg_render_inference(const mg_splats *splats, const uint32_t *sorted_vals,
+                              const uint32_t *ranges, const mg_view *views, int32_t n_views,
+                              const mg_raster_cfg *cfg, float *image, mg_stream_t stream);
 
 /* ---- helpers ------------------------------------------------------------------ */
 /* Synchronises `stream` and copies the device status word to *h_out (host). */

@@ -17,7 +17,11 @@ The oracle is a plain, slow, independent restatement of the method:
                      brute-force per-pixel forms, plain 3DGS Eq. 1-2, and the
                      mask/colour/alpha gradients of Eq. 6 and Appendix A.
 * ``pipeline``    -- the forward+backward of one training step built from
-                     the above.
+                     the above, with the mask loss of Eq. 7-8 and the
+                     ablations of Sec. 4.3 (threshold mask, mask x opacity).
+* ``pruning``     -- the pruning rule of Sec. 3.5 (keep what is sampled
+                     present in any of n draws) and the order-keeping
+                     compaction of the survivors.
 
 It shares no code with the CUDA path; the only common module is the seeded
 input generator ``paper_2412_20522_gb300.scenes``.

@@ -135,16 +135,18 @@ def exp32(x):
 # Mask sample (Sec. 3.3): Gumbel-max over the two existence scores.
 # ---------------------------------------------------------------------------
 
-def gumbel_uniforms(n, seed, it, index_offset=0):
+def gumbel_uniforms(n, seed, it, index_offset=0, draw=0):
     """The two uniforms u_0, u_1 of Gaussian i: Philox4x32-10 with
-    counter (i, iter_lo, iter_hi, 0) and key (seed_lo, seed_hi); i counts from
-    ``index_offset`` (the Gaussian's index in a batch of scenes)."""
+    counter (i, iter_lo, iter_hi, draw) and key (seed_lo, seed_hi); i counts
+    from ``index_offset`` (the Gaussian's index in a batch of scenes).  The
+    training sample is draw 0; the pruning draws are 1, 2, ..."""
     i = (np.arange(n, dtype=np.uint64) + np.uint64(index_offset)).astype(np.uint32)
     it = int(it)
     seed = int(seed)
     x = philox4x32_10(i, np.full(n, it & 0xFFFFFFFF, np.uint32),
                       np.full(n, (it >> 32) & 0xFFFFFFFF, np.uint32),
-                      np.zeros(n, np.uint32), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+                      np.full(n, int(draw) & 0xFFFFFFFF, np.uint32),
+                      seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     return uniform24(x[0]), uniform24(x[1])
 
 
@@ -153,15 +155,37 @@ def gumbel32(u):
     return -log32(-log32(u))
 
 
-def sample_mask(mask_logits, seed, it, index_offset=0):
+def sample_mask(mask_logits, seed, it, index_offset=0, draw=0):
     """Hard Gumbel-max sample M_i = [l_0 + g_0 >= l_1 + g_1] (index 0 = present,
     ties to 'present'), decided in FP32.  Returns (M uint8, margin f32, u0, u1)."""
     l = np.asarray(mask_logits, dtype=np.float32)
-    u0, u1 = gumbel_uniforms(l.shape[0], seed, it, index_offset)
+    u0, u1 = gumbel_uniforms(l.shape[0], seed, it, index_offset, draw)
     a0 = l[:, 0] + gumbel32(u0)
     a1 = l[:, 1] + gumbel32(u1)
     d = a0 - a1
     return (d >= f32(0.0)).astype(np.uint8), d, u0, u1
+
+
+def ste_mask(mask_logits, ste_logit):
+    """Deterministic threshold mask of the straight-through ablation (Sec. 4.3,
+    "Effect of Gumbel Softmax"): M_i = [sigmoid(l_0 - l_1) > theta], decided
+    as l_0 - l_1 > logit(theta) (sigmoid is increasing), one FP32 subtraction
+    and one comparison.  Returns (M uint8, d = l_0 - l_1 f32)."""
+    l = np.asarray(mask_logits, dtype=np.float32)
+    d = l[:, 0] - l[:, 1]
+    return (d > f32(ste_logit)).astype(np.uint8), d
+
+
+def prune_keep(mask_logits, seed, it, n_draws=10, index_offset=0):
+    """Pruning rule of Sec. 3.5: sample every Gaussian n_draws times (draws
+    1..n_draws of the noise stream) and keep those sampled present at least
+    once.  Returns keep (uint8)."""
+    l = np.asarray(mask_logits, dtype=np.float32)
+    keep = np.zeros(l.shape[0], np.uint8)
+    for d in range(1, int(n_draws) + 1):
+        M, _, _, _ = sample_mask(l, seed, it, index_offset, draw=d)
+        keep |= M
+    return keep
 
 
 # ---------------------------------------------------------------------------

@@ -8,6 +8,11 @@ summed over views.  Backward: Eq. 6 + Appendix A for the mask, the colour and
 alpha gradients of the same blend, then the exact derivative of the splat
 (autograd in FP64) down to the Gaussian parameters and, through the
 Gumbel-softmax straight-through estimator, to the two existence scores.
+The mask loss of Eq. 7-8 (lambda_m L_m) is added to the loss and its
+gradient flows through the same straight-through mask.  Ablations of
+Sec. 4.3: the deterministic threshold mask with a sigmoid straight-through
+gradient, and the mask multiplied into the opacity instead of masked
+rasterisation.
 """
 from __future__ import annotations
 
@@ -18,7 +23,9 @@ import torch
 
 from . import binning, fp32_path, preprocess, render
 
-MASK_GUMBEL, MASK_ALL_ONES, MASK_GIVEN = 0, 1, 2
+MASK_GUMBEL, MASK_ALL_ONES, MASK_GIVEN, MASK_STE = 0, 1, 2, 3
+APPLY_RASTER, APPLY_OPACITY = 0, 1
+LOSS_L2, LOSS_L1 = 0, 1
 PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")
 
 
@@ -35,6 +42,10 @@ class OracleConfig:
     eps: float = 1e-3           # straddle band of the alpha floor / power sign (relative)
     eps_T: float = 1e-3         # straddle band of the termination test (relative)
     index_offset: int = 0       # index of the first Gaussian in a batch of scenes (noise counter)
+    mask_apply: int = APPLY_RASTER   # masked rasterisation (Eq. 3-4) or mask x opacity (Sec. 4.3)
+    lambda_m: float = 0.0       # weight of the mask loss, Eq. 8
+    mask_loss: int = LOSS_L2    # Eq. 7 (squared mean) or the L1 form of Appendix C
+    ste_logit: float = 0.0      # MASK_STE threshold on l_0 - l_1 (FP32)
 
 
 @dataclass
@@ -64,9 +75,34 @@ def sample_masks(g, cfg: OracleConfig):
         return np.ones(n, np.uint8), None
     if cfg.mask_mode == MASK_GIVEN:
         return np.asarray(cfg.given_mask, dtype=np.uint8).copy(), None
+    if cfg.mask_mode == MASK_STE:
+        M, d = fp32_path.ste_mask(g.mask_logits, cfg.ste_logit)
+        return M, dict(margin=d)
     M, margin, u0, u1 = fp32_path.sample_mask(g.mask_logits, cfg.seed, cfg.iteration,
                                               cfg.index_offset)
     return M, dict(margin=margin, u0=u0, u1=u1)
+
+
+def mask_loss(M, cfg: OracleConfig) -> float:
+    """lambda_m L_m of Eq. 7-8 (L2: the squared fraction of present Gaussians;
+    L1: the fraction itself), over the N Gaussians of the scene."""
+    n = len(M)
+    if n == 0 or cfg.lambda_m == 0.0:
+        return 0.0
+    frac = float(np.sum(np.asarray(M, np.float64))) / n
+    return cfg.lambda_m * (frac * frac if cfg.mask_loss == LOSS_L2 else frac)
+
+
+def _mask_st(p64, M, minfo, cfg: OracleConfig):
+    """The mask as a differentiable tensor: hard value, straight-through
+    gradient (Sec. 3.3 for Gumbel-softmax, the sigmoid for the threshold
+    ablation); a constant for all-ones and given masks."""
+    if cfg.mask_mode == MASK_GUMBEL:
+        return preprocess.mask_straight_through(p64["mask_logits"], M, minfo["u0"], minfo["u1"],
+                                                cfg.tau)[0]
+    if cfg.mask_mode == MASK_STE:
+        return preprocess.mask_straight_through_ste(p64["mask_logits"], M)[0]
+    return torch.as_tensor(np.asarray(M, np.float64))
 
 
 def forward(g, cams, cfg: OracleConfig):
@@ -93,7 +129,11 @@ def forward(g, cams, cfg: OracleConfig):
         conic[vis] = sp["conic"].numpy()
         opac[vis] = sp["opacity"].numpy()
         rgb[vis] = sp["rgb"].numpy()
-        splats = render.SplatsF64(mean2d, conic, opac, rgb, M.astype(np.float64))
+        if cfg.mask_apply == APPLY_OPACITY:
+            # ablation: the mask scales the opacity, every splat blends unmasked
+            splats = render.SplatsF64(mean2d, conic, opac * M, rgb, np.ones(n))
+        else:
+            splats = render.SplatsF64(mean2d, conic, opac, rgb, M.astype(np.float64))
         out = render.render_tiled(splats, cam.width, cam.height, cfg.tile_w, cfg.tile_h,
                                   svals, ranges, cfg.bg, True, cfg.eps, cfg.eps_T)
         views.append(OracleView(fp, keys, vals, offsets, K, skeys, svals, ranges, vis,
@@ -124,21 +164,27 @@ def backward(g, cams, cfg: OracleConfig, views, M, minfo, dL_dimages):
         dmask_total += rg["dmask"]
 
     p64 = {k: t.clone().requires_grad_(True) for k, t in gaussian_params64(g).items()}
+    Mst = _mask_st(p64, M, minfo, cfg)
     total = torch.zeros((), dtype=torch.float64)
     for cam, v, rg in zip(cams, views, per_view):
         vis = torch.as_tensor(v.visible)
         sub = {k: t[vis] for k, t in p64.items()}
         sp = preprocess.splat(sub, cam)
         idx = v.visible
+        opacity = sp["opacity"]
+        if cfg.mask_apply == APPLY_OPACITY:
+            opacity = opacity * Mst[vis]          # o' = M o
         total = total + (sp["mean2d"] * torch.as_tensor(rg["dmean2d"][idx])).sum()
         total = total + (sp["conic"] * torch.as_tensor(rg["dconic"][idx])).sum()
-        total = total + (sp["opacity"] * torch.as_tensor(rg["dopacity"][idx])).sum()
+        total = total + (opacity * torch.as_tensor(rg["dopacity"][idx])).sum()
         total = total + (sp["rgb"] * torch.as_tensor(rg["drgb"][idx])).sum()
-    if cfg.mask_mode == MASK_GUMBEL:
-        Mst, _ = preprocess.mask_straight_through(p64["mask_logits"], M, minfo["u0"],
-                                                  minfo["u1"], cfg.tau)
+    if cfg.mask_apply == APPLY_RASTER:
         total = total + (Mst * torch.as_tensor(dmask_total)).sum()
-    total.backward()
+    if cfg.lambda_m != 0.0 and g.n > 0:
+        frac = Mst.sum() / g.n
+        total = total + cfg.lambda_m * (frac * frac if cfg.mask_loss == LOSS_L2 else frac)
+    if total.requires_grad:
+        total.backward()
     grads = {k: (t.grad.numpy() if t.grad is not None else np.zeros(tuple(t.shape)))
              for k, t in p64.items()}
     grads["dmask"] = dmask_total
@@ -153,6 +199,7 @@ def forward_backward_l1(g, cams, targets, cfg: OracleConfig):
         l, d = l1_loss_grad(v.out["image"], tgt)
         loss += l
         dimgs.append(d)
+    loss += mask_loss(M, cfg)
     grads, per_view = backward(g, cams, cfg, views, M, minfo, dimgs)
     return dict(views=views, mask=M, mask_info=minfo, loss=loss, dL_dimages=dimgs,
                 grads=grads, per_view=per_view)

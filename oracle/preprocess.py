@@ -172,3 +172,11 @@ def mask_straight_through(mask_logits, hard_mask, u0, u1, tau=1.0):
     y0 = y[:, 0]
     hard = torch.as_tensor(hard_mask, dtype=DT)
     return hard + (y0 - y0.detach()), y0
+
+
+def mask_straight_through_ste(mask_logits, hard_mask):
+    """Straight-through threshold mask (Sec. 4.3 ablation): forward value the
+    hard M, gradient that of p = sigmoid(l_0 - l_1).  Returns (M_st, p)."""
+    p = torch.sigmoid(mask_logits[:, 0] - mask_logits[:, 1])
+    hard = torch.as_tensor(hard_mask, dtype=DT)
+    return hard + (p - p.detach()), p
