@@ -13,7 +13,9 @@ import os
 from . import build as _build
 
 MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_CAPACITY, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = range(6)
-MG_MASK_GUMBEL, MG_MASK_ALL_ONES, MG_MASK_GIVEN = 0, 1, 2
+MG_MASK_GUMBEL, MG_MASK_ALL_ONES, MG_MASK_GIVEN, MG_MASK_STE = 0, 1, 2, 3
+MG_APPLY_RASTER, MG_APPLY_OPACITY = 0, 1
+MG_MASK_LOSS_L2, MG_MASK_LOSS_L1 = 0, 1
 MG_DTYPE_F32, MG_DTYPE_BF16, MG_DTYPE_F16 = 0, 1, 2
 MG_MAX_VIEWS = 64
 MG_RECORD_FLOATS = 12
@@ -23,7 +25,8 @@ EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes",
             "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
             "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
-            "mg_read_status", "mg_status_string", "mg_version")
+            "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
+            "mg_render_inference", "mg_read_status", "mg_status_string", "mg_version")
 
 
 class MaskgsError(RuntimeError):
@@ -57,12 +60,20 @@ class mg_view(C.Structure):
 class mg_raster_cfg(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
                 ("tau", C.c_float), ("seed", C.c_uint64), ("iteration", C.c_uint64),
-                ("mask_mode", C.c_int32), ("reserved", C.c_int32), ("given_mask", C.c_void_p)]
+                ("mask_mode", C.c_int32), ("mask_apply", C.c_int32), ("given_mask", C.c_void_p),
+                ("lambda_m", C.c_float), ("mask_loss", C.c_int32), ("ste_logit", C.c_float),
+                ("reserved", C.c_int32)]
 
 
 class mg_splats(C.Structure):
     _fields_ = [("record", C.c_void_p), ("tiles_touched", C.c_void_p), ("radius", C.c_void_p),
-                ("clamp", C.c_void_p), ("mask", C.c_void_p), ("mask_soft", C.c_void_p)]
+                ("clamp", C.c_void_p), ("mask", C.c_void_p), ("mask_soft", C.c_void_p),
+                ("mask_count", C.c_void_p)]
+
+
+class mg_gaussian_arrays(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("mask_logits", C.c_void_p)]
 
 
 class mg_param_grads(C.Structure):
@@ -115,6 +126,13 @@ def load(build_if_missing: bool = True):
         "mg_preprocess_backward": (st, [_P(mg_gaussians), _P(mg_view), C.c_int32,
                                         _P(mg_raster_cfg), _P(mg_splats), vp,
                                         _P(mg_param_grads), vp]),
+        "mg_mask_loss": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp, vp]),
+        "mg_prune_sample": (st, [_P(mg_gaussians), C.c_uint64, C.c_uint64, C.c_int32, vp, vp]),
+        "mg_compact": (st, [_P(mg_gaussians), vp, _P(mg_gaussian_arrays), vp, vp, vp, C.c_size_t,
+                            vp, vp]),
+        "mg_compact_workspace_bytes": (C.c_size_t, [C.c_int64]),
+        "mg_render_inference": (st, [_P(mg_splats), vp, vp, _P(mg_view), C.c_int32,
+                                     _P(mg_raster_cfg), vp, vp]),
         "mg_read_status": (st, [vp, _P(mg_status_word), vp]),
         "mg_status_string": (C.c_char_p, [C.c_int32]),
         "mg_version": (C.c_char_p, []),
@@ -231,6 +249,32 @@ def mg_render_backward(splats, sorted_vals, ranges, views, n_views, cfg, final_T
 def mg_preprocess_backward(g, views, n_views, cfg, splats, grad2d, out, stream):
     _check("mg_preprocess_backward", load().mg_preprocess_backward(
         C.byref(g), views, n_views, C.byref(cfg), C.byref(splats), ptr(grad2d), C.byref(out),
+        stream))
+
+
+def mg_mask_loss(splats, views, n_views, cfg, loss, stream):
+    _check("mg_mask_loss", load().mg_mask_loss(C.byref(splats), views, n_views, C.byref(cfg),
+                                               ptr(loss), stream))
+
+
+def mg_prune_sample(g, seed, iteration, n_draws, keep, stream):
+    _check("mg_prune_sample", load().mg_prune_sample(C.byref(g), seed, iteration, n_draws,
+                                                     ptr(keep), stream))
+
+
+def mg_compact(src, keep, dst, new_index, d_n_kept, workspace, workspace_bytes, d_status, stream):
+    _check("mg_compact", load().mg_compact(C.byref(src), ptr(keep), C.byref(dst), ptr(new_index),
+                                           ptr(d_n_kept), ptr(workspace), workspace_bytes,
+                                           ptr(d_status), stream))
+
+
+def mg_compact_workspace_bytes(n) -> int:
+    return int(load().mg_compact_workspace_bytes(n))
+
+
+def mg_render_inference(splats, sorted_vals, ranges, views, n_views, cfg, image, stream):
+    _check("mg_render_inference", load().mg_render_inference(
+        C.byref(splats), ptr(sorted_vals), ptr(ranges), views, n_views, C.byref(cfg), ptr(image),
         stream))
 
 

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmaskgs.so")
-SOURCES = ["abi.cu", "preprocess.cu", "binsort.cu", "render.cu"]
+SOURCES = ["abi.cu", "preprocess.cu", "binsort.cu", "render.cu", "prune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--use_fast_math=false", "-Xptxas", "-warn-spills"]

@@ -35,43 +35,7 @@ constexpr int kScanThreads = 256, kScanItems = 8, kScanPart = kScanThreads * kSc
 constexpr int kSortThreads = 256, kSortItems = 12, kSortPart = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValMask = (1u << 30) - 1u;
-constexpr uint64_t kFlagAgg64 = 1ull << 62, kFlagPrefix64 = 2ull << 62,
-                   kValMask64 = (1ull << 62) - 1ull;
 constexpr int kMaxPasses = 8;
-
-__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
-    return *reinterpret_cast<const volatile uint32_t *>(p);
-}
-__device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
-    return *reinterpret_cast<const volatile uint64_t *>(p);
-}
-
-__device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t *sm_warp,
-                                                             uint64_t &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    if (lane == 31) sm_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint64_t w = lane < (int)(blockDim.x >> 5) ? sm_warp[lane] : 0;
-        uint64_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < (int)(blockDim.x >> 5)) sm_warp[lane] = wi - w;
-        if (lane == 31) sm_warp[32] = wi;
-    }
-    __syncthreads();
-    total = sm_warp[32];
-    return sm_warp[warp] + inc - v;
-}
 
 // --------------------------------------------------------------------------
 // scan of tiles_touched (in the given order)

@@ -37,6 +37,46 @@ __device__ __forceinline__ void raise_status(mg_status_word *w, int32_t st, int3
     atomicCAS(&w->detail, 0, detail);
 }
 
+// single-pass scans (decoupled look-back) ------------------------------------
+// A partition's 64-bit status word: flag in the top two bits (1 = aggregate
+// only, 2 = inclusive prefix), value below.
+constexpr uint64_t kFlagAgg64 = 1ull << 62, kFlagPrefix64 = 2ull << 62,
+                   kValMask64 = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
+    return *reinterpret_cast<const volatile uint64_t *>(p);
+}
+
+__device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t *sm_warp,
+                                                             uint64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sm_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < (int)(blockDim.x >> 5) ? sm_warp[lane] : 0;
+        uint64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < (int)(blockDim.x >> 5)) sm_warp[lane] = wi - w;
+        if (lane == 31) sm_warp[32] = wi;
+    }
+    __syncthreads();
+    total = sm_warp[32];
+    return sm_warp[warp] + inc - v;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
 // (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
@@ -109,6 +149,24 @@ __device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float ml(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float dv(float a, float b) { return __fdiv_rn(a, b); }
 // (a*b + c*d) + e*f with every product and sum rounded
+// Mask sample of Sec. 3.3.  Noise block of Gaussian i for one draw: Philox
+// counter (i, iteration_lo, iteration_hi, draw), key (seed_lo, seed_hi); the
+// training sample is draw 0, the pruning draws of Sec. 3.5 are 1, 2, ...
+__device__ __forceinline__ uint4 gumbel_counter(int64_t i, uint64_t iteration, uint32_t draw,
+                                                uint64_t seed) {
+    return philox4x32_10(
+        make_uint4((uint32_t)i, (uint32_t)iteration, (uint32_t)(iteration >> 32), draw),
+        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Gumbel-max margin (l_0 + g_0) - (l_1 + g_1), g_k = -log(-log u_k), every
+// operation correctly rounded FP32 (M = 1 iff the margin is >= 0).
+__device__ __forceinline__ float gumbel_margin(float2 l, uint4 x) {
+    const float g0 = -log32(-log32(uniform24(x.x)));
+    const float g1 = -log32(-log32(uniform24(x.y)));
+    return sb(ad(l.x, g0), ad(l.y, g1));
+}
+
 __device__ __forceinline__ float dot3(float a, float b, float c, float d, float e, float f) {
     return ad(ad(ml(a, b), ml(c, d)), ml(e, f));
 }

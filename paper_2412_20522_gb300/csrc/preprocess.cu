@@ -213,25 +213,38 @@ template <int DEG, typename ST>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out) {
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
-    if (i >= g.n) return;
+    const bool active = i < g.n;
 
-    // --- mask sample (Sec. 3.3): Gumbel-max over the two existence scores
-    float Mf = 1.0f;
-    if (cfg.mask_mode == MG_MASK_GUMBEL) {
-        const uint4 x = philox4x32_10(
-            make_uint4((uint32_t)i, (uint32_t)cfg.iteration, (uint32_t)(cfg.iteration >> 32), 0u),
-            make_uint2((uint32_t)cfg.seed, (uint32_t)(cfg.seed >> 32)));
-        const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);  // FP32
-        const float g0 = -log32(-log32(uniform24(x.x)));
-        const float g1 = -log32(-log32(uniform24(x.y)));
-        const float d = sb(ad(l.x, g0), ad(l.y, g1));
-        Mf = d >= 0.0f ? 1.0f : 0.0f;
-        out.mask_soft[i] = 1.0f / (1.0f + expf(-d / cfg.tau));
-    } else {
-        if (cfg.mask_mode == MG_MASK_GIVEN) Mf = cfg.given_mask[i] ? 1.0f : 0.0f;
-        out.mask_soft[i] = 1.0f;
+    // --- mask (Sec. 3.3): Gumbel-max over the two existence scores, or the
+    // threshold of the straight-through ablation (Sec. 4.3)
+    float Mf = active ? 1.0f : 0.0f;
+    if (active) {
+        if (cfg.mask_mode == MG_MASK_GUMBEL) {
+            const uint4 x = gumbel_counter(i, cfg.iteration, 0u, cfg.seed);
+            const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);  // FP32
+            const float d = gumbel_margin(l, x);
+            Mf = d >= 0.0f ? 1.0f : 0.0f;
+            out.mask_soft[i] = 1.0f / (1.0f + expf(-d / cfg.tau));
+        } else if (cfg.mask_mode == MG_MASK_STE) {
+            const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);
+            const float d = sb(l.x, l.y);
+            Mf = d > cfg.ste_logit ? 1.0f : 0.0f;
+            out.mask_soft[i] = 1.0f / (1.0f + expf(-d));
+        } else {
+            if (cfg.mask_mode == MG_MASK_GIVEN) Mf = cfg.given_mask[i] ? 1.0f : 0.0f;
+            out.mask_soft[i] = 1.0f;
+        }
+        out.mask[i] = Mf != 0.0f;
     }
-    out.mask[i] = Mf != 0.0f;
+    // sum of M over each view's range (for L_m, Eq. 7): one atomic per warp
+    if (out.mask_count != nullptr) {
+        for (int v = 0; v < vt.n_views; ++v) {
+            const bool in = active && i >= vt.g_off[v] && i < vt.g_off[v] + vt.g_cnt[v];
+            const unsigned b = __ballot_sync(0xffffffffu, in && Mf != 0.0f);
+            if ((threadIdx.x & 31) == 0 && b != 0u) atomicAdd(out.mask_count + v, (uint32_t)__popc(b));
+        }
+    }
+    if (!active) return;
 
     const float *means = reinterpret_cast<const float *>(g.means);
     const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
@@ -279,8 +292,12 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         rec[0] = make_float4(S.px, S.py, ux, uy);
         // mask in the sign of the opacity; e_min just below log2(1/(255 o)) (a
         // splat with o under the floor never reaches it: e_min = 1 > any e)
-        const float e_min = op >= kAlphaMin ? __log2f(kAlphaMin / op) - 1e-3f : 1.0f;
-        rec[1] = make_float4(-0.5f * kLog2e / l1, -0.5f * kLog2e / l2, Mf != 0.0f ? op : -op, e_min);
+        // (mask x opacity ablation: the opacity is M o, +0 for a masked splat)
+        const bool by_opacity = cfg.mask_apply == MG_APPLY_OPACITY;
+        const float o_eff = by_opacity ? Mf * op : op;
+        const float e_min = o_eff >= kAlphaMin ? __log2f(kAlphaMin / o_eff) - 1e-3f : 1.0f;
+        rec[1] = make_float4(-0.5f * kLog2e / l1, -0.5f * kLog2e / l2,
+                             (by_opacity || Mf != 0.0f) ? o_eff : -op, e_min);
         rec[2] = make_float4(rgb[0], rgb[1], rgb[2], S.tz);
     }
 }
@@ -588,11 +605,31 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
         out.log_scales[3 * i + 1] = d_ls[1];
         out.log_scales[3 * i + 2] = d_ls[2];
         reinterpret_cast<float4 *>(out.quats)[i] = make_float4(d_q[0], d_q[1], d_q[2], d_q[3]);
+        if (cfg.mask_apply == MG_APPLY_OPACITY) {
+            // o' = M o: dL/do = M dL/do', dL/dM = o dL/do'
+            const float Mf = sp.mask[i] ? 1.0f : 0.0f;
+            d_M = op * d_op;
+            d_op *= Mf;
+        }
         out.opacity_logit[i] = d_op * op * (1.0f - op);
+        // lambda_m dL_m/dM_i of the Gaussian's scene (Eq. 7-8)
+        if (cfg.lambda_m != 0.0f && sp.mask_count != nullptr) {
+            for (int v = 0; v < vt.n_views; ++v) {
+                if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
+                const float N = (float)vt.g_cnt[v];
+                d_M += cfg.mask_loss == MG_MASK_LOSS_L1
+                           ? cfg.lambda_m / N
+                           : 2.0f * cfg.lambda_m * ((float)sp.mask_count[v] / N) / N;
+                break;
+            }
+        }
         float dl0 = 0.0f;
         if (cfg.mask_mode == MG_MASK_GUMBEL) {
             const float y0 = sp.mask_soft[i];
             dl0 = d_M * y0 * (1.0f - y0) / cfg.tau;
+        } else if (cfg.mask_mode == MG_MASK_STE) {
+            const float p = sp.mask_soft[i];
+            dl0 = d_M * p * (1.0f - p);
         }
         reinterpret_cast<float2 *>(out.mask_logits)[i] = make_float2(dl0, -dl0);
     }
@@ -679,23 +716,37 @@ static mg_status check_views(const mg_gaussians *g, const mg_view *views, int32_
     return MG_OK;
 }
 
+static mg_status check_mask_cfg(const mg_raster_cfg *cfg) {
+    if (!(cfg->tau > 0.0f)) return MG_ERR_INVALID_ARG;
+    if (cfg->mask_mode < MG_MASK_GUMBEL || cfg->mask_mode > MG_MASK_STE) return MG_ERR_INVALID_ARG;
+    if (cfg->mask_mode == MG_MASK_GIVEN && cfg->given_mask == nullptr) return MG_ERR_INVALID_ARG;
+    if (cfg->mask_apply != MG_APPLY_RASTER && cfg->mask_apply != MG_APPLY_OPACITY)
+        return MG_ERR_INVALID_ARG;
+    if (cfg->mask_loss != MG_MASK_LOSS_L2 && cfg->mask_loss != MG_MASK_LOSS_L1)
+        return MG_ERR_INVALID_ARG;
+    if (!isfinite(cfg->lambda_m) || !isfinite(cfg->ste_logit)) return MG_ERR_INVALID_ARG;
+    return MG_OK;
+}
+
 extern "C" mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, int32_t n_views,
                                    const mg_raster_cfg *cfg, const mg_splats *out,
                                    mg_status_word *d_status, mg_stream_t stream) {
     (void)d_status;
-    if (check_gaussians(g) != MG_OK || cfg == nullptr || out == nullptr || !(cfg->tau > 0.0f))
+    if (check_gaussians(g) != MG_OK || cfg == nullptr || out == nullptr ||
+        check_mask_cfg(cfg) != MG_OK)
         return MG_ERR_INVALID_ARG;
-    if (cfg->mask_mode < 0 || cfg->mask_mode > 2) return MG_ERR_INVALID_ARG;
-    if (cfg->mask_mode == MG_MASK_GIVEN && cfg->given_mask == nullptr) return MG_ERR_INVALID_ARG;
     ViewTable vt;
     mg_status st = check_views(g, views, n_views, cfg, &vt);
     if (st != MG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (out->mask_count != nullptr &&
+        cudaMemsetAsync(out->mask_count, 0, sizeof(uint32_t) * n_views, s) != cudaSuccess)
+        return MG_ERR_CUDA;
     if (g->n == 0) return MG_OK;
     if (!out->record || !out->tiles_touched || !out->radius || !out->clamp || !out->mask ||
         !out->mask_soft || !aligned(out->record, 16))
         return MG_ERR_INVALID_ARG;
     const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
-    cudaStream_t s = (cudaStream_t)stream;
     switch (g->sh_degree) {
         case 0: launch_preprocess<0>(g->dtype, grid, s, vt, *g, *cfg, *out); break;
         case 1: launch_preprocess<1>(g->dtype, grid, s, vt, *g, *cfg, *out); break;
@@ -710,15 +761,17 @@ extern "C" mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view
                                             const mg_splats *splats, const float *grad2d,
                                             const mg_param_grads *out, mg_stream_t stream) {
     if (check_gaussians(g) != MG_OK || cfg == nullptr || splats == nullptr || out == nullptr ||
-        !(cfg->tau > 0.0f))
+        check_mask_cfg(cfg) != MG_OK)
         return MG_ERR_INVALID_ARG;
+    if (cfg->lambda_m != 0.0f && splats->mask_count == nullptr) return MG_ERR_INVALID_ARG;
     ViewTable vt;
     mg_status st = check_views(g, views, n_views, cfg, &vt);
     if (st != MG_OK) return st;
     if (g->n == 0) return MG_OK;
     if (!grad2d || !aligned(grad2d, 16) || !out->means || !out->log_scales || !out->quats ||
         !aligned(out->quats, 16) || !out->opacity_logit || !out->sh || !out->mask_logits ||
-        !aligned(out->mask_logits, 8) || !splats->radius || !splats->clamp || !splats->mask_soft)
+        !aligned(out->mask_logits, 8) || !splats->radius || !splats->clamp || !splats->mask_soft ||
+        !splats->mask)
         return MG_ERR_INVALID_ARG;
     const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
     cudaStream_t s = (cudaStream_t)stream;
@@ -728,5 +781,54 @@ extern "C" mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view
         case 2: launch_preprocess_backward<2>(g->dtype, grid, s, vt, *g, *cfg, *splats, grad2d, *out); break;
         default: launch_preprocess_backward<3>(g->dtype, grid, s, vt, *g, *cfg, *splats, grad2d, *out); break;
     }
+    return mg_host::launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Mask loss value (Eq. 7-8): lambda_m L_m per scene, a scene being a distinct
+// Gaussian range among the views.
+// ---------------------------------------------------------------------------
+namespace mg {
+struct SceneList {
+    int32_t n;
+    int32_t view[MG_MAX_VIEWS];
+    int64_t count[MG_MAX_VIEWS];
+};
+
+__global__ void mask_loss_kernel(SceneList sl, const uint32_t *__restrict__ mask_count,
+                                 float lambda_m, int32_t kind, float *loss) {
+    if (threadIdx.x != 0) return;
+    double acc = 0.0;
+    for (int k = 0; k < sl.n; ++k) {
+        const double frac = (double)mask_count[sl.view[k]] / (double)sl.count[k];
+        acc += kind == MG_MASK_LOSS_L1 ? frac : frac * frac;
+    }
+    *loss += (float)((double)lambda_m * acc);
+}
+}  // namespace mg
+
+extern "C" mg_status mg_mask_loss(const mg_splats *splats, const mg_view *views, int32_t n_views,
+                                  const mg_raster_cfg *cfg, float *loss, mg_stream_t stream) {
+    if (splats == nullptr || views == nullptr || cfg == nullptr || loss == nullptr ||
+        splats->mask_count == nullptr || n_views < 1 || n_views > MG_MAX_VIEWS ||
+        (cfg->mask_loss != MG_MASK_LOSS_L2 && cfg->mask_loss != MG_MASK_LOSS_L1) ||
+        !isfinite(cfg->lambda_m))
+        return MG_ERR_INVALID_ARG;
+    SceneList sl;
+    sl.n = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (views[v].gaussian_count <= 0) continue;
+        bool seen = false;
+        for (int u = 0; u < v; ++u)
+            seen |= views[u].gaussian_offset == views[v].gaussian_offset &&
+                    views[u].gaussian_count == views[v].gaussian_count;
+        if (seen) continue;
+        sl.view[sl.n] = v;
+        sl.count[sl.n] = views[v].gaussian_count;
+        ++sl.n;
+    }
+    if (sl.n == 0 || cfg->lambda_m == 0.0f) return MG_OK;
+    mask_loss_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(sl, splats->mask_count, cfg->lambda_m,
+                                                        cfg->mask_loss, loss);
     return mg_host::launch_status();
 }

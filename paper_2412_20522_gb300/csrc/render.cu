@@ -142,8 +142,9 @@ __device__ __forceinline__ bool all_done(const bool *done) {
 // COUNT = true adds per-fragment counters (an untimed diagnostic variant):
 // [0] positions walked (sum of n_contrib), [1] unmasked positions walked,
 // [2] unmasked splats blended, [3] masked splats above the alpha floor.
-// They count every walked position, culled or not.
-template <bool COUNT>
+// They count every walked position, culled or not.  AUX = false is the
+// inference form: the image only, no final_T / n_contrib for a backward.
+template <bool COUNT, bool AUX = true>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, float bg0, float bg1, float bg2,
@@ -273,8 +274,10 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
         img[ti.pix[k]] = C0[k] + T[k] * bg0;
         img[HW + ti.pix[k]] = C1[k] + T[k] * bg1;
         img[2 * HW + ti.pix[k]] = C2[k] + T[k] * bg2;
-        final_T[vt.pix_off[ti.v] + ti.pix[k]] = T[k];
-        n_contrib[vt.pix_off[ti.v] + ti.pix[k]] = stop[k];
+        if (AUX) {
+            final_T[vt.pix_off[ti.v] + ti.pix[k]] = T[k];
+            n_contrib[vt.pix_off[ti.v] + ti.pix[k]] = stop[k];
+        }
     }
 }
 
@@ -568,6 +571,24 @@ extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_v
         render_forward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
             vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T,
             n_contrib, nullptr);
+    return mg_host::launch_status();
+}
+
+extern "C" mg_status mg_render_inference(const mg_splats *splats, const uint32_t *sorted_vals,
+                                         const uint32_t *ranges, const mg_view *views,
+                                         int32_t n_views, const mg_raster_cfg *cfg, float *image,
+                                         mg_stream_t stream) {
+    if (!splats || !splats->record || !sorted_vals || !ranges || !image)
+        return MG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats->record) & 15u) != 0) return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    const int64_t tiles = vt.tile_off[n_views];
+    if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
+    render_forward_kernel<false, false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+        vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, cfg->bg[0],
+        cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
     return mg_host::launch_status();
 }
 

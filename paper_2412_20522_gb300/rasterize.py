@@ -28,6 +28,17 @@ class RasterConfig:
     iteration: int = 0
     mask_mode: int = abi.MG_MASK_GUMBEL
     given_mask: torch.Tensor | None = None     # uint8 [n] on the device
+    mask_apply: int = abi.MG_APPLY_RASTER      # or MG_APPLY_OPACITY (ablation, Sec. 4.3)
+    lambda_m: float = 0.0                      # mask-loss weight, Eq. 8
+    mask_loss: int = abi.MG_MASK_LOSS_L2       # Eq. 7, or the L1 form
+    ste_logit: float = 0.0                     # MG_MASK_STE threshold on l_0 - l_1
+
+    @staticmethod
+    def ste_logit_of(theta: float) -> float:
+        """The l_0 - l_1 threshold (an FP32 value) equivalent to
+        sigmoid(l_0 - l_1) > theta."""
+        import numpy as np
+        return float(np.float32(math.log(theta / (1.0 - theta))))
 
     def c(self) -> abi.mg_raster_cfg:
         cfg = abi.mg_raster_cfg()
@@ -39,6 +50,10 @@ class RasterConfig:
         cfg.iteration = int(self.iteration)
         cfg.mask_mode = int(self.mask_mode)
         cfg.given_mask = abi.ptr(self.given_mask) if self.given_mask is not None else None
+        cfg.mask_apply = int(self.mask_apply)
+        cfg.lambda_m = float(self.lambda_m)
+        cfg.mask_loss = int(self.mask_loss)
+        cfg.ste_logit = float(self.ste_logit)
         return cfg
 
 
@@ -128,8 +143,9 @@ class Rasterizer:
     def _stream(self):
         return C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
 
-    def _splats(self, R, n):
+    def _splats(self, R, n, V):
         s = abi.mg_splats()
+        s.mask_count = self._get("mask_count", V, torch.int32).data_ptr()
         s.record = self._get("record", R * abi.MG_RECORD_FLOATS, torch.float32).data_ptr()
         s.tiles_touched = self._get("tiles", R, torch.int32).data_ptr()
         s.radius = self._get("radius", R, torch.int32).data_ptr()
@@ -147,9 +163,13 @@ class Rasterizer:
 
     # -- forward --------------------------------------------------------------
     def forward(self, params: dict, cams, cfg: RasterConfig, view_ranges=None, check=True,
-                count_fragments=False, stage_events=None):
+                count_fragments=False, stage_events=None, inference=False):
         """Masked forward.  Returns the concatenated images (flat float32,
-        per view [3][H][W])."""
+        per view [3][H][W]).  ``inference``: the forward-only renderer of a
+        (pruned) model -- every Gaussian present, no state for a backward."""
+        if inference:
+            cfg = RasterConfig(**{**cfg.__dict__, "mask_mode": abi.MG_MASK_ALL_ONES,
+                                  "given_mask": None, "lambda_m": 0.0})
         n = int(params["means"].shape[0])
         sh_degree = int(round(math.sqrt(params["sh"].shape[1]))) - 1
         ranges = view_ranges if view_ranges is not None else [(0, n)] * len(cams)
@@ -164,7 +184,7 @@ class Rasterizer:
         stream = self._stream()
         ev = _Events(stage_events)
         self.status.zero_()
-        splats = self._splats(R, n)
+        splats = self._splats(R, n, V)
         ev.begin("preprocess")
         abi.mg_preprocess(g, views, V, ccfg, splats, self.status, stream)
         ev.end("preprocess")
@@ -209,6 +229,17 @@ class Rasterizer:
         ev.end("sort")
         sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
         image = self._get("image", 3 * pix, torch.float32)
+        if inference:
+            ev.begin("render")
+            abi.mg_render_inference(splats, sorted_vals, ranges_buf, views, V, ccfg, image, stream)
+            ev.end("render")
+            self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1
+            self._state = None
+            if check:
+                st = abi.mg_read_status(self.status, stream)
+                if st.status != abi.MG_OK:
+                    raise abi.MaskgsError("inference forward", st.status)
+            return image
         final_T = self._get("final_T", pix, torch.float32)
         n_contrib = self._get("n_contrib", pix, torch.int32)
         if count_fragments:
@@ -238,12 +269,24 @@ class Rasterizer:
         return 2
 
     def l1_loss_grad(self, image, target):
+        """L = L_render (L1) + lambda_m L_m (Eq. 8; the mask loss only when
+        lambda_m != 0, its gradient is added by the backward) and dL/dimage."""
         s = self._state
         dimg = self._get("dL_dimage", 3 * s["pix"], torch.float32)
         loss = self._get("loss", 1, torch.float32)
         loss.zero_()
         abi.mg_l1_loss_grad(image, target, s["views"], s["V"], dimg, loss, self._stream())
+        if s["cfg"].lambda_m != 0.0:
+            abi.mg_mask_loss(s["splats"], s["views"], s["V"], s["cfg"], loss, self._stream())
         return loss, dimg
+
+    def mask_loss(self):
+        """lambda_m L_m of the last forward (Eq. 7-8), a device scalar."""
+        s = self._state
+        loss = self._get("mask_loss", 1, torch.float32)
+        loss.zero_()
+        abi.mg_mask_loss(s["splats"], s["views"], s["V"], s["cfg"], loss, self._stream())
+        return loss
 
     # -- backward -------------------------------------------------------------
     def backward(self, dL_dimage, out: dict | None = None, stage_events=None,
@@ -281,6 +324,7 @@ class Rasterizer:
                     tiles=self._buf["tiles"][:R], radius=self._buf["radius"][:R],
                     clamp=self._buf["clamp"][:R], mask=self._buf["mask"][:n],
                     mask_soft=self._buf["mask_soft"][:n], offsets=self._buf["offsets"][:R],
+                    mask_count=self._buf["mask_count"][:s["V"]],
                     sorted_vals=s["sorted_vals"], ranges=s["ranges"][:2 * s["tiles"]],
                     final_T=self._buf["final_T"][:s["pix"]],
                     n_contrib=self._buf["n_contrib"][:s["pix"]],

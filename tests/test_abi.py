@@ -83,3 +83,34 @@ def test_bad_arguments_rejected_on_host(lib):
     st = lib.mg_sort(None, None, None, None, None, 0, 20, None, 1, None, 0, C.byref(alt), None,
                      None)
     assert st == abi.MG_ERR_INVALID_ARG
+
+
+def test_mask_pruning_and_inference_arguments_rejected_on_host(lib):
+    """New entry points check their arguments before any launch."""
+    from paper_2412_20522_gb300 import abi, scenes
+    from paper_2412_20522_gb300.rasterize import RasterConfig, make_views
+    cam = scenes.look_at_camera((0, 0, -3), (0, 0, 0), 64, 64, 50.0)
+    views = make_views([cam], [(0, 5)])
+    g = abi.mg_gaussians()
+    g.n, g.sh_degree = 5, 3
+    out = abi.mg_splats()
+    for field, bad in (("mask_mode", 4), ("mask_apply", 2), ("mask_loss", 5)):
+        cfg = RasterConfig().c()
+        setattr(cfg, field, bad)
+        assert lib.mg_preprocess(C.byref(g), views, 1, C.byref(cfg), C.byref(out), None,
+                                 None) == abi.MG_ERR_INVALID_ARG
+    cfg = RasterConfig(lambda_m=float("nan")).c()
+    assert lib.mg_preprocess(C.byref(g), views, 1, C.byref(cfg), C.byref(out), None,
+                             None) == abi.MG_ERR_INVALID_ARG
+    # mask loss needs the per-view counts
+    cfg = RasterConfig(lambda_m=0.1).c()
+    assert lib.mg_mask_loss(C.byref(out), views, 1, C.byref(cfg), None, None) == abi.MG_ERR_INVALID_ARG
+    # pruning: draw count and arrays
+    assert lib.mg_prune_sample(C.byref(g), 1, 2, 0, None, None) == abi.MG_ERR_INVALID_ARG
+    assert lib.mg_prune_sample(C.byref(g), 1, 2, 10, None, None) == abi.MG_ERR_INVALID_ARG
+    dst = abi.mg_gaussian_arrays()
+    assert lib.mg_compact(C.byref(g), None, C.byref(dst), None, None, None, 0, None,
+                          None) == abi.MG_ERR_INVALID_ARG
+    assert abi.mg_compact_workspace_bytes(1_000_000) >= 4 * 1_000_000
+    assert lib.mg_render_inference(C.byref(out), None, None, views, 1, C.byref(cfg), None,
+                                   None) == abi.MG_ERR_INVALID_ARG

@@ -49,7 +49,10 @@ def _tile_lists(rast, t0, nt, r0):
     return [vals[s:e].astype(np.int64) - r0 for s, e in rng]
 
 
-def test_uneven_scene_batch_matches_oracle_per_scene():
+@pytest.mark.parametrize("lambda_m", [0.0, 0.3])
+def test_uneven_scene_batch_matches_oracle_per_scene(lambda_m):
+    """With lambda_m > 0 every scene has its own mask loss L_m over its own
+    N Gaussians (Eq. 7), so the mask-logit gradients differ per scene."""
     from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
     sizes = [1500, 4000, 9000]
     sc = [scenes.cluster_gaussians(n, seed=40 + k, centre_radius=1.5, reject_radius=2.0,
@@ -62,9 +65,10 @@ def test_uneven_scene_batch_matches_oracle_per_scene():
     gall = scenes.Gaussians(**cat, sh_degree=3)
     offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
     ranges = [(int(o), n) for o, n in zip(offs, sizes)]
-    cfg = RasterConfig(bg=(0.3, 0.3, 0.3), seed=77, iteration=2)
+    cfg = RasterConfig(bg=(0.3, 0.3, 0.3), seed=77, iteration=2, lambda_m=lambda_m)
     rast = Rasterizer()
     img = rast.forward(to_device(gall), cams, cfg, view_ranges=ranges)
+    mloss = float(rast.mask_loss().item())
     tg = [scenes.target_image(c.height, c.width, seed=60 + k) for k, c in enumerate(cams)]
     torch.cuda.synchronize()
     gimg = img.cpu().numpy()
@@ -76,10 +80,12 @@ def test_uneven_scene_batch_matches_oracle_per_scene():
     orc = []
     for k, (s, cam) in enumerate(zip(sc, cams)):
         ocfg = pipeline.OracleConfig(bg=cfg.bg, seed=cfg.seed, iteration=cfg.iteration,
-                                     index_offset=int(offs[k]), eps=1e-4)
+                                     index_offset=int(offs[k]), eps=1e-4, lambda_m=lambda_m)
         views, M, minfo = pipeline.forward(s, [cam], ocfg)
         v = views[0]
         assert np.array_equal(mask[offs[k]:offs[k] + sizes[k]], M)
+        assert int(so["mask_count"][k].item()) == int(M.sum())
+        mloss -= pipeline.mask_loss(M, ocfg)
         gx, gy = v.fp32["grid"]
         lists = _tile_lists(rast, t0, gx * gy, int(offs[k]))
         for t, lst in enumerate(lists):
@@ -96,6 +102,7 @@ def test_uneven_scene_batch_matches_oracle_per_scene():
         orc.append((s, cam, ocfg, views, M, minfo, dg))
         po += n
         t0 += gx * gy
+    assert abs(mloss) < 1e-6                      # sum over scenes of lambda_m L_m
     flat = np.concatenate([d.reshape(-1) for d in dimgs]).astype(np.float32)
     out = rast.backward(torch.as_tensor(flat).cuda())
     torch.cuda.synchronize()
