@@ -1,9 +1,10 @@
 """Attribute storage in BF16 / FP16 (log-scales, quaternions, opacity logits,
 SH; means and mask scores stay FP32): values are unpacked to FP32 exactly, so
 the step must be bit-identical to the FP32 step on the unpacked values, and
-match the oracle on them like any FP32 run.  (Gradients are summed by float
-atomics whose order varies from run to run, so they are compared to a
-rounding-level tolerance; every forward output is compared bitwise.)"""
+match the oracle on them like any FP32 run.  (Gradients and the loss are
+summed by float atomics whose order varies from run to run, so they are
+compared to a rounding-level tolerance; every other forward output is
+compared bitwise.)"""
 import numpy as np
 import pytest
 import torch
@@ -14,7 +15,7 @@ from paper_2412_20522_gb300 import scenes
 pytestmark = pytest.mark.gpu
 
 STORED = ("log_scales", "quats", "opacity_logit", "sh")
-GRADS = ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")
+GRADS = ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits", "loss")
 
 
 def _step(params, cams, tgt):
