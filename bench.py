@@ -312,6 +312,7 @@ def run_ours(args):
     }
     if not args.no_forms:
         line["forms"] = run_forms(dev, g, cams, target, ms, W * H)
+        line["forms"]["next_rows"] = run_next_rows(dev, g, cams, target, ms, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(steps=1)
     if clk is not None and clk["samples"] < 3:
@@ -415,6 +416,90 @@ def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
     forms["uneven_batch_bf16"] = {"scenes": len(sizes), "ms_per_step": ms,
                                   "mpix_per_s": pix / 1e6 / (ms * 1e-3), "per_scene": per_scene}
     return forms
+
+
+def run_next_rows(dev, g, cams, target, plain_ms, peaks, steps=10):
+    """The rows after the hot path, on the same 1.2M-Gaussian view: the mask
+    loss (Eq. 7-8) and the ablations of Sec. 4.3 in the training step; the
+    pruning of Sec. 3.5 (sampler and compaction, HBM-bound); the inference
+    renderer of the pruned model (rendering speed, Sec. 4.2)."""
+    import torch
+    from paper_2412_20522_gb300 import prune, scenes
+    from paper_2412_20522_gb300.autotune import GraphStep, time_step
+    from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
+
+    out = {}
+    p = _device_params(g, dev)
+    tgt = torch.as_tensor(target).to(dev).reshape(-1)
+    base = GraphStep(p, cams, RasterConfig(), tgt)
+    out["graph_step_ms"] = time_step(base.replay, steps=steps)
+    del base
+    for name, cfg in (("mask_loss_l2_lambda0.1", RasterConfig(lambda_m=0.1)),
+                      ("ablation_mask_x_opacity", RasterConfig(mask_apply=1)),
+                      ("ablation_ste_threshold_0.01",
+                       RasterConfig(mask_mode=3, ste_logit=RasterConfig.ste_logit_of(0.01)))):
+        gs = GraphStep(p, cams, cfg, tgt)
+        out[name] = {"ms_per_step": time_step(gs.replay, steps=steps), "status": gs.status()}
+        del gs
+    torch.cuda.empty_cache()
+
+    # pruning: converged-looking mask scores (62.4 % almost never sampled)
+    pp = dict(p)
+    pp["mask_logits"] = torch.as_tensor(scenes.converged_mask_logits(g.n)).to(dev)
+    n = g.n
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    comp = prune.Compactor(dev)
+    keep = prune.prune_sample(pp, 7, 30000, 10)
+    comp.run(pp, keep)
+    torch.cuda.synchronize()
+    t_s, t_c = [], []
+    for _ in range(steps):
+        ev[0].record()
+        keep = prune.prune_sample(pp, 7, 30000, 10)
+        ev[1].record()
+        comp.run(pp, keep)
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_s.append(ev[0].elapsed_time(ev[1]))
+        t_c.append(ev[1].elapsed_time(ev[2]))
+    small, _ = comp.result()
+    kept = small["means"].shape[0]
+    row = sum(v[0].numel() * v.element_size() for v in pp.values())      # 244 B (FP32)
+    sample_bytes = n * (8 + 1)
+    compact_bytes = n * (1 + 4 + 4) + 2 * kept * row
+    hbm = float(peaks["hbm_gbs"])
+    ms_s, ms_c = statistics.median(t_s), statistics.median(t_c)
+    out["prune"] = {
+        "gaussians": n, "kept": kept, "pruned_fraction": 1 - kept / n, "draws": 10,
+        "sample_ms": ms_s, "compact_ms": ms_c,
+        "roofline_sample": {"bound": "hbm", "achieved": sample_bytes / (ms_s * 1e-3) / 1e9,
+                            "peak": hbm, "unit": "GB/s",
+                            "frac": sample_bytes / (ms_s * 1e-3) / 1e9 / hbm},
+        "roofline_compact": {"bound": "hbm", "achieved": compact_bytes / (ms_c * 1e-3) / 1e9,
+                             "peak": hbm, "unit": "GB/s",
+                             "frac": compact_bytes / (ms_c * 1e-3) / 1e9 / hbm},
+        "bytes_note": "sample: 8 B logits + 1 B flag per Gaussian; compact: flag + index "
+                      "write + index read per Gaussian, one read and one write of each "
+                      f"survivor's {row} B row"}
+
+    # inference renderer (forward only, every Gaussian present) of the full
+    # and of the pruned model
+    W, H = cams[0].width, cams[0].height
+    for name, params in (("inference_full", p), ("inference_pruned", small)):
+        r = Rasterizer(dev)
+        cfg = RasterConfig()
+        r.forward(params, cams, cfg, check=True, inference=True)
+        torch.cuda.synchronize()
+        ms = time_step(lambda: r.forward(params, cams, cfg, check=False, inference=True),
+                       steps=4 * steps)
+        out[name] = {"gaussians": int(params["means"].shape[0]), "ms_per_frame": ms,
+                     "fps": 1000.0 / ms, "mpix_per_s": W * H / 1e6 / (ms * 1e-3)}
+        del r
+    out["inference_speedup_pruned"] = out["inference_full"]["ms_per_frame"] / \
+        out["inference_pruned"]["ms_per_frame"]
+    del p, pp, small, comp
+    torch.cuda.empty_cache()
+    return out
 
 
 def precision_crop_errors(dev, g, cam):

@@ -183,3 +183,17 @@ def scene_workload(n=1_200_000, views=1, width=1557, height=1038, focal=1150.0,
     cams = [ring_camera(2 * math.pi * k / max(views, 1), ring_radius, width, height,
                         focal) for k in range(views)]
     return g, cams, target_image(height, width)
+
+
+def converged_mask_logits(n, absent_fraction=0.624, seed=SCENE_SEED + 7) -> np.ndarray:
+    """Mask scores of the kind a trained model ends with (a stand-in: no
+    trained weights are available): a fraction of the Gaussians with
+    l_0 - l_1 ~ N(-7, 1) (almost never sampled), the rest ~ N(3, 1).  The
+    default fraction is the pruning ratio the paper reports on Mip-NeRF360
+    (62.4 %, Sec. 4.2)."""
+    rng = np.random.default_rng(seed)
+    absent = rng.random(n) < absent_fraction
+    d = np.where(absent, rng.normal(-7.0, 1.0, n), rng.normal(3.0, 1.0, n))
+    out = np.zeros((n, 2), np.float32)
+    out[:, 0] = d.astype(np.float32)
+    return out
