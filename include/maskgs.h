@@ -9,8 +9,8 @@
  *                             Gumbel-softmax over two existence scores) and
  *                             splat every Gaussian, unmasked, to a 2D
  *                             Gaussian with a view-dependent colour (Sec. 3.1)
- *   2. mg_depth_order, mg_bin order the splats by depth (Sec. 3.1, "the i-th
- *                             Gaussian in the depth order") and duplicate each
+ *   2. mg_depth_order, mg_bin order the splats by depth (Sec. 3.1: the blend
+ *                             indexes Gaussians front to back) and duplicate each
  *                             visible splat once per 16x16 tile it intersects
  *                             (Sec. 3.1), keyed by (tile, depth)
  *   3. mg_sort                group the instances by tile, keeping the depth

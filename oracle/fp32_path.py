@@ -3,8 +3,8 @@
 Every integer the rasteriser derives from floating point -- the sampled mask
 M_i (Sec. 3.3), the near-plane and determinant culls, the splat radius, the
 tile rectangle that decides which 16x16 tiles a Gaussian intersects (Sec. 3.1)
-and the depth key that orders the Gaussians of a pixel (Sec. 3.1, "i-th
-Gaussian in the depth order") -- is decided here in FP32, by a fixed sequence
+and the depth key that orders the Gaussians of a pixel (Sec. 3.1, front to
+back) -- is decided here in FP32, by a fixed sequence
 of correctly rounded IEEE operations (add, sub, mul, div, sqrt, floor, ceil,
 rint; never a fused multiply-add).  The CUDA kernels take the same decisions
 with the same sequence, so the discrete outputs must agree bit for bit.

@@ -1,6 +1,6 @@
 // Tile binning (Sec. 3.1: a Gaussian takes part in a tile's pixels only if it
-// intersects the tile) and depth ordering (Sec. 3.1: Gaussians blended "in
-// the depth order").
+// intersects the tile) and depth ordering (Sec. 3.1: the blend visits a
+// pixel's Gaussians front to back by depth).
 //
 //   depth order  stable radix sort of the splat records by the float bits of
 //                their depth (4 passes over R records)
