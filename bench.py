@@ -434,6 +434,10 @@ def run_next_rows(dev, g, cams, target, plain_ms, peaks, steps=10):
     base = GraphStep(p, cams, RasterConfig(), tgt)
     out["graph_step_ms"] = time_step(base.replay, steps=steps)
     del base
+    # the same step with tiles launched in tile-id order (no longest-first order)
+    plain = GraphStep(p, cams, RasterConfig(), tgt, tile_order=False)
+    out["graph_step_ms_tile_id_order"] = time_step(plain.replay, steps=steps)
+    del plain
     for name, cfg in (("mask_loss_l2_lambda0.1", RasterConfig(lambda_m=0.1)),
                       ("ablation_mask_x_opacity", RasterConfig(mask_apply=1)),
                       ("ablation_ste_threshold_0.01",

@@ -286,6 +286,15 @@ int32_t mg_tile_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg 
 int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
 
 /* ---- 4. render forward (Eq. 3-4) -------------------------------------------- */
+/* Longest-first launch order of the tiles (all render calls take it):
+ * tile_order[n_tiles_total] (u32) = the global tile ids, tiles with longer
+ * lists first (by quarter-octave length classes; the order within a class is
+ * unspecified).  One CTA renders one tile, so this only changes which tile
+ * starts first (list scheduling, longest first), never a result.  ranges:
+ * from mg_sort, 8-byte aligned. */
+mg_status mg_tile_order(const uint32_t *ranges, int64_t n_tiles_total, uint32_t *tile_order,
+                        mg_stream_t stream);
+
 /* Per pixel, front to back over its tile's range: alpha = min(0.99,
  * o exp(power)); splats with alpha < 1/255 are skipped (masked or not);
  * test T' = T (1 - M alpha); if T' < 1e-4 blending stops before this splat;
@@ -297,10 +306,11 @@ int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cf
  * by a slower counting variant of the kernel: [0] (pixel, splat) pairs walked
  * (the sum of n_contrib, the pairs both render kernels evaluate), [1] of which
  * unmasked, [2] unmasked splats blended, [3] masked splats at or above the
- * alpha floor (the ones that receive dL/dM). */
+ * alpha floor (the ones that receive dL/dM).
+ * tile_order (nullable: tile-id order): from mg_tile_order. */
 mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
-                    const uint32_t *ranges, const mg_view *views, int32_t n_views,
-                    const mg_raster_cfg *cfg, float *image, float *final_T,
+                    const uint32_t *ranges, const uint32_t *tile_order, const mg_view *views,
+                    int32_t n_views, const mg_raster_cfg *cfg, float *image, float *final_T,
                     uint32_t *n_contrib, uint64_t *frag_count, mg_stream_t stream);
 
 /* ---- 5. L1 render loss ------------------------------------------------------ */
@@ -324,10 +334,11 @@ mg_status mg_l1_loss_grad(const float *image, const float *target, const mg_view
  * counters (nullable): device u64[6] of profiling counters, accumulated, taken
  * by a slower counting variant: [0] (warp, splat) iterations after culling,
  * [1] of which masked, [2] unmasked with at least one contributing pixel,
- * [3] masked with one, [4] contributing pixels summed over [2], [5] batches. */
+ * [3] masked with one, [4] contributing pixels summed over [2], [5] batches.
+ * tile_order (nullable): as for mg_render. */
 mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
-                             const uint32_t *ranges, const mg_view *views,
-                             int32_t n_views, const mg_raster_cfg *cfg,
+                             const uint32_t *ranges, const uint32_t *tile_order,
+                             const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
                              const float *final_T, const uint32_t *n_contrib,
                              const float *dL_dimage, float *grad2d, uint64_t *counters,
                              mg_stream_t stream);
@@ -391,10 +402,12 @@ size_t mg_compact_workspace_bytes(int64_t n);
 /* ---- 10. inference render (Sec. 4.2, rendering speed) ----------------------- */
 /* Forward-only blend of splats made with MG_MASK_ALL_ONES (a pruned model
  * renders every Gaussian it keeps; masked records, if any, are skipped):
- * image[3][H][W] per view, as mg_render, without final_T and n_contrib. */
+ * image[3][H][W] per view, as mg_render, without final_T and n_contrib.
+ * tile_order (nullable): as for mg_render. */
 mg_status mg_render_inference(const mg_splats *splats, const uint32_t *sorted_vals,
-                              const uint32_t *ranges, const mg_view *views, int32_t n_views,
-                              const mg_raster_cfg *cfg, float *image, mg_stream_t stream);
+                              const uint32_t *ranges, const uint32_t *tile_order,
+                              const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                              float *image, mg_stream_t stream);
 
 /* ---- helpers ------------------------------------------------------------------ */
 /* Synchronises `stream` and copies the device status word to *h_out (host). */

@@ -26,7 +26,8 @@ EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes",
             "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
-            "mg_render_inference", "mg_read_status", "mg_status_string", "mg_version")
+            "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
+            "mg_version")
 
 
 class MaskgsError(RuntimeError):
@@ -118,10 +119,11 @@ def load(build_if_missing: bool = True):
         "mg_sort_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int32]),
         "mg_tile_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_total_tiles": (C.c_int64, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
-        "mg_render": (st, [_P(mg_splats), vp, vp, _P(mg_view), C.c_int32, _P(mg_raster_cfg),
-                           vp, vp, vp, vp, vp]),
+        "mg_render": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
+                           _P(mg_raster_cfg), vp, vp, vp, vp, vp]),
+        "mg_tile_order": (st, [vp, C.c_int64, vp, vp]),
         "mg_l1_loss_grad": (st, [vp, vp, _P(mg_view), C.c_int32, vp, vp, vp]),
-        "mg_render_backward": (st, [_P(mg_splats), vp, vp, _P(mg_view), C.c_int32,
+        "mg_render_backward": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
                                     _P(mg_raster_cfg), vp, vp, vp, vp, vp, vp]),
         "mg_preprocess_backward": (st, [_P(mg_gaussians), _P(mg_view), C.c_int32,
                                         _P(mg_raster_cfg), _P(mg_splats), vp,
@@ -131,7 +133,7 @@ def load(build_if_missing: bool = True):
         "mg_compact": (st, [_P(mg_gaussians), vp, _P(mg_gaussian_arrays), vp, vp, vp, C.c_size_t,
                             vp, vp]),
         "mg_compact_workspace_bytes": (C.c_size_t, [C.c_int64]),
-        "mg_render_inference": (st, [_P(mg_splats), vp, vp, _P(mg_view), C.c_int32,
+        "mg_render_inference": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
                                      _P(mg_raster_cfg), vp, vp]),
         "mg_read_status": (st, [vp, _P(mg_status_word), vp]),
         "mg_status_string": (C.c_char_p, [C.c_int32]),
@@ -227,11 +229,17 @@ def mg_total_tiles(views, n_views, cfg) -> int:
     return int(load().mg_total_tiles(views, n_views, C.byref(cfg)))
 
 
-def mg_render(splats, sorted_vals, ranges, views, n_views, cfg, image, final_T, n_contrib,
-              frag_count, stream):
-    _check("mg_render", load().mg_render(C.byref(splats), ptr(sorted_vals), ptr(ranges), views,
-                                         n_views, C.byref(cfg), ptr(image), ptr(final_T),
-                                         ptr(n_contrib), ptr(frag_count), stream))
+def mg_tile_order(ranges, n_tiles_total, tile_order, stream):
+    _check("mg_tile_order", load().mg_tile_order(ptr(ranges), n_tiles_total, ptr(tile_order),
+                                                 stream))
+
+
+def mg_render(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, image, final_T,
+              n_contrib, frag_count, stream):
+    _check("mg_render", load().mg_render(C.byref(splats), ptr(sorted_vals), ptr(ranges),
+                                         ptr(tile_order), views, n_views, C.byref(cfg),
+                                         ptr(image), ptr(final_T), ptr(n_contrib),
+                                         ptr(frag_count), stream))
 
 
 def mg_l1_loss_grad(image, target, views, n_views, dL_dimage, loss, stream):
@@ -239,10 +247,11 @@ def mg_l1_loss_grad(image, target, views, n_views, dL_dimage, loss, stream):
                                                      ptr(dL_dimage), ptr(loss), stream))
 
 
-def mg_render_backward(splats, sorted_vals, ranges, views, n_views, cfg, final_T, n_contrib,
-                       dL_dimage, grad2d, counters, stream):
+def mg_render_backward(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, final_T,
+                       n_contrib, dL_dimage, grad2d, counters, stream):
     _check("mg_render_backward", load().mg_render_backward(
-        C.byref(splats), ptr(sorted_vals), ptr(ranges), views, n_views, C.byref(cfg),
+        C.byref(splats), ptr(sorted_vals), ptr(ranges), ptr(tile_order), views, n_views,
+        C.byref(cfg),
         ptr(final_T), ptr(n_contrib), ptr(dL_dimage), ptr(grad2d), ptr(counters), stream))
 
 
@@ -272,10 +281,11 @@ def mg_compact_workspace_bytes(n) -> int:
     return int(load().mg_compact_workspace_bytes(n))
 
 
-def mg_render_inference(splats, sorted_vals, ranges, views, n_views, cfg, image, stream):
+def mg_render_inference(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, image,
+                        stream):
     _check("mg_render_inference", load().mg_render_inference(
-        C.byref(splats), ptr(sorted_vals), ptr(ranges), views, n_views, C.byref(cfg), ptr(image),
-        stream))
+        C.byref(splats), ptr(sorted_vals), ptr(ranges), ptr(tile_order), views, n_views,
+        C.byref(cfg), ptr(image), stream))
 
 
 def mg_read_status(d_status, stream) -> mg_status_word:

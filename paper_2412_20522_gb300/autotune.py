@@ -38,13 +38,14 @@ class GraphStep:
     All buffers are sized by a synchronising first step; the captured graph
     then replays the whole sequence (no host synchronisation inside)."""
 
-    def __init__(self, params, cams, cfg: RasterConfig, target, view_ranges=None, warmup=2):
+    def __init__(self, params, cams, cfg: RasterConfig, target, view_ranges=None, warmup=2,
+                 tile_order=True):
         self.params = params
         self.cams = cams
         self.cfg = cfg
         self.target = target
         self.view_ranges = view_ranges
-        self.rast = Rasterizer(params["means"].device)
+        self.rast = Rasterizer(params["means"].device, tile_order=tile_order)
         self.grads = {k: torch.empty(params[k].shape, dtype=torch.float32,
                                      device=params[k].device) for k in PARAM_NAMES}
         self.rast.forward(params, cams, cfg, view_ranges=view_ranges, check=True)

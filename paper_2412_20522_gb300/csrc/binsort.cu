@@ -80,21 +80,7 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
             atomicExch((unsigned long long *)&ws->status[0], (unsigned long long)(kFlagPrefix64 | agg));
         } else {
             atomicExch((unsigned long long *)&ws->status[part], (unsigned long long)(kFlagAgg64 | agg));
-            for (int64_t q = part - 1; q >= 0; --q) {
-                uint64_t s = ld_volatile(&ws->status[q]);
-                int spins = 0;
-                while ((s >> 62) == 0 && spins < kMaxTimeoutSpins) {
-                    __nanosleep(20);
-                    s = ld_volatile(&ws->status[q]);
-                    ++spins;
-                }
-                if ((s >> 62) == 0) {
-                    raise_status(st, MG_ERR_TIMEOUT, 1, 0);
-                    break;
-                }
-                prefix += s & kValMask64;
-                if ((s >> 62) == 2) break;
-            }
+            prefix = lookback<uint64_t, 62>(ws->status, 1, part, st, 1);
             atomicExch((unsigned long long *)&ws->status[part],
                        (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
         }
@@ -254,7 +240,7 @@ __global__ void sort_offsets_kernel(SortWS *ws) {
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint64_t *d_n,
                 uint64_t capacity, int pass, int shift, SortWS *ws, int64_t max_parts,
@@ -331,21 +317,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
         // ---- decoupled look-back per digit
         uint32_t excl = 0;
         if (part > 0) {
-            for (int64_t q = part - 1; q >= 0; --q) {
-                uint32_t s = ld_volatile(&status[q * 256 + d]);
-                int spins = 0;
-                while ((s >> 30) == 0 && spins < kMaxTimeoutSpins) {
-                    __nanosleep(20);
-                    s = ld_volatile(&status[q * 256 + d]);
-                    ++spins;
-                }
-                if ((s >> 30) == 0) {
-                    raise_status(st, MG_ERR_TIMEOUT, 2, 0);
-                    break;
-                }
-                excl += s & kValMask;
-                if ((s >> 30) == 2) break;
-            }
+            excl = lookback<uint32_t, 30>(status + d, 256, part, st, 2);
             atomicExch(&status[part * 256 + d], kFlagPrefix | ((excl + tot) & kValMask));
         }
         gbase[d] = (int64_t)ws->hist[pass][d] + excl - (int64_t)ds;

@@ -77,6 +77,47 @@ __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_
     return sm_warp[warp] + inc - v;
 }
 
+// Decoupled look-back: the exclusive prefix of partition `part` from the
+// status words of its predecessors (word of partition q at status[q * stride]),
+// summing aggregates back to the first inclusive prefix.  kLookbackWindow
+// predecessors are read at once, so a walk over published aggregates costs
+// one memory round trip per window instead of one per partition.  A word not
+// yet published is polled at most kMaxTimeoutSpins times; then MG_ERR_TIMEOUT
+// (with `detail`) is raised and the partial sum returned.
+constexpr int kLookbackWindow = 8;
+
+template <typename W, int FLAG_SHIFT>
+__device__ __forceinline__ W lookback(const W *status, int64_t stride, int64_t part,
+                                      mg_status_word *st, int32_t detail) {
+    constexpr W kMask = (W(1) << FLAG_SHIFT) - W(1);
+    W excl = 0;
+    int64_t q = part - 1;
+    while (q >= 0) {
+        W s[kLookbackWindow];
+#pragma unroll
+        for (int k = 0; k < kLookbackWindow; ++k)
+            s[k] = (q - k >= 0) ? ld_volatile(status + (q - k) * stride) : W(0);
+#pragma unroll
+        for (int k = 0; k < kLookbackWindow; ++k) {
+            if (q - k < 0) return excl;
+            int spins = 0;
+            while ((s[k] >> FLAG_SHIFT) == 0 && spins < kMaxTimeoutSpins) {
+                __nanosleep(20);
+                s[k] = ld_volatile(status + (q - k) * stride);
+                ++spins;
+            }
+            if ((s[k] >> FLAG_SHIFT) == 0) {
+                raise_status(st, MG_ERR_TIMEOUT, detail, 0);
+                return excl;
+            }
+            excl += s[k] & kMask;
+            if ((s[k] >> FLAG_SHIFT) == 2) return excl;
+        }
+        q -= kLookbackWindow;
+    }
+    return excl;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
 // (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),

@@ -73,21 +73,7 @@ compact_scan_kernel(const uint8_t *__restrict__ keep, int64_t n, int32_t *__rest
             atomicExch((unsigned long long *)&ws->status[0], (unsigned long long)(kFlagPrefix64 | agg));
         } else {
             atomicExch((unsigned long long *)&ws->status[part], (unsigned long long)(kFlagAgg64 | agg));
-            for (int64_t q = part - 1; q >= 0; --q) {
-                uint64_t s = ld_volatile(&ws->status[q]);
-                int spins = 0;
-                while ((s >> 62) == 0 && spins < kMaxTimeoutSpins) {
-                    __nanosleep(20);
-                    s = ld_volatile(&ws->status[q]);
-                    ++spins;
-                }
-                if ((s >> 62) == 0) {
-                    raise_status(st, MG_ERR_TIMEOUT, 3, 0);
-                    break;
-                }
-                prefix += s & kValMask64;
-                if ((s >> 62) == 2) break;
-            }
+            prefix = lookback<uint64_t, 62>(ws->status, 1, part, st, 3);
             atomicExch((unsigned long long *)&ws->status[part],
                        (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
         }

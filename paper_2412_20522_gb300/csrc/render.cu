@@ -147,13 +147,14 @@ __device__ __forceinline__ bool all_done(const bool *done) {
 template <bool COUNT, bool AUX = true>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
-                      const uint32_t *__restrict__ ranges, float bg0, float bg1, float bg2,
+                      const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ tile_order,
+                      float bg0, float bg1, float bg2,
                       float *__restrict__ image, float *__restrict__ final_T,
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count) {
     __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
     __shared__ uint8_t sM[kBatch];
     __shared__ unsigned long long s_frags[4];
-    const int64_t t = blockIdx.x;
+    const int64_t t = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -320,6 +321,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads, 768 / kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+                       const uint32_t *__restrict__ tile_order,
                        float bg0, float bg1, float bg2, const float *__restrict__ final_T,
                        const uint32_t *__restrict__ n_contrib, const float *__restrict__ dL_dimage,
                        float *__restrict__ grad2d, unsigned long long *counters) {
@@ -329,7 +331,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     __shared__ uint8_t sM[kBatch];
     __shared__ float sG[kBatch][kAcc];
     __shared__ uint32_t s_maxstop;
-    const int64_t t = blockIdx.x;
+    const int64_t t = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -551,9 +553,10 @@ __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ imag
 using namespace mg;
 
 extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
-                               const uint32_t *ranges, const mg_view *views, int32_t n_views,
-                               const mg_raster_cfg *cfg, float *image, float *final_T,
-                               uint32_t *n_contrib, uint64_t *frag_count, mg_stream_t stream) {
+                               const uint32_t *ranges, const uint32_t *tile_order,
+                               const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                               float *image, float *final_T, uint32_t *n_contrib,
+                               uint64_t *frag_count, mg_stream_t stream) {
     if (!splats || !splats->record || !sorted_vals || !ranges || !image || !final_T || !n_contrib)
         return MG_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(splats->record) & 15u) != 0) return MG_ERR_INVALID_ARG;
@@ -565,18 +568,19 @@ extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_v
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (frag_count != nullptr)
         render_forward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T,
-            n_contrib, reinterpret_cast<unsigned long long *>(frag_count));
+            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
+            final_T, n_contrib, reinterpret_cast<unsigned long long *>(frag_count));
     else
         render_forward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T,
-            n_contrib, nullptr);
+            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
+            final_T, n_contrib, nullptr);
     return mg_host::launch_status();
 }
 
 extern "C" mg_status mg_render_inference(const mg_splats *splats, const uint32_t *sorted_vals,
-                                         const uint32_t *ranges, const mg_view *views,
-                                         int32_t n_views, const mg_raster_cfg *cfg, float *image,
+                                         const uint32_t *ranges, const uint32_t *tile_order,
+                                         const mg_view *views, int32_t n_views,
+                                         const mg_raster_cfg *cfg, float *image,
                                          mg_stream_t stream) {
     if (!splats || !splats->record || !sorted_vals || !ranges || !image)
         return MG_ERR_INVALID_ARG;
@@ -587,14 +591,15 @@ extern "C" mg_status mg_render_inference(const mg_splats *splats, const uint32_t
     const int64_t tiles = vt.tile_off[n_views];
     if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
     render_forward_kernel<false, false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-        vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, cfg->bg[0],
-        cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
+        vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, tile_order,
+        cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
     return mg_host::launch_status();
 }
 
 extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
-                                        const uint32_t *ranges, const mg_view *views,
-                                        int32_t n_views, const mg_raster_cfg *cfg,
+                                        const uint32_t *ranges, const uint32_t *tile_order,
+                                        const mg_view *views, int32_t n_views,
+                                        const mg_raster_cfg *cfg,
                                         const float *final_T, const uint32_t *n_contrib,
                                         const float *dL_dimage, float *grad2d,
                                         uint64_t *counters, mg_stream_t stream) {
@@ -616,12 +621,12 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (counters != nullptr)
         render_backward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
-            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T, n_contrib,
-            dL_dimage, grad2d, reinterpret_cast<unsigned long long *>(counters));
+            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
+            n_contrib, dL_dimage, grad2d, reinterpret_cast<unsigned long long *>(counters));
     else
         render_backward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
-            vt, rec, sorted_vals, ranges, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T, n_contrib,
-            dL_dimage, grad2d, nullptr);
+            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
+            n_contrib, dL_dimage, grad2d, nullptr);
     return mg_host::launch_status();
 }
 
@@ -641,5 +646,57 @@ extern "C" mg_status mg_l1_loss_grad(const float *image, const float *target,
     const dim3 grid((unsigned)(bx < 2048 ? (bx > 0 ? bx : 1) : 2048), (unsigned)n_views);
     l1_loss_grad_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(vt, image, target, dL_dimage,
                                                                loss);
+    return mg_host::launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Longest-first tile order.  A tile's render time grows with its list length
+// and one CTA renders one tile, so launching the long lists first keeps the
+// SMs busy to the end (list scheduling, longest processing time first).  A
+// one-block counting sort over quarter-octave buckets of the list length;
+// the order inside a bucket is whatever the shared-memory atomics give (it
+// changes only which CTA starts first, never a result).
+// ---------------------------------------------------------------------------
+namespace mg {
+constexpr int kOrderBuckets = 128;
+
+__device__ __forceinline__ int length_bucket(uint32_t c) {
+    if (c < 4) return (int)c;
+    const int msb = 31 - __clz(c);
+    return 4 * (msb - 1) + (int)((c >> (msb - 2)) & 3u);      // 4 .. 123
+}
+
+__global__ void __launch_bounds__(1024)
+tile_order_kernel(const uint32_t *__restrict__ ranges, int64_t n, uint32_t *__restrict__ order) {
+    __shared__ uint32_t hist[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const uint2 r = reinterpret_cast<const uint2 *>(ranges)[t];
+        atomicAdd(&hist[length_bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {                       // starts, longest bucket first
+        uint32_t run = 0;
+        for (int b = kOrderBuckets - 1; b >= 0; --b) {
+            const uint32_t c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const uint2 r = reinterpret_cast<const uint2 *>(ranges)[t];
+        order[atomicAdd(&hist[length_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
+}
+}  // namespace mg
+
+extern "C" mg_status mg_tile_order(const uint32_t *ranges, int64_t n_tiles_total,
+                                   uint32_t *tile_order, mg_stream_t stream) {
+    if (ranges == nullptr || tile_order == nullptr || n_tiles_total <= 0 ||
+        n_tiles_total >= (int64_t(1) << 31) || (reinterpret_cast<uintptr_t>(ranges) & 7u) != 0)
+        return MG_ERR_INVALID_ARG;
+    tile_order_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(ranges, n_tiles_total, tile_order);
     return mg_host::launch_status();
 }

@@ -122,8 +122,10 @@ class Rasterizer:
     """Owns the device buffers of one masked forward+backward and issues the
     C-ABI calls on the current torch stream."""
 
-    def __init__(self, device="cuda", capacity: int = 0, capacity_headroom: float = 1.25):
+    def __init__(self, device="cuda", capacity: int = 0, capacity_headroom: float = 1.25,
+                 tile_order: bool = True):
         self.device = torch.device(device)
+        self.tile_order = tile_order
         self.capacity = int(capacity)
         self.headroom = capacity_headroom
         self._buf = {}
@@ -228,12 +230,17 @@ class Rasterizer:
                           ranges_buf, tiles, sort_ws, sort_ws.numel(), self.status, stream)
         ev.end("sort")
         sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
+        # longest tile lists first (launch order only)
+        tile_order = self._get("tile_order", tiles, torch.int32) if self.tile_order else None
+        if tile_order is not None:
+            abi.mg_tile_order(ranges_buf, tiles, tile_order, stream)
         image = self._get("image", 3 * pix, torch.float32)
         if inference:
             ev.begin("render")
-            abi.mg_render_inference(splats, sorted_vals, ranges_buf, views, V, ccfg, image, stream)
+            abi.mg_render_inference(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg,
+                                    image, stream)
             ev.end("render")
-            self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1
+            self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
             self._state = None
             if check:
                 st = abi.mg_read_status(self.status, stream)
@@ -245,15 +252,16 @@ class Rasterizer:
         if count_fragments:
             self.frag_count.zero_()
         ev.begin("render")
-        abi.mg_render(splats, sorted_vals, ranges_buf, views, V, ccfg, image, final_T, n_contrib,
-                      self.frag_count if count_fragments else None, stream)
+        abi.mg_render(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image, final_T,
+                      n_contrib, self.frag_count if count_fragments else None, stream)
         ev.end("render")
         # kernels of ours per forward: preprocess; depth keys, histogram,
         # offsets, 4 digit passes; scan, duplicate; histogram, offsets, one per
         # tile digit pass, ranges; render
-        self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1
+        self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
         self._state = dict(g=g, views=views, V=V, cfg=ccfg, splats=splats, R=R, n=n, pix=pix,
                            sorted_vals=sorted_vals, ranges=ranges_buf, tiles=tiles,
+                           tile_order=tile_order,
                            sh_degree=sh_degree, params=params, cams=cams)
         if check:
             st = abi.mg_read_status(self.status, stream)
@@ -300,9 +308,10 @@ class Rasterizer:
         ev.begin("render_bwd")
         if count_iterations:
             self.bwd_count.zero_()
-        abi.mg_render_backward(s["splats"], s["sorted_vals"], s["ranges"], s["views"], s["V"],
-                               s["cfg"], self._buf["final_T"], self._buf["n_contrib"], dL_dimage,
-                               grad2d, self.bwd_count if count_iterations else None, stream)
+        abi.mg_render_backward(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"],
+                               s["views"], s["V"], s["cfg"], self._buf["final_T"],
+                               self._buf["n_contrib"], dL_dimage, grad2d,
+                               self.bwd_count if count_iterations else None, stream)
         if out is None:
             out = {k: torch.empty(s["params"][k].shape, dtype=torch.float32, device=self.device)
                    for k in PARAM_NAMES}

@@ -76,7 +76,7 @@ def test_bad_arguments_rejected_on_host(lib):
     g.sh_degree = 3                                           # null arrays
     st = lib.mg_preprocess(C.byref(g), views, 1, C.byref(cfg), C.byref(out), None, None)
     assert st == abi.MG_ERR_INVALID_ARG
-    st = lib.mg_render(C.byref(out), None, None, views, 1, C.byref(cfg), None, None, None,
+    st = lib.mg_render(C.byref(out), None, None, None, views, 1, C.byref(cfg), None, None, None,
                        None, None)
     assert st == abi.MG_ERR_INVALID_ARG
     alt = C.c_int32(0)
@@ -112,5 +112,6 @@ def test_mask_pruning_and_inference_arguments_rejected_on_host(lib):
     assert lib.mg_compact(C.byref(g), None, C.byref(dst), None, None, None, 0, None,
                           None) == abi.MG_ERR_INVALID_ARG
     assert abi.mg_compact_workspace_bytes(1_000_000) >= 4 * 1_000_000
-    assert lib.mg_render_inference(C.byref(out), None, None, views, 1, C.byref(cfg), None,
+    assert lib.mg_render_inference(C.byref(out), None, None, None, views, 1, C.byref(cfg), None,
                                    None) == abi.MG_ERR_INVALID_ARG
+    assert lib.mg_tile_order(None, 10, None, None) == abi.MG_ERR_INVALID_ARG
