@@ -288,20 +288,66 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Warp sum of 16 values by halving exchanges (16 shuffles instead of 80):
-// on return lane l holds the sum over the warp of v[l >> 1].
-__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane) {
+// Warp sums of a splat's ten gradient terms by halving exchanges that split
+// the values unevenly where ten does not halve (10 -> 5 -> 3|2 -> 2|1 -> 1):
+// 12 shuffles.  On return the lane holds the warp sum of term
+// red_term(lane) (see below); every term is held by at least two lanes.
+__device__ __forceinline__ float warp_transpose_sum10(const float v[10], int lane) {
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2;
+    // xor 16: keep five (0-4 or 5-9), send the other five
+    float a[5];
 #pragma unroll
-    for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
-        const bool up = (lane & bit) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const float send = up ? v[i] : v[i + half];
-            const float keep = up ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
-        }
+    for (int i = 0; i < 5; ++i) {
+        const float send = b16 ? v[i] : v[i + 5];
+        const float keep = b16 ? v[i + 5] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    // xor 8: lanes without bit 8 keep a0..a2, lanes with it keep a3, a4
+    float b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float send = b8 ? a[i] : (i < 2 ? a[i + 3] : 0.0f);
+        const float keep = b8 ? (i < 2 ? a[i + 3] : 0.0f) : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    // xor 4: three values split 2 | 1, two values split 1 | 1
+    float c[2];
+    {
+        // first exchange: (no bit 8) bit 4 clear keeps b0, sends b2; set keeps b2, sends b0
+        //                 (bit 8)    bit 4 clear keeps b0, sends b1; set keeps b1, sends b0
+        const float send0 = b4 ? b[0] : (b8 ? b[1] : b[2]);
+        const float keep0 = b4 ? (b8 ? b[1] : b[2]) : b[0];
+        c[0] = keep0 + __shfl_xor_sync(0xffffffffu, send0, 4);
+        // second exchange: only the three-value lanes move b1 (kept by bit 4 clear)
+        const float send1 = (!b8 && b4) ? b[1] : 0.0f;
+        const float keep1 = (!b8 && !b4) ? b[1] : 0.0f;
+        c[1] = keep1 + __shfl_xor_sync(0xffffffffu, send1, 4);
+    }
+    // xor 2: the two-value lanes (no bit 8, no bit 4) split c0 | c1; the others add
+    float d;
+    {
+        const bool two = !b8 && !b4;
+        const float send = two ? (b2 ? c[0] : c[1]) : c[0];
+        const float keep = two ? (b2 ? c[1] : c[0]) : c[0];
+        d = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+
+// The term whose warp sum warp_transpose_sum10 leaves in `lane`, and whether
+// the lane is the one that flushes it (one lane per term).
+__device__ __forceinline__ int red_term(int lane, bool &writer) {
+    const int hi = (lane & 16) ? 5 : 0;
+    const bool b8 = lane & 8, b4 = lane & 4, b2 = lane & 2, b1 = lane & 1;
+    int term;
+    if (!b8 && !b4) {
+        term = hi + (b2 ? 1 : 0);
+        writer = !b1;
+    } else {
+        term = hi + (b8 ? (b4 ? 4 : 3) : 2);
+        writer = !b1 && !b2;
+    }
+    return term;
 }
 
 // Per splat and tile, the backward accumulates in shared memory
@@ -335,6 +381,8 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     const TileInfo ti = tile_info(vt, t);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool red_writer;
+    const int red_t = red_term(lane, red_writer);   // term this lane flushes
 
     float fpx[kPix], fpy[kPix], T[kPix], g0[kPix], g1[kPix], g2[kPix], bc0[kPix], bc1[kPix],
         bc2[kPix];
@@ -421,9 +469,9 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     for (int k = 0; k < kPix; ++k) ncontrib += (int)on[k];
                     if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) continue;
                     const float4 c = sC[j];
-                    float v[16];
+                    float v[10];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+                    for (int q = 0; q < 10; ++q) v[q] = 0.0f;
 #pragma unroll
                     for (int k = 0; k < kPix; ++k) {
                         if (!on[k]) continue;
@@ -468,8 +516,8 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                             const float dm = warp_sum(v[9]);
                             if (lane == 0) atomicAdd(&sG[j][9], dm);
                         } else {
-                            const float r = warp_transpose_sum16(v, lane);
-                            if ((lane & 1) == 0 && (lane >> 1) < kAcc) atomicAdd(&sG[j][lane >> 1], r);
+                            const float r = warp_transpose_sum10(v, lane);
+                            if (red_writer) atomicAdd(&sG[j][red_t], r);
                         }
                     }
                 }
