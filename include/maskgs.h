@@ -141,8 +141,9 @@ typedef struct {
     int64_t gaussian_count;
 } mg_view;
 
-/* tile_w x tile_h must be 256 pixels with both sides powers of two
- * (16x16 is the paper's grid, Sec. 3.1; 8x32 and 32x8 are also accepted).
+/* tile_w x tile_h: 16x16 (the paper's grid, Sec. 3.1), 32x8 or 8x32 (256
+ * pixels, both sides powers of two and at least 8; other shapes return
+ * MG_ERR_INVALID_ARG).
  * Gumbel noise: u_k from Philox4x32-10 (Salmon et al., SC'11) with counter
  * (i, iteration_lo, iteration_hi, 0) and key (seed_lo, seed_hi), outputs 0 and
  * 1 mapped to (2 (x >> 9) + 1) 2^-24.  mask_mode MG_MASK_GIVEN reads

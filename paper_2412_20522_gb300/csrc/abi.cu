@@ -12,7 +12,9 @@ mg_status build_view_table(const mg_view *views, int32_t n_views, const mg_raste
                            mg::ViewTable *vt) {
     if (views == nullptr || cfg == nullptr || vt == nullptr) return MG_ERR_INVALID_ARG;
     if (n_views < 1 || n_views > MG_MAX_VIEWS) return MG_ERR_INVALID_ARG;
-    if (!pow2(cfg->tile_w) || !pow2(cfg->tile_h) || cfg->tile_w * cfg->tile_h != mg::kTilePixels)
+    // 256-pixel tiles made of four 8x8 warp blocks: 16x16, 32x8 or 8x32
+    if (!pow2(cfg->tile_w) || !pow2(cfg->tile_h) || cfg->tile_w * cfg->tile_h != mg::kTilePixels ||
+        cfg->tile_w < 8 || cfg->tile_h < 8)
         return MG_ERR_INVALID_ARG;
     memset(vt, 0, sizeof(*vt));
     vt->n_views = n_views;

@@ -62,13 +62,17 @@ __device__ __forceinline__ void frag_alpha(const float4 &A, const float4 &B, flo
     }
 }
 
-// Tile of the CTA and the kPix pixels of this thread.  Warp w owns rows
-// [w * bh, (w+1) * bh) of the tile, bh = 32 kPix / tw; a lane's pixels are
-// (l % tw, l / tw) and the same column 32/tw, 2*32/tw, ... rows further down.
+// Tile of the CTA and the kPix pixels of this thread.  Each warp owns one
+// 8x8 block of the tile (square blocks: fewer splats straddle a block edge
+// than with 16x4 strips), block w at (8 (w % nbx), 8 (w / nbx)), nbx =
+// tile_w / 8; lane l's pixels are (l % 8, l / 8) and the same column 4 rows
+// further down.
+constexpr int kBlock = 8;
+
 struct TileInfo {
     int v;
     int x0, y0;          // tile origin (pixels)
-    int bh;              // rows per warp block (64 / tile_w)
+    int nbx;             // 8x8 blocks per tile row
     int px[kPix], py[kPix];
     bool inside[kPix];
     int64_t pix[kPix];   // pixel index within the view
@@ -81,14 +85,14 @@ __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
     const int gx = vt.gx[ti.v];
     ti.x0 = (int)(lt % gx) * vt.tile_w;
     ti.y0 = (int)(lt / gx) * vt.tile_h;
-    const int tw = vt.tile_w;
-    ti.bh = (32 * kPix) / tw;
+    ti.nbx = vt.tile_w / kBlock;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int bx = ti.x0 + kBlock * (warp % ti.nbx), by = ti.y0 + kBlock * (warp / ti.nbx);
     const mg_camera &C = vt.cam[ti.v];
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
-        ti.px[k] = ti.x0 + (lane & (tw - 1));
-        ti.py[k] = ti.y0 + warp * ti.bh + (lane >> vt.log2_tw) + k * (32 / tw);
+        ti.px[k] = bx + (lane & (kBlock - 1));
+        ti.py[k] = by + (lane >> 3) + k * (32 / kBlock);
         ti.inside[k] = ti.px[k] < C.width && ti.py[k] < C.height;
         ti.pix[k] = (int64_t)ti.py[k] * C.width + ti.px[k];
     }
@@ -105,7 +109,7 @@ __device__ __forceinline__ TileInfo tile_info(const ViewTable &vt, int64_t t) {
 // per-pixel alpha test, on the same set of splats.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t block_mask(const float4 &A, const float4 &B, float x0,
-                                               float y0, int bw, int bh) {
+                                               float y0, int nbx) {
     // e_min < 0 is the stored skip threshold (already pushed outwards by
     // 1e-3 in log2 alpha); e_min > 0 marks a splat that never reaches the floor
     const float e_thr = B.w;
@@ -116,12 +120,13 @@ __device__ __forceinline__ uint32_t block_mask(const float4 &A, const float4 &B,
     const float aux = fabsf(ux), auy = fabsf(uy);
     const float ex = sqrtf(r1 * r1 * ux * ux + r2 * r2 * uy * uy) + 0.02f;
     const float ey = sqrtf(r1 * r1 * uy * uy + r2 * r2 * ux * ux) + 0.02f;
-    const float hw = 0.5f * (float)(bw - 1), hh = 0.5f * (float)(bh - 1);
-    const float cx = x0 + 0.5f * (float)bw;
+    // pixel centres of a block span its origin + 0.5 .. + 7.5
+    const float hw = 0.5f * (float)(kBlock - 1), hh = hw;
     uint32_t m = 0u;
 #pragma unroll
     for (int w = 0; w < kRenderWarps; ++w) {
-        const float cy = y0 + (float)(w * bh) + 0.5f * (float)bh;
+        const float cx = x0 + (float)(kBlock * (w % nbx)) + 0.5f * (float)kBlock;
+        const float cy = y0 + (float)(kBlock * (w / nbx)) + 0.5f * (float)kBlock;
         const float dx = cx - A.x, dy = cy - A.y;
         const bool sep_x = fabsf(dx) > ex + hw;
         const bool sep_y = fabsf(dy) > ey + hh;
@@ -186,7 +191,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 sC[i] = rec[3 * (int64_t)r + 2];
                 // masked splats neither colour nor attenuate: out of every forward list
                 sM[i] = (uint8_t)((B.z > 0.0f)
-                                      ? block_mask(A, B, (float)ti.x0, (float)ti.y0, vt.tile_w, ti.bh)
+                                      ? block_mask(A, B, (float)ti.x0, (float)ti.y0, ti.nbx)
                                       : 0u);
             }
         }
@@ -438,7 +443,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                 sA[i] = A;
                 sB[i] = B;
                 sC[i] = rec[3 * (int64_t)r + 2];
-                sM[i] = (uint8_t)block_mask(A, B, (float)ti.x0, (float)ti.y0, vt.tile_w, ti.bh);
+                sM[i] = (uint8_t)block_mask(A, B, (float)ti.x0, (float)ti.y0, ti.nbx);
             }
 #pragma unroll
             for (int k = 0; k < kAcc; ++k) sG[i][k] = 0.0f;

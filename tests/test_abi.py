@@ -58,6 +58,8 @@ def test_host_only_helpers(lib):
     assert abi.mg_total_tiles(views, 1, cfg) == 195 * 33
     cfg.tile_w = 12
     assert abi.mg_total_tiles(views, 1, cfg) == -1          # not a power of two
+    cfg.tile_w, cfg.tile_h = 64, 4
+    assert abi.mg_total_tiles(views, 1, cfg) == -1          # no 8x8 warp blocks
     assert abi.mg_bin_workspace_bytes(1_200_000) > 8 * (1_200_000 // 2048)
     assert abi.mg_sort_workspace_bytes(10_000_000, 46) > 2 * 256 * 4 * (10_000_000 // 3072)
 

@@ -39,7 +39,7 @@ def test_graph_replay_equals_eager_step():
     for k in PARAM_NAMES:
         # atomics may reorder FP32 sums: equal up to rounding
         assert rel_l2(gs.grads[k].cpu().numpy(), grads[k].cpu().numpy()) < 1e-5, k
-    assert abs(float(loss) - float(gs.loss)) < 1e-6
+    assert abs(float(loss) - float(gs.loss)) < 1e-5 * abs(float(loss))    # atomic sum
 
 
 def _tile_lists(rast, t0, nt, r0):
