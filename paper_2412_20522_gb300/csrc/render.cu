@@ -21,10 +21,7 @@
 
 namespace mg {
 
-#ifndef MG_RENDER_PIX
-#define MG_RENDER_PIX 2
-#endif
-constexpr int kPix = MG_RENDER_PIX;              // pixels per thread
+constexpr int kPix = 2;                          // pixels per thread (one column pair)
 constexpr int kRenderThreads = 256 / kPix;       // threads per CTA (one 256-pixel tile)
 constexpr int kRenderWarps = kRenderThreads / 32;
 constexpr int kBatch = 256;                      // splats staged per batch
@@ -46,12 +43,11 @@ struct Frag {
 // preprocess, just below log2(1/(255 o))) lets both kernels skip the exp of
 // fragments whose alpha is certainly under the floor; the alpha test itself
 // still decides every other fragment, identically in both kernels.
-__device__ __forceinline__ void frag_alpha(const float4 &A, const float4 &B, float fpx, float fpy,
-                                           Frag &f) {
-    f.dx = __fsub_rn(fpx, A.x);
-    f.dy = __fsub_rn(fpy, A.y);
-    f.p1 = __fmaf_rn(f.dy, A.w, __fmul_rn(f.dx, A.z));
-    f.p2 = __fmaf_rn(f.dy, A.z, -__fmul_rn(f.dx, A.w));
+// A thread's two pixels share a column, kRowStep rows apart: the second
+// pixel's offsets follow from the first's (d.y + 4, p1 + 4 uy, p2 + 4 ux).
+constexpr float kRowStep = 4.0f;
+
+__device__ __forceinline__ void frag_finish(const float4 &B, Frag &f) {
     f.e = __fmaf_rn(__fmul_rn(B.x, f.p1), f.p1, __fmul_rn(__fmul_rn(B.y, f.p2), f.p2));
     f.on = false;
     if (f.e >= B.w) {
@@ -60,6 +56,20 @@ __device__ __forceinline__ void frag_alpha(const float4 &A, const float4 &B, flo
         f.alpha = fminf(kAlphaMax, f.araw);
         f.on = f.alpha >= kAlphaMin;
     }
+}
+
+__device__ __forceinline__ void frag_alpha_pair(const float4 &A, const float4 &B, float fpx,
+                                                float fpy0, Frag f[2]) {
+    f[0].dx = __fsub_rn(fpx, A.x);
+    f[0].dy = __fsub_rn(fpy0, A.y);
+    f[0].p1 = __fmaf_rn(f[0].dy, A.w, __fmul_rn(f[0].dx, A.z));
+    f[0].p2 = __fmaf_rn(f[0].dy, A.z, -__fmul_rn(f[0].dx, A.w));
+    f[1].dx = f[0].dx;
+    f[1].dy = __fadd_rn(f[0].dy, kRowStep);
+    f[1].p1 = __fmaf_rn(kRowStep, A.w, f[0].p1);
+    f[1].p2 = __fmaf_rn(kRowStep, A.z, f[0].p2);
+    frag_finish(B, f[0]);
+    frag_finish(B, f[1]);
 }
 
 // Tile of the CTA and the kPix pixels of this thread.  Each warp owns one
@@ -205,8 +215,9 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 float Tc = T[k];
                 for (int j = 0; j < cnt; ++j) {
                     const float4 B = sB[j];
-                    Frag f;
-                    frag_alpha(sA[j], B, fpx[k], fpy[k], f);
+                    Frag fp[kPix];
+                    frag_alpha_pair(sA[j], B, fpx[0], fpy[0], fp);
+                    const Frag &f = fp[k];
                     if (B.z < 0.0f) {
                         c_masked += f.on;
                         continue;
@@ -232,11 +243,12 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 const int j = (ch << 5) + __ffs(word) - 1;
                 word &= word - 1;
                 const float4 A = sA[j], B = sB[j], c = sC[j];
+                Frag fp[kPix];
+                frag_alpha_pair(A, B, fpx[0], fpy[0], fp);
 #pragma unroll
                 for (int k = 0; k < kPix; ++k) {
                     if (done[k]) continue;
-                    Frag f;
-                    frag_alpha(A, B, fpx[k], fpy[k], f);
+                    const Frag &f = fp[k];
                     if (!f.on) continue;
                     const float testT = T[k] * (1.0f - f.alpha);
                     if (testT < kTMin) {
@@ -464,11 +476,9 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     // alpha of every pixel first: independent, so they interleave
                     Frag f[kPix];
                     bool on[kPix];
+                    frag_alpha_pair(A, B, fpx[0], fpy[0], f);
 #pragma unroll
-                    for (int k = 0; k < kPix; ++k) {
-                        frag_alpha(A, B, fpx[k], fpy[k], f[k]);
-                        on[k] = pos0 + j < stop[k] && f[k].on;
-                    }
+                    for (int k = 0; k < kPix; ++k) on[k] = pos0 + j < stop[k] && f[k].on;
                     int ncontrib = 0;
 #pragma unroll
                     for (int k = 0; k < kPix; ++k) ncontrib += (int)on[k];
