@@ -173,7 +173,11 @@ typedef struct {
  *     e_min, a skip threshold just below log2(1/(255 o)) for the exponent
  *     (1 if o < 1/255: the splat never reaches the floor); r, g, b; depth tz.
  *   tiles_touched[R] u32 (0 = culled), radius[R] i32 (pixels, 0 = culled),
- *   clamp[R] u8 (bit c: colour channel c was clamped at 0).
+ *   clamp[R] u8 (bit c: colour channel c was clamped at 0),
+ *   tile_rect[R][2] u32 of a visible record: the global id of the first
+ *   (top-left) tile of its rectangle, and w | gx << 16 (rectangle width and
+ *   the view's tiles per row); tile m of the rectangle (row-major) is
+ *   first + (m / w) gx + m % w.
  *   With MG_APPLY_OPACITY the stored opacity is M o (+0 for a masked splat,
  *   e_min = 1).
  * Per-Gaussian (n):
@@ -188,6 +192,7 @@ typedef struct {
     uint32_t *tiles_touched;
     int32_t *radius;
     uint8_t *clamp;
+    uint32_t *tile_rect;
     uint8_t *mask;
     float *mask_soft;
     uint32_t *mask_count;

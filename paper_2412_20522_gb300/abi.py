@@ -68,8 +68,8 @@ class mg_raster_cfg(C.Structure):
 
 class mg_splats(C.Structure):
     _fields_ = [("record", C.c_void_p), ("tiles_touched", C.c_void_p), ("radius", C.c_void_p),
-                ("clamp", C.c_void_p), ("mask", C.c_void_p), ("mask_soft", C.c_void_p),
-                ("mask_count", C.c_void_p)]
+                ("clamp", C.c_void_p), ("tile_rect", C.c_void_p), ("mask", C.c_void_p),
+                ("mask_soft", C.c_void_p), ("mask_count", C.c_void_p)]
 
 
 class mg_gaussian_arrays(C.Structure):

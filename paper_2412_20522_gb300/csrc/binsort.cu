@@ -102,65 +102,95 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 // --------------------------------------------------------------------------
 // key duplication
 // --------------------------------------------------------------------------
-// A warp's 32 positions own one contiguous range of instance slots (their
-// offsets are consecutive).  The warp writes that range 32 slots at a time,
-// fully coalesced: slot p belongs to the last lane L with offsets[L] <= p
-// (binary search over the lanes by shuffles), and is tile m = p - offsets[L]
-// of L's rectangle, row-major.
+// Slot-parallel: warp w writes instance slots [w C, (w + 1) C), C = 1024,
+// whatever splats they belong to.  (A warp per 32 splats would leave the
+// nearest splats -- first in depth order, and the largest, thousands of
+// tiles each -- to a few warps: the kernel's time was their tail.)  The warp
+// finds the position owning its first slot by a 32-ary search of the offsets
+// (non-decreasing; the owner is the last position whose offset is <= the
+// slot), then walks positions 32 at a time: each lane holds one position's
+// offset, record and tile rectangle, and every 32 consecutive slots find
+// their owner lane by a binary search over the lanes (shuffles) and are
+// written fully coalesced.  Slot m of a rectangle is tile first +
+// (m / w) gx + m % w (row-major), the quotient through an FP32 reciprocal
+// corrected to the exact integer.
+constexpr int kDupChunk = 1024;
+
 __global__ void __launch_bounds__(256)
-duplicate_kernel(ViewTable vt, const float *__restrict__ record,
-                 const int32_t *__restrict__ radius, const uint32_t *__restrict__ tiles,
+duplicate_kernel(const uint2 *__restrict__ tile_rect, const uint32_t *__restrict__ tiles,
                  const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
-                 int64_t n_records, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                 uint64_t capacity) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                 int64_t n_records, const uint64_t *__restrict__ d_num_instances,
+                 uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t capacity) {
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = i - lane;
-    if (w0 >= n_records) return;                       // whole warp past the end
-    uint32_t r = 0, nt = 0, off, tbase = 0, gx = 1, x0 = 0, y0 = 0, w = 1;
-    if (i < n_records) {
-        r = order ? order[i] : (uint32_t)i;
-        off = offsets[i];
-        nt = tiles[r];
-        if (nt != 0) {
-            int v = 0;
-            while (v + 1 < vt.n_views && vt.rec_off[v + 1] <= (int64_t)r) ++v;
-            const float2 m = *reinterpret_cast<const float2 *>(record + 12 * (int64_t)r);
-            int ix0, ix1, iy0, iy1;
-            if (tile_rect(m.x, m.y, (float)radius[r], vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v],
-                          ix0, ix1, iy0, iy1)) {
-                gx = (uint32_t)vt.gx[v];
-                tbase = (uint32_t)vt.tile_off[v];
-                x0 = (uint32_t)ix0;
-                y0 = (uint32_t)iy0;
-                w = (uint32_t)(ix1 - ix0 + 1);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t total = *d_num_instances;
+    const uint64_t K = total < capacity ? total : capacity;
+    const uint64_t s0 = (uint64_t)gw * kDupChunk;
+    if (s0 >= K) return;                                  // warp-uniform
+    const uint64_t s1 = s0 + kDupChunk < K ? s0 + kDupChunk : K;
+
+    // owner of slot s0: the last position i with offsets[i] <= s0 (offsets[0] = 0)
+    int64_t lo = 0, hi = n_records;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = lo + (int64_t)lane * step;
+        const bool le = idx < hi && (uint64_t)offsets[idx] <= s0;
+        const unsigned b = __ballot_sync(FULL, le);
+        lo += (int64_t)(31 - __clz(b)) * step;
+        hi = lo + step < hi ? lo + step : hi;
+    }
+    {
+        const int64_t idx = lo + lane;
+        const bool le = idx < hi && (uint64_t)offsets[idx] <= s0;
+        lo += 31 - __clz(__ballot_sync(FULL, le));
+    }
+
+    uint64_t s = s0;
+    for (int64_t i = lo; s < s1; i += 32) {
+        const int64_t ip = i + lane;
+        uint32_t off = 0xFFFFFFFFu, nt = 0, r = 0, first = 0, w = 1, gx = 1;
+        if (ip < n_records) {
+            off = offsets[ip];
+            r = order ? order[ip] : (uint32_t)ip;
+            nt = tiles[r];
+            if (nt != 0) {
+                const uint2 rc = tile_rect[r];
+                first = rc.x;
+                w = rc.y & 0xFFFFu;
+                gx = rc.y >> 16;
             }
         }
-    } else {
-        off = offsets[n_records - 1] + tiles[order ? order[n_records - 1] : (uint32_t)(n_records - 1)];
-    }
-    const uint64_t begin = __shfl_sync(0xffffffffu, off, 0);
-    const uint64_t end = (uint64_t)__shfl_sync(0xffffffffu, off + nt, 31);
-    const uint64_t stop = end < capacity ? end : capacity;
-    for (uint64_t base = begin; base < stop; base += 32) {   // warp-uniform trip count
-        const uint64_t p = base + lane;
-        const uint32_t pp = (uint32_t)p;
-        int L = 0;
+        const float rw = 1.0f / (float)w;
+        // slots of these 32 positions: up to the end of the last valid one
+        const uint64_t last = ip < n_records ? (uint64_t)off + nt : K;
+        const uint64_t gend_all = __shfl_sync(FULL, last, 31);
+        const uint64_t gend = gend_all < s1 ? gend_all : s1;
+        for (uint64_t base = s; base < gend; base += 32) {      // warp-uniform trip count
+            const uint64_t p = base + lane;
+            const uint32_t pp = (uint32_t)p;
+            int L = 0;
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t oc = __shfl_sync(0xffffffffu, off, L + step);
-            if (oc <= pp) L += step;
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t oc = __shfl_sync(FULL, off, L + step);
+                if (oc <= pp) L += step;
+            }
+            const uint32_t m = pp - __shfl_sync(FULL, off, L);
+            const uint32_t wl = __shfl_sync(FULL, w, L);
+            const float rwl = __shfl_sync(FULL, rw, L);
+            uint32_t q = (uint32_t)((float)m * rwl);
+            int32_t rem = (int32_t)(m - q * wl);
+            if (rem < 0) { --q; rem += (int32_t)wl; }
+            else if (rem >= (int32_t)wl) { ++q; rem -= (int32_t)wl; }
+            const uint32_t key = __shfl_sync(FULL, first, L) + q * __shfl_sync(FULL, gx, L) +
+                                 (uint32_t)rem;
+            const uint32_t rr = __shfl_sync(FULL, r, L);
+            if (p < gend) {
+                keys[p] = key;
+                vals[p] = rr;
+            }
         }
-        const uint32_t m = pp - __shfl_sync(0xffffffffu, off, L);
-        const uint32_t wl = __shfl_sync(0xffffffffu, w, L);
-        const uint32_t key = __shfl_sync(0xffffffffu, tbase, L) +
-                             (__shfl_sync(0xffffffffu, y0, L) + m / wl) * __shfl_sync(0xffffffffu, gx, L) +
-                             __shfl_sync(0xffffffffu, x0, L) + m % wl;
-        const uint32_t rr = __shfl_sync(0xffffffffu, r, L);
-        if (p < stop) {
-            keys[p] = key;
-            vals[p] = rr;
-        }
+        s = gend;
     }
 }
 
@@ -378,6 +408,12 @@ __global__ void depth_keys_kernel(const float *__restrict__ record,
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = (uint64_t)n;
 }
 
+static unsigned dup_blocks(uint64_t capacity) {
+    const uint64_t warps = (capacity + kDupChunk - 1) / kDupChunk;
+    const uint64_t blocks = (warps + 7) / 8;
+    return (unsigned)(blocks > 0 ? blocks : 1);
+}
+
 static int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -476,8 +512,8 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
                             uint32_t *keys, uint32_t *vals, uint64_t capacity,
                             uint64_t *d_num_instances, void *workspace, size_t workspace_bytes,
                             mg_status_word *d_status, mg_stream_t stream) {
-    if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
-        !offsets || !d_num_instances || !workspace)
+    if (splats == nullptr || !splats->tile_rect || !splats->tiles_touched || !offsets ||
+        !d_num_instances || !workspace)
         return MG_ERR_INVALID_ARG;
     if (capacity > 0 && (!keys || !vals)) return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
@@ -502,9 +538,9 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
                                                          d_num_instances, capacity, ws, parts,
                                                          d_status);
     if (capacity > 0)
-        duplicate_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(
-            vt, splats->record, splats->radius, splats->tiles_touched, order, offsets, R, keys,
-            vals, capacity);
+        duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
+            reinterpret_cast<const uint2 *>(splats->tile_rect), splats->tiles_touched, order,
+            offsets, R, d_num_instances, keys, vals, capacity);
     return mg_host::launch_status();
 }
 
@@ -587,8 +623,8 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
                                     const uint32_t *order, uint32_t *offsets, uint32_t *keys,
                                     uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
                                     mg_status_word *d_status, mg_stream_t stream) {
-    if (splats == nullptr || !splats->record || !splats->radius || !splats->tiles_touched ||
-        !offsets || !d_num_instances)
+    if (splats == nullptr || !splats->tile_rect || !splats->tiles_touched || !offsets ||
+        !d_num_instances)
         return MG_ERR_INVALID_ARG;
     if (capacity > 0 && (!keys || !vals)) return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
@@ -618,8 +654,8 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
                                                          d_num_instances, capacity, ws, parts,
                                                          d_status);
     if (capacity > 0)
-        duplicate_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(
-            vt, splats->record, splats->radius, splats->tiles_touched, order, offsets, R, keys,
-            vals, capacity);
+        duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
+            reinterpret_cast<const uint2 *>(splats->tile_rect), splats->tiles_touched, order,
+            offsets, R, d_num_instances, keys, vals, capacity);
     return mg_host::launch_status();
 }

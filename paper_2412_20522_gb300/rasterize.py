@@ -152,6 +152,7 @@ class Rasterizer:
         s.tiles_touched = self._get("tiles", R, torch.int32).data_ptr()
         s.radius = self._get("radius", R, torch.int32).data_ptr()
         s.clamp = self._get("clamp", R, torch.uint8).data_ptr()
+        s.tile_rect = self._get("tile_rect", 2 * R, torch.int32).data_ptr()
         s.mask = self._get("mask", n, torch.uint8).data_ptr()
         s.mask_soft = self._get("mask_soft", n, torch.float32).data_ptr()
         return s
