@@ -3,18 +3,25 @@
 Sec. 3.1: only Gaussians intersecting a tile of the 16x16 grid take part in
 that tile's pixels, and each pixel blends its Gaussians in depth order.
 Instances are emitted per visible Gaussian in index order, tiles row-major
-within its rectangle, with key (tile << 32) | depth_bits; a stable sort by
-key therefore orders each tile's list by depth and breaks depth ties by
-Gaussian index.  numpy's stable argsort serves as the sort primitive.
+within its rectangle, with key (tile << 32) | depth_bits; the tile filter of
+the decision path drops the pairs where the Gaussian stays under the alpha
+floor in the whole tile; a stable sort by key orders each tile's list by
+depth and breaks depth ties by Gaussian index.  numpy's stable argsort
+serves as the sort primitive.
 """
 from __future__ import annotations
 
 import numpy as np
 
+from . import fp32_path
 
-def emit_instances(fp32, grid_w):
+
+def emit_instances(fp32, grid_w, tile_w=16, tile_h=16):
     """Keys (uint64) and values (uint32 Gaussian index) in emission order,
-    plus the exclusive prefix sum of tiles-touched (uint64) and K."""
+    the exclusive prefix sum of tiles-touched (uint64), K (the rectangle's
+    instances) and keep (bool per instance): the decision-path tile filter
+    (``fp32_path.tile_hit``) that drops the pairs where the Gaussian is under
+    the alpha floor at every pixel of the tile."""
     tiles = fp32["tiles"].astype(np.int64)
     n = tiles.shape[0]
     offsets = np.zeros(n + 1, np.int64)
@@ -29,7 +36,10 @@ def emit_instances(fp32, grid_w):
     tid = (ty * grid_w + tx).astype(np.uint64)
     keys = (tid << np.uint64(32)) | fp32["depth_bits"].astype(np.uint64)[g]
     vals = g.astype(np.uint32)
-    return keys, vals, offsets[:-1].astype(np.uint64), K
+    tdet, rba, rbc = fp32_path.tile_filter_params(fp32)
+    keep = fp32_path.tile_hit(fp32["px"][g], fp32["py"][g], fp32["a"][g], fp32["b"][g],
+                              fp32["c"][g], tdet[g], rba[g], rbc[g], tx, ty, tile_w, tile_h)
+    return keys, vals, offsets[:-1].astype(np.uint64), K, keep
 
 
 def sort_instances(keys, vals):

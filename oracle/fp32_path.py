@@ -300,3 +300,57 @@ def project32(means, log_scales, quats, cam, tile_w=16, tile_h=16):
                 x0=x0i, x1=x1i, y0=y0i, y1=y1i, tiles=tiles,
                 depth_bits=tz.view(np.uint32).copy(), visible=nonempty,
                 grid=(gx, gy))
+
+
+# ---------------------------------------------------------------------------
+# Tile filter of the binning: a Gaussian is kept in a tile of its rectangle
+# unless, at every pixel centre of the tile, its quadratic form
+# q = d^T Sigma_bar^-1 d exceeds 2 ln 255 -- where alpha = o exp(-q/2) <
+# 1/255 for any opacity o <= 1, so the Gaussian is filtered at every pixel
+# of the tile (Sec. 3.1: only Gaussians with alpha above the floor take
+# part).  Dropping such pairs changes no image and no gradient; it shortens
+# the tile lists.  The test takes the minimum of the numerator
+# N = c dx^2 - 2 b dx dy + a dy^2 = det q over the box of pixel centres (the
+# centre inside, else the minimum of each edge at its clamped stationary
+# point) and keeps the pair if N <= 11.1 det + 1e-4 (|terms| summed): 11.1 >
+# 2 ln 255 = 11.0825, and the relative slack covers the rounding of N.
+# ---------------------------------------------------------------------------
+T_BIN = f32(11.1)
+REL_BIN = f32(1e-4)
+
+
+def tile_filter_params(fp):
+    """Per Gaussian: (t det, b / a, b / c), correctly rounded FP32."""
+    a, b, c, det = fp["a"], fp["b"], fp["c"], fp["det"]
+    ok = fp["tiles"] > 0
+    one = f32(1.0)
+    aa = np.where(ok, a, one)
+    cc = np.where(ok, c, one)
+    return T_BIN * det, b / aa, b / cc
+
+
+def _edge_hit(N_terms, tdet):
+    t1, t2, t3 = N_terms
+    t22 = t2 + t2
+    N = (t1 - t22) + t3
+    bnd = (t1 + np.abs(t22)) + t3
+    return N <= tdet + REL_BIN * bnd
+
+
+def tile_hit(px, py, a, b, c, tdet, rba, rbc, tx, ty, tile_w, tile_h):
+    """Keep (True) or drop the Gaussian/tile pairs given per pair (arrays of
+    equal length; tile column tx and row ty within the view)."""
+    X0 = (tx * tile_w).astype(np.float32) + f32(0.5)
+    Y0 = (ty * tile_h).astype(np.float32) + f32(0.5)
+    X1 = X0 + f32(tile_w - 1)
+    Y1 = Y0 + f32(tile_h - 1)
+    dx0, dx1 = X0 - px, X1 - px
+    dy0, dy1 = Y0 - py, Y1 - py
+    hit = (dx0 <= f32(0.0)) & (dx1 >= f32(0.0)) & (dy0 <= f32(0.0)) & (dy1 >= f32(0.0))
+    for dxe in (dx0, dx1):                      # vertical edges
+        dyc = np.minimum(np.maximum(rba * dxe, dy0), dy1)
+        hit |= _edge_hit((c * (dxe * dxe), (b * dxe) * dyc, a * (dyc * dyc)), tdet)
+    for dye in (dy0, dy1):                      # horizontal edges
+        dxc = np.minimum(np.maximum(rbc * dye, dx0), dx1)
+        hit |= _edge_hit((c * (dxc * dxc), (b * dxc) * dye, a * (dye * dye)), tdet)
+    return hit

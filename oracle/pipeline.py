@@ -62,6 +62,12 @@ class OracleView:
     splats: render.SplatsF64
     out: dict
     values64: dict = field(default_factory=dict)
+    keep: np.ndarray | None = None     # tile filter per emitted instance
+
+    @property
+    def K_kept(self) -> int:
+        """Instances in the tile lists (the rectangle's K minus the filtered)."""
+        return int(self.sorted_vals.shape[0])
 
 
 def gaussian_params64(g) -> dict:
@@ -113,8 +119,8 @@ def forward(g, cams, cfg: OracleConfig):
     for cam in cams:
         fp = fp32_path.project32(g.means, g.log_scales, g.quats, cam, cfg.tile_w, cfg.tile_h)
         gx, gy = fp["grid"]
-        keys, vals, offsets, K = binning.emit_instances(fp, gx)
-        skeys, svals = binning.sort_instances(keys, vals)
+        keys, vals, offsets, K, keep = binning.emit_instances(fp, gx, cfg.tile_w, cfg.tile_h)
+        skeys, svals = binning.sort_instances(keys[keep], vals[keep])
         ranges = binning.tile_ranges(skeys, gx * gy)
         vis = np.nonzero(fp["visible"])[0]
         n = g.n
@@ -139,7 +145,7 @@ def forward(g, cams, cfg: OracleConfig):
         views.append(OracleView(fp, keys, vals, offsets, K, skeys, svals, ranges, vis,
                                 splats, out,
                                 dict(mean2d=mean2d, conic=conic, opacity=opac, rgb=rgb,
-                                     rgb_clamped=np.zeros((n, 3), bool))))
+                                     rgb_clamped=np.zeros((n, 3), bool)), keep))
         views[-1].values64["rgb_clamped"][vis] = sp["rgb_clamped"].numpy()
     return views, M, minfo
 
