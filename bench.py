@@ -219,12 +219,25 @@ def run_ours(args):
         ms = float(t.item())
     stage_ms = {k: statistics.mean(e[k][0].elapsed_time(e[k][1]) for e in evs) for k in stage_names}
 
-    # counts of this workload (one extra counted step, outside the timed region)
+    # counts of this workload (extra counted steps, outside the timed region):
+    # the method's fragments over its own tile lists (whole 3-sigma
+    # rectangles, as the 3DGS rasteriser bins), and what our kernels execute
+    # over the filtered lists
     step(count=True)
     torch.cuda.synchronize()
-    counts = rast.frag_count.cpu().tolist()
+    counts_exec = rast.frag_count.cpu().tolist()
     bwd_counts = rast.bwd_count.cpu().tolist()
+    K_kept = int(rast.num_sorted.item())
+    rect = Rasterizer(dev)
+    rect.forward(params, cams, RasterConfig(bin_mode=abi.MG_BIN_RECT), check=True,
+                 count_fragments=True)
+    torch.cuda.synchronize()
+    counts = rect.frag_count.cpu().tolist()
+    del rect
     flops_fwd, flops_bwd = render_flops(counts)
+    # executed by the backward: every (warp, splat) iteration evaluates 64 alphas
+    flops_bwd_exec = (bwd_counts[0] * 64 * FLOPS_ALPHA + counts[3] * FLOPS_BWD_MASKED +
+                      counts[2] * FLOPS_BWD_UNMASKED)
     K = int(rast.num_instances.item())
     so = rast.splat_outputs()
     visible = int((so["radius"] > 0).sum().item())
@@ -279,7 +292,14 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                 "traffic": _profiled_traffic(dom),
-                "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)"}
+                "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)",
+                "flops_basis": "fragments of the 3-sigma rectangle tile lists up to each "
+                               "pixel's stop (the method's walk)"}
+        if dom == "render_bwd":
+            ex = flops_bwd_exec / (stage_ms[dom] * 1e-3) / 1e12
+            roof["executed"] = {"achieved": ex, "frac": ex / fp32_peak_tflops,
+                                "basis": "alphas our kernel evaluates (warp iterations x 64) "
+                                         "+ masked and blended fragment work"}
     else:
         bytes_per = {"sort": K * 152, "preprocess": g.n * 244 + visible * 60,
                      "preprocess_bwd": g.n * (244 + 244) + visible * 48}[dom]
@@ -296,8 +316,11 @@ def run_ours(args):
         "data": "synthetic (seeded cluster-mixture scene standing in for Mip-NeRF360-scale captures)",
         "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W, "height": H, "views": 1,
                    "tile": "16x16", "sh_degree": 3, "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"replicas x{ws}", "instances_K": K, "fragments": {"walked": counts[0], "walked_unmasked": counts[1],
-                                                  "blended": counts[2], "masked_above_floor": counts[3]},
+                   "parallelism": f"replicas x{ws}", "instances_K": K,
+                   "instances_kept": K_kept,
+                   "fragments": {"walked": counts[0], "walked_unmasked": counts[1],
+                                 "blended": counts[2], "masked_above_floor": counts[3],
+                                 "walked_filtered_lists": counts_exec[0]},
                    "render_gflop": {"fwd": flops_fwd / 1e9, "bwd": flops_bwd / 1e9},
                    "bwd_iterations": dict(zip(("list", "masked", "contrib_unmasked",
                                                "contrib_masked", "contrib_lanes", "batches"),

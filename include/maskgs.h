@@ -87,6 +87,11 @@ typedef enum {
 enum { MG_MASK_GUMBEL = 0, MG_MASK_ALL_ONES = 1, MG_MASK_GIVEN = 2, MG_MASK_STE = 3 };
 enum { MG_APPLY_RASTER = 0, MG_APPLY_OPACITY = 1 };
 enum { MG_MASK_LOSS_L2 = 0, MG_MASK_LOSS_L1 = 1 };
+/* Tile lists (mg_raster_cfg.bin_mode): MG_BIN_FILTERED drops the (Gaussian,
+ * tile) pairs of the 3-sigma rectangle where the Gaussian stays under the
+ * alpha floor at every pixel (no result changes; shorter lists); MG_BIN_RECT
+ * keeps the whole rectangle, as the 3DGS rasteriser bins. */
+enum { MG_BIN_FILTERED = 0, MG_BIN_RECT = 1 };
 enum { MG_DTYPE_F32 = 0, MG_DTYPE_BF16 = 1, MG_DTYPE_F16 = 2 };
 enum { MG_MAX_VIEWS = 64, MG_RECORD_FLOATS = 12, MG_GRAD2D_FLOATS = 12 };
 
@@ -162,7 +167,7 @@ typedef struct {
     float lambda_m;          /* weight of L_m in L = L_render + lambda_m L_m (Eq. 8); 0 = off */
     int32_t mask_loss;       /* MG_MASK_LOSS_* */
     float ste_logit;         /* MG_MASK_STE threshold on l_0 - l_1 (FP32 comparison) */
-    int32_t reserved;        /* 0 */
+    int32_t bin_mode;        /* MG_BIN_* */
 } mg_raster_cfg;
 
 /* Per-view preprocess outputs (R = sum_v gaussian_count_v records):
@@ -174,10 +179,12 @@ typedef struct {
  *     (1 if o < 1/255: the splat never reaches the floor); r, g, b; depth tz.
  *   tiles_touched[R] u32 (0 = culled), radius[R] i32 (pixels, 0 = culled),
  *   clamp[R] u8 (bit c: colour channel c was clamped at 0),
- *   tile_rect[R][2] u32 of a visible record: the global id of the first
- *   (top-left) tile of its rectangle, and w | gx << 16 (rectangle width and
- *   the view's tiles per row); tile m of the rectangle (row-major) is
- *   first + (m / w) gx + m % w.
+ *   bin_record[R][12] (48 bytes, 16-byte aligned) of a visible record, for
+ *   the binning: FP32 px, py, a, b, c (the 2D covariance [[a, b], [b, c]]),
+ *   11.1 det, b / a, b / c (decision-path values), then u32 x0 | y0 << 16
+ *   (first tile column and row of the rectangle), w (its width), the global
+ *   id of its first tile, and the view's tiles per row gx; tile m of the
+ *   rectangle (row-major) is first + (m / w) gx + m % w.
  *   With MG_APPLY_OPACITY the stored opacity is M o (+0 for a masked splat,
  *   e_min = 1).
  * Per-Gaussian (n):
@@ -192,7 +199,7 @@ typedef struct {
     uint32_t *tiles_touched;
     int32_t *radius;
     uint8_t *clamp;
-    uint32_t *tile_rect;
+    float *bin_record;
     uint8_t *mask;
     float *mask_soft;
     uint32_t *mask_count;
@@ -239,7 +246,11 @@ size_t mg_depth_order_workspace_bytes(int64_t n_records);
  * position i, offsets[i] = sum_{j<i} tiles_touched[order[j]] (u32) and the
  * total K into *d_num_instances (device u64); then, for every visible record
  * r = order[i] and every tile of its rectangle (row-major), the key = global
- * tile id (u32) and the value r at offsets[i] + k.  Instances beyond `capacity` are not written and raise
+ * tile id (u32) and the value r at offsets[i] + k -- or, with bin_mode
+ * MG_BIN_FILTERED, the key 0xFFFFFFFF when the record's Gaussian stays under
+ * the alpha floor at every pixel of that tile (its quadratic form above
+ * 2 ln 255 at every pixel centre, tested in correctly rounded FP32 from
+ * bin_record): such a pair is a no-op, and mg_sort drops it.  Instances beyond `capacity` are not written and raise
  * MG_ERR_CAPACITY with `required` = K.  workspace: device scratch of
  * mg_bin_workspace_bytes(R) bytes, any content. */
 mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
@@ -271,21 +282,25 @@ mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views, int32_t 
 /* ---- 3. sort + tile ranges (Sec. 3.1) -------------------------------------- */
 /* Stable LSD radix sort (8-bit digits, single-pass "onesweep" passes with
  * decoupled look-back) of the first *d_num_instances (tile id, value) pairs by
- * the low key_bits bits of the tile id (mg_tile_bits), then ranges[t] =
- * [start, end) of the instances of global tile t (n_tiles_total = sum of all
- * views' tiles).  With the instances emitted in depth order (mg_depth_order,
- * then mg_bin), each tile's list comes out ordered by (depth, record index).
- * The sorted pairs end in (keys, vals) when *result_in_alt (host int) is set
- * to 0, else in (keys_alt, vals_alt); it is known on the host from key_bits
- * alone.  When *d_num_instances exceeds capacity (mg_bin raised
- * MG_ERR_CAPACITY) nothing is sorted and every range is empty.  workspace:
- * mg_sort_workspace_bytes(capacity, key_bits) bytes, any content.  key_bits:
- * 1..32 with n_tiles_total <= 2^key_bits; capacity < 2^30. */
+ * the low key_bits bits of the tile id (mg_tile_bits); pairs whose key is
+ * 0xFFFFFFFF (filtered by mg_bin) are dropped in the first pass, and the
+ * number kept is written to *d_num_sorted (device u64, nullable).  Then
+ * ranges[t] = [start, end) of the kept instances of global tile t
+ * (n_tiles_total = sum of all views' tiles).  With the instances emitted in
+ * depth order (mg_depth_order, then mg_bin), each tile's list comes out
+ * ordered by (depth, record index) -- the order a full sort of 64-bit
+ * (tile, depth) keys of record-ordered instances gives.  The sorted pairs end
+ * in (keys, vals) when *result_in_alt (host int) is set to 0, else in
+ * (keys_alt, vals_alt); it is known on the host from key_bits alone.  When
+ * *d_num_instances exceeds capacity (mg_bin raised MG_ERR_CAPACITY) nothing is
+ * sorted and every range is empty.  workspace: mg_sort_workspace_bytes(
+ * capacity, key_bits) bytes, any content.  key_bits: 1..32 with
+ * n_tiles_total <= 2^key_bits; capacity < 2^30. */
 mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                   const uint64_t *d_num_instances, uint64_t capacity, int32_t key_bits,
                   uint32_t *ranges, int64_t n_tiles_total, void *workspace,
-                  size_t workspace_bytes, int32_t *result_in_alt, mg_status_word *d_status,
-                  mg_stream_t stream);
+                  size_t workspace_bytes, int32_t *result_in_alt, uint64_t *d_num_sorted,
+                  mg_status_word *d_status, mg_stream_t stream);
 size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);
 /* Bits of a global tile id for a set of views: ceil(log2(n_tiles_total)), >= 1. */
 int32_t mg_tile_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);

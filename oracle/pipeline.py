@@ -46,6 +46,7 @@ class OracleConfig:
     lambda_m: float = 0.0       # weight of the mask loss, Eq. 8
     mask_loss: int = LOSS_L2    # Eq. 7 (squared mean) or the L1 form of Appendix C
     ste_logit: float = 0.0      # MASK_STE threshold on l_0 - l_1 (FP32)
+    bin_mode: int = 0           # 0: tile-filtered lists; 1: whole 3-sigma rectangles
 
 
 @dataclass
@@ -120,6 +121,8 @@ def forward(g, cams, cfg: OracleConfig):
         fp = fp32_path.project32(g.means, g.log_scales, g.quats, cam, cfg.tile_w, cfg.tile_h)
         gx, gy = fp["grid"]
         keys, vals, offsets, K, keep = binning.emit_instances(fp, gx, cfg.tile_w, cfg.tile_h)
+        if cfg.bin_mode == 1:
+            keep = np.ones_like(keep)
         skeys, svals = binning.sort_instances(keys[keep], vals[keep])
         ranges = binning.tile_ranges(skeys, gx * gy)
         vis = np.nonzero(fp["visible"])[0]

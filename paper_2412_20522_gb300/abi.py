@@ -16,6 +16,7 @@ MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_CAPACITY, MG_ERR_TIMEOUT, MG_ERR_
 MG_MASK_GUMBEL, MG_MASK_ALL_ONES, MG_MASK_GIVEN, MG_MASK_STE = 0, 1, 2, 3
 MG_APPLY_RASTER, MG_APPLY_OPACITY = 0, 1
 MG_MASK_LOSS_L2, MG_MASK_LOSS_L1 = 0, 1
+MG_BIN_FILTERED, MG_BIN_RECT = 0, 1
 MG_DTYPE_F32, MG_DTYPE_BF16, MG_DTYPE_F16 = 0, 1, 2
 MG_MAX_VIEWS = 64
 MG_RECORD_FLOATS = 12
@@ -63,12 +64,12 @@ class mg_raster_cfg(C.Structure):
                 ("tau", C.c_float), ("seed", C.c_uint64), ("iteration", C.c_uint64),
                 ("mask_mode", C.c_int32), ("mask_apply", C.c_int32), ("given_mask", C.c_void_p),
                 ("lambda_m", C.c_float), ("mask_loss", C.c_int32), ("ste_logit", C.c_float),
-                ("reserved", C.c_int32)]
+                ("bin_mode", C.c_int32)]
 
 
 class mg_splats(C.Structure):
     _fields_ = [("record", C.c_void_p), ("tiles_touched", C.c_void_p), ("radius", C.c_void_p),
-                ("clamp", C.c_void_p), ("tile_rect", C.c_void_p), ("mask", C.c_void_p),
+                ("clamp", C.c_void_p), ("bin_record", C.c_void_p), ("mask", C.c_void_p),
                 ("mask_soft", C.c_void_p), ("mask_count", C.c_void_p)]
 
 
@@ -115,7 +116,7 @@ def load(build_if_missing: bool = True):
                                 vp, vp, vp, C.c_uint64, vp, vp, vp]),
         "mg_bin_workspace_bytes": (C.c_size_t, [C.c_int64]),
         "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, vp, C.c_int64, vp,
-                         C.c_size_t, _P(C.c_int32), vp, vp]),
+                         C.c_size_t, _P(C.c_int32), vp, vp, vp]),
         "mg_sort_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int32]),
         "mg_tile_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_total_tiles": (C.c_int64, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
@@ -208,12 +209,12 @@ def mg_bin_workspace_bytes(n_records) -> int:
 
 
 def mg_sort(keys, vals, keys_alt, vals_alt, d_num_instances, capacity, key_bits, ranges,
-            n_tiles_total, workspace, workspace_bytes, d_status, stream) -> int:
+            n_tiles_total, workspace, workspace_bytes, d_num_sorted, d_status, stream) -> int:
     alt = C.c_int32(0)
     _check("mg_sort", load().mg_sort(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt),
                                      ptr(d_num_instances), capacity, key_bits, ptr(ranges),
                                      n_tiles_total, ptr(workspace), workspace_bytes,
-                                     C.byref(alt), ptr(d_status), stream))
+                                     C.byref(alt), ptr(d_num_sorted), ptr(d_status), stream))
     return int(alt.value)
 
 

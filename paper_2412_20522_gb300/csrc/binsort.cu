@@ -109,18 +109,22 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 // finds the position owning its first slot by a 32-ary search of the offsets
 // (non-decreasing; the owner is the last position whose offset is <= the
 // slot), then walks positions 32 at a time: each lane holds one position's
-// offset, record and tile rectangle, and every 32 consecutive slots find
+// offset, record and binning record, and every 32 consecutive slots find
 // their owner lane by a binary search over the lanes (shuffles) and are
-// written fully coalesced.  Slot m of a rectangle is tile first +
-// (m / w) gx + m % w (row-major), the quotient through an FP32 reciprocal
-// corrected to the exact integer.
+// written fully coalesced.  Slot m of a rectangle is tile (x0 + m % w,
+// y0 + m / w), the quotient through an FP32 reciprocal corrected to the
+// exact integer.  A slot whose tile the Gaussian cannot reach above the
+// alpha floor (bin_tile_hit) gets the key kDroppedKey, which the tile sort
+// drops.
 constexpr int kDupChunk = 1024;
+constexpr uint32_t kDroppedKey = 0xFFFFFFFFu;
 
 __global__ void __launch_bounds__(256)
-duplicate_kernel(const uint2 *__restrict__ tile_rect, const uint32_t *__restrict__ tiles,
+duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restrict__ tiles,
                  const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
                  int64_t n_records, const uint64_t *__restrict__ d_num_instances,
-                 uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t capacity) {
+                 uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t capacity,
+                 int tile_w, int tile_h, bool filter) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -149,16 +153,21 @@ duplicate_kernel(const uint2 *__restrict__ tile_rect, const uint32_t *__restrict
     uint64_t s = s0;
     for (int64_t i = lo; s < s1; i += 32) {
         const int64_t ip = i + lane;
-        uint32_t off = 0xFFFFFFFFu, nt = 0, r = 0, first = 0, w = 1, gx = 1;
+        uint32_t off = 0xFFFFFFFFu, nt = 0, r = 0, xy0 = 0, w = 1, first = 0, gx = 1;
+        float4 b0 = make_float4(0.f, 0.f, 1.f, 0.f), b1 = make_float4(1.f, 0.f, 0.f, 0.f);
         if (ip < n_records) {
             off = offsets[ip];
             r = order ? order[ip] : (uint32_t)ip;
             nt = tiles[r];
             if (nt != 0) {
-                const uint2 rc = tile_rect[r];
-                first = rc.x;
-                w = rc.y & 0xFFFFu;
-                gx = rc.y >> 16;
+                const float4 *br = bin_record + 3 * (int64_t)r;
+                b0 = br[0];
+                b1 = br[1];
+                const uint4 u = reinterpret_cast<const uint4 *>(br)[2];
+                xy0 = u.x;
+                w = u.y;
+                first = u.z;
+                gx = u.w;
             }
         }
         const float rw = 1.0f / (float)w;
@@ -182,8 +191,15 @@ duplicate_kernel(const uint2 *__restrict__ tile_rect, const uint32_t *__restrict
             int32_t rem = (int32_t)(m - q * wl);
             if (rem < 0) { --q; rem += (int32_t)wl; }
             else if (rem >= (int32_t)wl) { ++q; rem -= (int32_t)wl; }
-            const uint32_t key = __shfl_sync(FULL, first, L) + q * __shfl_sync(FULL, gx, L) +
-                                 (uint32_t)rem;
+            const uint32_t xy = __shfl_sync(FULL, xy0, L);
+            const bool hit = !filter || bin_tile_hit(
+                __shfl_sync(FULL, b0.x, L), __shfl_sync(FULL, b0.y, L), __shfl_sync(FULL, b0.z, L),
+                __shfl_sync(FULL, b0.w, L), __shfl_sync(FULL, b1.x, L), __shfl_sync(FULL, b1.y, L),
+                __shfl_sync(FULL, b1.z, L), __shfl_sync(FULL, b1.w, L),
+                (int)(xy & 0xFFFFu) + rem, (int)(xy >> 16) + (int)q, tile_w, tile_h);
+            const uint32_t fl = __shfl_sync(FULL, first, L);     // every lane shuffles
+            const uint32_t gl = __shfl_sync(FULL, gx, L);
+            const uint32_t key = hit ? fl + q * gl + (uint32_t)rem : kDroppedKey;
             const uint32_t rr = __shfl_sync(FULL, r, L);
             if (p < gend) {
                 keys[p] = key;
@@ -206,6 +222,7 @@ __device__ __forceinline__ int64_t sort_count(const uint64_t *d_n, uint64_t capa
 
 struct SortWS {
     uint64_t n;                        // element count for sorts whose count is host-known
+    uint64_t n_kept;                   // elements kept (all but dropped keys), set per sort
     uint32_t hist[kMaxPasses][256];    // digit counts, then exclusive offsets
     uint32_t counter[kMaxPasses];
     uint32_t pad[6];
@@ -218,7 +235,7 @@ struct SortWS {
 template <typename K>
 __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t *d_n,
                                       uint64_t capacity, int begin_bit, int passes, SortWS *ws,
-                                      int64_t max_parts) {
+                                      int64_t max_parts, bool drop) {
     __shared__ uint32_t h[kMaxPasses][256];
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -234,11 +251,13 @@ __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t
             const uint32_t e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
+                if (drop && e[u] == kDroppedKey) continue;
                 const uint64_t k = (uint64_t)e[u] >> begin_bit;
                 for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
             }
         }
         for (int64_t i = (n4 << 2) + t; i < n; i += nt) {
+            if (drop && (uint32_t)keys[i] == kDroppedKey) continue;
             const uint64_t k = (uint64_t)keys[i] >> begin_bit;
             for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
         }
@@ -267,9 +286,10 @@ __global__ void sort_offsets_kernel(SortWS *ws) {
     uint64_t tot;
     const uint64_t e = block_exclusive_scan_u64(c, sm_warp, tot);
     ws->hist[p][threadIdx.x] = (uint32_t)e;
+    if (p == 0 && threadIdx.x == 0) ws->n_kept = tot;      // elements the sort keeps
 }
 
-template <typename K>
+template <typename K, bool DROP>
 __global__ void __launch_bounds__(kSortThreads, 4)
 onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint64_t *d_n,
@@ -310,7 +330,8 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
             const bool valid = idx < n;
             k[i] = valid ? keys_in[idx] : (K)0;
             val[i] = valid ? vals_in[idx] : 0u;
-            dig[i] = valid ? (int)(((uint64_t)k[i] >> shift) & 0xFF) : 256;
+            const bool kept = valid && !(DROP && (uint32_t)k[i] == kDroppedKey);
+            dig[i] = kept ? (int)(((uint64_t)k[i] >> shift) & 0xFF) : 256;
         }
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
@@ -363,7 +384,10 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
             }
         }
         __syncthreads();
-        const int cnt = (int)(n - part * kSortPart < kSortPart ? n - part * kSortPart : kSortPart);
+        // kept elements of the partition: the block total of the digit counts
+        const int cnt = DROP ? (int)sm_warp[32]
+                             : (int)(n - part * kSortPart < kSortPart ? n - part * kSortPart
+                                                                      : kSortPart);
         for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
             const K kk = sk[j];
             const int64_t dst = gbase[((uint64_t)kk >> shift) & 0xFF] + j;
@@ -431,10 +455,13 @@ static size_t sort_ws_bytes(uint64_t capacity) {
 
 // Enqueue a radix sort of the first *d_n pairs by key bits [begin_bit,
 // begin_bit + 8 passes); tells whether the result is in the alt buffers.
+// With `drop`, elements whose key is kDroppedKey leave in the first pass; the
+// count kept is ws->n_kept (device), the count the later passes use.
 template <typename K>
 static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
                             const uint64_t *d_n, uint64_t capacity, int begin_bit, int passes,
-                            SortWS *ws, mg_status_word *st, cudaStream_t s, bool *in_alt) {
+                            bool drop, SortWS *ws, mg_status_word *st, cudaStream_t s,
+                            bool *in_alt) {
     *in_alt = (passes & 1) != 0;
     if (cudaMemsetAsync(&ws->hist[0][0], 0, sizeof(ws->hist) + sizeof(ws->counter), s) !=
         cudaSuccess)
@@ -445,17 +472,25 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     const int64_t hblocks = (int64_t)((capacity + 4095) / 4096);
     const int64_t hcap = (int64_t)sms * 2;
     sort_histogram_kernel<K><<<(unsigned)(hblocks < hcap ? (hblocks > 0 ? hblocks : 1) : hcap),
-                               512, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws, max_parts);
+                               512, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws, max_parts,
+                                            drop);
     sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<K>, kSortThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<K, false>, kSortThreads,
+                                                  0);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = (int64_t)sms * per_sm < max_parts ? (int64_t)sms * per_sm : max_parts;
     K *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     for (int p = 0; p < passes; ++p) {
-        onesweep_kernel<K><<<(unsigned)grid, kSortThreads, 0, s>>>(
-            kin, vin, kout, vout, d_n, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
+        // after a dropping first pass the later ones sort the kept elements
+        const uint64_t *np_ = (drop && p > 0) ? &ws->n_kept : d_n;
+        if (drop && p == 0)
+            onesweep_kernel<K, true><<<(unsigned)grid, kSortThreads, 0, s>>>(
+                kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
+        else
+            onesweep_kernel<K, false><<<(unsigned)grid, kSortThreads, 0, s>>>(
+                kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
         K *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
@@ -491,8 +526,8 @@ extern "C" mg_status mg_depth_order(const mg_splats *splats, const mg_view *view
                                                       keys, order, &ws->n);
     bool in_alt = false;
     // 4 passes (an even number): the result is back in (keys, order)
-    st = radix_sort<uint32_t>(keys, order, keys_alt, order_alt, &ws->n, (uint64_t)R, 0, 4, ws,
-                              d_status, s, &in_alt);
+    st = radix_sort<uint32_t>(keys, order, keys_alt, order_alt, &ws->n, (uint64_t)R, 0, 4, false,
+                              ws, d_status, s, &in_alt);
     if (st != MG_OK) return st;
     return mg_host::launch_status();
 }
@@ -512,10 +547,12 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
                             uint32_t *keys, uint32_t *vals, uint64_t capacity,
                             uint64_t *d_num_instances, void *workspace, size_t workspace_bytes,
                             mg_status_word *d_status, mg_stream_t stream) {
-    if (splats == nullptr || !splats->tile_rect || !splats->tiles_touched || !offsets ||
+    if (splats == nullptr || !splats->bin_record || !splats->tiles_touched || !offsets ||
         !d_num_instances || !workspace)
         return MG_ERR_INVALID_ARG;
     if (capacity > 0 && (!keys || !vals)) return MG_ERR_INVALID_ARG;
+    if (cfg == nullptr || (cfg->bin_mode != MG_BIN_FILTERED && cfg->bin_mode != MG_BIN_RECT))
+        return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
     ViewTable vt;
     mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
@@ -539,8 +576,9 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
                                                          d_status);
     if (capacity > 0)
         duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
-            reinterpret_cast<const uint2 *>(splats->tile_rect), splats->tiles_touched, order,
-            offsets, R, d_num_instances, keys, vals, capacity);
+            reinterpret_cast<const float4 *>(splats->bin_record), splats->tiles_touched, order,
+            offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
+            cfg->bin_mode == MG_BIN_FILTERED);
     return mg_host::launch_status();
 }
 
@@ -548,15 +586,16 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
                              uint32_t *vals_alt, const uint64_t *d_num_instances,
                              uint64_t capacity, int32_t key_bits, uint32_t *ranges,
                              int64_t n_tiles_total, void *workspace, size_t workspace_bytes,
-                             int32_t *result_in_alt, mg_status_word *d_status,
-                             mg_stream_t stream) {
+                             int32_t *result_in_alt, uint64_t *d_num_sorted,
+                             mg_status_word *d_status, mg_stream_t stream) {
     if (!keys || !vals || !keys_alt || !vals_alt || !d_num_instances || !ranges || !workspace ||
         !result_in_alt || key_bits < 1 || key_bits > 32 || n_tiles_total <= 0)
         return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
     if (workspace_bytes < mg_sort_workspace_bytes(capacity, key_bits)) return MG_ERR_INVALID_ARG;
     if ((n_tiles_total >> 32) != 0 || (key_bits < 32 && (n_tiles_total >> key_bits) > 1) ||
-        (key_bits < 32 && (n_tiles_total > (int64_t(1) << key_bits))))
+        (key_bits < 32 && (n_tiles_total > (int64_t(1) << key_bits))) ||
+        n_tiles_total >= (int64_t)kDroppedKey)
         return MG_ERR_INVALID_ARG;
     const int passes = (key_bits + 7) / 8;
     cudaStream_t s = (cudaStream_t)stream;
@@ -565,14 +604,19 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
         cudaSuccess)
         return MG_ERR_CUDA;
     bool in_alt = false;
+    // filtered instances (key kDroppedKey) leave in the first pass
     mg_status st = radix_sort<uint32_t>(keys, vals, keys_alt, vals_alt, d_num_instances, capacity,
-                                        0, passes, ws, d_status, s, &in_alt);
+                                        0, passes, true, ws, d_status, s, &in_alt);
     if (st != MG_OK) return st;
     *result_in_alt = in_alt ? 1 : 0;
     if (capacity == 0) return mg_host::launch_status();
+    if (d_num_sorted != nullptr &&
+        cudaMemcpyAsync(d_num_sorted, &ws->n_kept, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+        return MG_ERR_CUDA;
     const int64_t rblocks = (int64_t)((capacity + 1023) / 1024);
     ranges_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), 256, 0, s>>>(
-        in_alt ? keys_alt : keys, d_num_instances, capacity, ranges, n_tiles_total);
+        in_alt ? keys_alt : keys, &ws->n_kept, capacity, ranges, n_tiles_total);
     return mg_host::launch_status();
 }
 
@@ -623,10 +667,12 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
                                     const uint32_t *order, uint32_t *offsets, uint32_t *keys,
                                     uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,
                                     mg_status_word *d_status, mg_stream_t stream) {
-    if (splats == nullptr || !splats->tile_rect || !splats->tiles_touched || !offsets ||
+    if (splats == nullptr || !splats->bin_record || !splats->tiles_touched || !offsets ||
         !d_num_instances)
         return MG_ERR_INVALID_ARG;
     if (capacity > 0 && (!keys || !vals)) return MG_ERR_INVALID_ARG;
+    if (cfg == nullptr || (cfg->bin_mode != MG_BIN_FILTERED && cfg->bin_mode != MG_BIN_RECT))
+        return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
     ViewTable vt;
     mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
@@ -655,7 +701,8 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
                                                          d_status);
     if (capacity > 0)
         duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
-            reinterpret_cast<const uint2 *>(splats->tile_rect), splats->tiles_touched, order,
-            offsets, R, d_num_instances, keys, vals, capacity);
+            reinterpret_cast<const float4 *>(splats->bin_record), splats->tiles_touched, order,
+            offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
+            cfg->bin_mode == MG_BIN_FILTERED);
     return mg_host::launch_status();
 }

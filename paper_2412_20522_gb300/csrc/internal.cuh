@@ -283,6 +283,47 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     dx[15] = -kSH3a * 3.0f * (xx - yy);       dy[15] = kSH3a * 6.0f * x * y;           dz[15] = 0.0f;
 }
 
+// Tile filter of the binning (Sec. 3.1: only Gaussians whose alpha reaches
+// the floor take part): drop a Gaussian from a tile of its rectangle when its
+// quadratic form q = d^T Sigma_bar^-1 d exceeds 2 ln 255 at every pixel centre
+// of the tile -- there alpha = o exp(-q/2) < 1/255 for any opacity o <= 1,
+// so the pair is a no-op and dropping it changes no result.  The minimum of
+// N = c dx^2 - 2 b dx dy + a dy^2 = det q over the box of pixel centres is 0
+// if the mean is inside, else the least of the four edges' minima at their
+// clamped stationary points; the pair is kept if N <= 11.1 det + 1e-4 (sum
+// of |terms|) (11.1 > 2 ln 255; the slack covers N's rounding).  Every
+// operation is a correctly rounded FP32 one, in a fixed order, so the
+// decision is reproducible bit for bit.
+constexpr float kBinThreshold = 11.1f;
+constexpr float kBinRelSlack = 1e-4f;
+
+__device__ __forceinline__ bool bin_edge_hit(float t1, float t2, float t3, float tdet) {
+    const float t22 = ad(t2, t2);
+    const float N = ad(sb(t1, t22), t3);
+    const float bnd = ad(ad(t1, fabsf(t22)), t3);
+    return N <= ad(tdet, ml(kBinRelSlack, bnd));
+}
+
+__device__ __forceinline__ bool bin_tile_hit(float px, float py, float a, float b, float c,
+                                             float tdet, float rba, float rbc, int tx, int ty,
+                                             int tw, int th) {
+    const float X0 = ad((float)(tx * tw), 0.5f), Y0 = ad((float)(ty * th), 0.5f);
+    const float X1 = ad(X0, (float)(tw - 1)), Y1 = ad(Y0, (float)(th - 1));
+    const float dx0 = sb(X0, px), dx1 = sb(X1, px), dy0 = sb(Y0, py), dy1 = sb(Y1, py);
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
+    bool hit = false;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dxe = e ? dx1 : dx0;
+        const float dyc = fminf(fmaxf(ml(rba, dxe), dy0), dy1);
+        hit |= bin_edge_hit(ml(c, ml(dxe, dxe)), ml(ml(b, dxe), dyc), ml(a, ml(dyc, dyc)), tdet);
+        const float dye = e ? dy1 : dy0;
+        const float dxc = fminf(fmaxf(ml(rbc, dye), dx0), dx1);
+        hit |= bin_edge_hit(ml(c, ml(dxc, dxc)), ml(ml(b, dxc), dye), ml(a, ml(dye, dye)), tdet);
+    }
+    return hit;
+}
+
 __host__ __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int64_t t) {
     int v = 0;
     while (v + 1 < vt.n_views && vt.tile_off[v + 1] <= t) ++v;

@@ -268,9 +268,14 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
             continue;
         }
         out.tiles_touched[r] = (uint32_t)((S.x1 - S.x0 + 1) * (S.y1 - S.y0 + 1));
-        reinterpret_cast<uint2 *>(out.tile_rect)[r] =
-            make_uint2((uint32_t)(vt.tile_off[v] + (int64_t)S.y0 * vt.gx[v] + S.x0),
-                       (uint32_t)(S.x1 - S.x0 + 1) | ((uint32_t)vt.gx[v] << 16));
+        // binning record: tile-filter inputs (decision path) and the rectangle
+        float4 *br = reinterpret_cast<float4 *>(out.bin_record) + 3 * r;
+        br[0] = make_float4(S.px, S.py, S.a, S.b);
+        br[1] = make_float4(S.c, ml(kBinThreshold, S.det), dv(S.b, S.a), dv(S.b, S.c));
+        reinterpret_cast<uint4 *>(br)[2] =
+            make_uint4((uint32_t)S.x0 | ((uint32_t)S.y0 << 16), (uint32_t)(S.x1 - S.x0 + 1),
+                       (uint32_t)(vt.tile_off[v] + (int64_t)S.y0 * vt.gx[v] + S.x0),
+                       (uint32_t)vt.gx[v]);
         out.radius[r] = (int32_t)S.rf;
         float ux, uy, l1, l2;
         eigen2(S, ux, uy, l1, l2);
@@ -747,11 +752,11 @@ extern "C" mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, 
         return MG_ERR_CUDA;
     if (g->n == 0) return MG_OK;
     if (!out->record || !out->tiles_touched || !out->radius || !out->clamp || !out->mask ||
-        !out->mask_soft || !out->tile_rect || !aligned(out->record, 16) ||
-        !aligned(out->tile_rect, 8))
+        !out->mask_soft || !out->bin_record || !aligned(out->record, 16) ||
+        !aligned(out->bin_record, 16))
         return MG_ERR_INVALID_ARG;
     for (int v = 0; v < n_views; ++v)
-        if (vt.gx[v] >= 65536) return MG_ERR_INVALID_ARG;
+        if (vt.gx[v] >= 65536 || vt.gy[v] >= 65536) return MG_ERR_INVALID_ARG;
     const dim3 grid((unsigned)((g->n + kPreThreads - 1) / kPreThreads));
     switch (g->sh_degree) {
         case 0: launch_preprocess<0>(g->dtype, grid, s, vt, *g, *cfg, *out); break;

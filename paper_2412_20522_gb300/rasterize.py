@@ -32,6 +32,7 @@ class RasterConfig:
     lambda_m: float = 0.0                      # mask-loss weight, Eq. 8
     mask_loss: int = abi.MG_MASK_LOSS_L2       # Eq. 7, or the L1 form
     ste_logit: float = 0.0                     # MG_MASK_STE threshold on l_0 - l_1
+    bin_mode: int = abi.MG_BIN_FILTERED        # or MG_BIN_RECT (whole 3-sigma rectangles)
 
     @staticmethod
     def ste_logit_of(theta: float) -> float:
@@ -54,6 +55,7 @@ class RasterConfig:
         cfg.lambda_m = float(self.lambda_m)
         cfg.mask_loss = int(self.mask_loss)
         cfg.ste_logit = float(self.ste_logit)
+        cfg.bin_mode = int(self.bin_mode)
         return cfg
 
 
@@ -133,6 +135,7 @@ class Rasterizer:
         self.frag_count = torch.zeros(4, dtype=torch.int64, device=self.device)
         self.bwd_count = torch.zeros(6, dtype=torch.int64, device=self.device)
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.num_sorted = torch.zeros(1, dtype=torch.int64, device=self.device)
 
     # -- buffers -------------------------------------------------------------
     def _get(self, name, numel, dtype):
@@ -152,7 +155,7 @@ class Rasterizer:
         s.tiles_touched = self._get("tiles", R, torch.int32).data_ptr()
         s.radius = self._get("radius", R, torch.int32).data_ptr()
         s.clamp = self._get("clamp", R, torch.uint8).data_ptr()
-        s.tile_rect = self._get("tile_rect", 2 * R, torch.int32).data_ptr()
+        s.bin_record = self._get("bin_record", 12 * R, torch.float32).data_ptr()
         s.mask = self._get("mask", n, torch.uint8).data_ptr()
         s.mask_soft = self._get("mask_soft", n, torch.float32).data_ptr()
         return s
@@ -228,7 +231,8 @@ class Rasterizer:
         # instances arrive in depth order: a stable sort by tile id suffices
         alt = abi.mg_sort(self._buf["keys"], self._buf["vals"], self._buf["keys_alt"],
                           self._buf["vals_alt"], self.num_instances, self.capacity, key_bits,
-                          ranges_buf, tiles, sort_ws, sort_ws.numel(), self.status, stream)
+                          ranges_buf, tiles, sort_ws, sort_ws.numel(), self.num_sorted,
+                          self.status, stream)
         ev.end("sort")
         sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
         # longest tile lists first (launch order only)
@@ -338,7 +342,8 @@ class Rasterizer:
                     sorted_vals=s["sorted_vals"], ranges=s["ranges"][:2 * s["tiles"]],
                     final_T=self._buf["final_T"][:s["pix"]],
                     n_contrib=self._buf["n_contrib"][:s["pix"]],
-                    num_instances=self.num_instances, grad2d=self._buf.get("grad2d"))
+                    num_instances=self.num_instances, num_sorted=self.num_sorted,
+                    grad2d=self._buf.get("grad2d"))
 
     def sorted_keys(self):
         s = self._state

@@ -83,7 +83,7 @@ def test_bad_arguments_rejected_on_host(lib):
     assert st == abi.MG_ERR_INVALID_ARG
     alt = C.c_int32(0)
     st = lib.mg_sort(None, None, None, None, None, 0, 20, None, 1, None, 0, C.byref(alt), None,
-                     None)
+                     None, None)
     assert st == abi.MG_ERR_INVALID_ARG
 
 

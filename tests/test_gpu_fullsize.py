@@ -37,8 +37,10 @@ def test_scene_scale_single_view():
     assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order)
     K = int(so["num_instances"].item())
     assert K == v.K
-    keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:K]
-    vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:K]
+    Ks = int(so["num_sorted"].item())
+    assert Ks == v.K_kept
+    keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:Ks]
+    vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:Ks]
     assert np.array_equal(keys.astype(np.uint64), v.sorted_keys >> np.uint64(32))
     assert np.array_equal(vals, v.sorted_vals)
     rng = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
@@ -53,7 +55,7 @@ def test_scene_scale_single_view():
     gn = rast.splat_outputs()["n_contrib"].cpu().numpy().reshape(H, W)
     assert fc[0] == int(gn.sum())
     assert np.array_equal(gn[~straddle], v.out["n_contrib"][~straddle])
-    print(f"K={K} frags(gpu)={fc.tolist()} straddle px={int(straddle.sum())} "
+    print(f"K={K} kept={Ks} frags(gpu)={fc.tolist()} straddle px={int(straddle.sum())} "
           f"over 2e-4: {int((d > 2e-4).sum())} clean max err {d[~straddle].max():.3e}")
     assert not ((d > 2e-4) & ~straddle).any(), d[~straddle].max()
     assert straddle.mean() < 0.02

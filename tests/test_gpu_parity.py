@@ -66,13 +66,15 @@ def _check_discrete(rast, views, M, cams):
     rec = so["record"].cpu().numpy()
     tiles = so["tiles"].cpu().numpy().view(np.uint32)
     radius = so["radius"].cpu().numpy()
-    K_gpu = int(so["num_instances"].item())
+    K_gpu = int(so["num_instances"].item())               # rectangle instances
+    Ks_gpu = int(so["num_sorted"].item())                 # kept by the tile filter
     R0 = 0
     T0 = 0
     K0 = 0
+    Kc = 0
     ranges = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
-    vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:K_gpu]
-    keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:K_gpu]
+    vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:Ks_gpu]
+    keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:Ks_gpu]
     for v, cam in zip(views, cams):
         n = v.fp32["tiles"].shape[0]
         fp = v.fp32
@@ -86,8 +88,9 @@ def _check_discrete(rast, views, M, cams):
         nt = v.ranges.shape[0]
         # instance keys are global tile ids: the oracle's tile of view v plus T0
         otiles = (v.sorted_keys >> np.uint64(32)).astype(np.int64) + T0
-        assert np.array_equal(keys[K0:K0 + v.K].astype(np.int64), otiles), "sorted tiles differ"
-        assert np.array_equal(vals[K0:K0 + v.K], v.sorted_vals.astype(np.uint32) + R0), "sorted values differ"
+        assert np.array_equal(keys[K0:K0 + v.K_kept].astype(np.int64), otiles), "sorted tiles differ"
+        assert np.array_equal(vals[K0:K0 + v.K_kept], v.sorted_vals.astype(np.uint32) + R0), \
+            "sorted values differ"
         gr = ranges[T0:T0 + nt].astype(np.int64)
         orr = v.ranges.astype(np.int64)
         nonempty = orr[:, 1] > orr[:, 0]
@@ -95,8 +98,10 @@ def _check_discrete(rast, views, M, cams):
         assert (gr[~nonempty, 1] == gr[~nonempty, 0]).all()
         R0 += n
         T0 += nt
-        K0 += v.K
-    assert K_gpu == K0
+        K0 += v.K_kept
+        Kc += v.K
+    assert K_gpu == Kc
+    assert Ks_gpu == K0
 
 
 def _check_images(rast, img, views, cams, report):
@@ -170,6 +175,16 @@ def test_tiny_workload(rz):
 def test_tiny_workload_background_and_other_seed(rz):
     g, cams, tgt = scenes.tiny_workload()
     _full_check(rz, g, cams, [tgt], dict(bg=(0.9, 0.4, 0.1), seed=77, iteration=12345678901))
+
+
+def test_whole_rectangle_tile_lists(rz):
+    """bin_mode MG_BIN_RECT: the 3DGS lists (whole 3-sigma rectangles, no tile
+    filter) -- same images and gradients, longer lists."""
+    g, cams, tgt = scenes.tiny_workload()
+    _full_check(rz, g, cams, [tgt], dict(bin_mode=1, bg=(0.3, 0.2, 0.1)))
+    g = scenes.cluster_gaussians(40_000, seed=8)
+    cams = [scenes.ring_camera(0.0, 4.0, 200, 130, 150.0)]
+    _full_check(rz, g, cams, [scenes.target_image(130, 200, seed=2)], dict(bin_mode=1))
 
 
 def test_tile_8x32_and_ragged_frame(rz):
