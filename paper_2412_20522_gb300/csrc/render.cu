@@ -484,36 +484,46 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     for (int k = 0; k < kPix; ++k) ncontrib += (int)on[k];
                     if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) continue;
                     const float4 c = sC[j];
+                    // the mask is uniform over the warp: two straight-line paths
                     float v[10];
 #pragma unroll
                     for (int q = 0; q < 10; ++q) v[q] = 0.0f;
+                    if (masked) {
+                        // M = 0: T and the colour behind are unchanged; only dL/dM
 #pragma unroll
-                    for (int k = 0; k < kPix; ++k) {
-                        if (!on[k]) continue;
-                        const float alpha = f[k].alpha;
-                        const float ma = masked ? 0.0f : alpha;
-                        const float Tj = __fdividef(T[k], 1.0f - ma);
-                        const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
-                                          g2[k] * (c.z - bc2[k]);
-                        v[9] += alpha * Tj * gcb;               // Eq. 6 + Appendix A
-                        if (!masked) {
+                        for (int k = 0; k < kPix; ++k) {
+                            if (!on[k]) continue;
+                            const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
+                                              g2[k] * (c.z - bc2[k]);
+                            v[9] = fmaf(f[k].alpha * T[k], gcb, v[9]);   // Eq. 6 + Appendix A
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < kPix; ++k) {
+                            if (!on[k]) continue;
+                            const float alpha = f[k].alpha;
+                            const float Tj = __fdividef(T[k], 1.0f - alpha);
+                            const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
+                                              g2[k] * (c.z - bc2[k]);
                             const float wt = alpha * Tj;
-                            v[6] += wt * g0[k];
-                            v[7] += wt * g1[k];
-                            v[8] += wt * g2[k];
+                            const float dm = wt * gcb;
+                            v[9] += dm;                                   // Eq. 6 + Appendix A
+                            v[6] = fmaf(wt, g0[k], v[6]);
+                            v[7] = fmaf(wt, g1[k], v[7]);
+                            v[8] = fmaf(wt, g2[k], v[8]);
                             bc0[k] = fmaf(alpha, c.x - bc0[k], bc0[k]);
                             bc1[k] = fmaf(alpha, c.y - bc1[k], bc1[k]);
                             bc2[k] = fmaf(alpha, c.z - bc2[k], bc2[k]);
                             T[k] = Tj;
                             if (f[k].araw < kAlphaMax) {
-                                const float dpow = Tj * gcb * alpha;    // dL/dalpha * alpha
-                                const float pdx = dpow * f[k].dx, pdy = dpow * f[k].dy;
-                                v[0] += dpow;
+                                // dL/dalpha * alpha (0 through the 0.99 clamp)
+                                const float pdx = dm * f[k].dx, pdy = dm * f[k].dy;
+                                v[0] += dm;
                                 v[1] += pdx;
                                 v[2] += pdy;
-                                v[3] += pdx * f[k].dx;
-                                v[4] += pdx * f[k].dy;
-                                v[5] += pdy * f[k].dy;
+                                v[3] = fmaf(pdx, f[k].dx, v[3]);
+                                v[4] = fmaf(pdx, f[k].dy, v[4]);
+                                v[5] = fmaf(pdy, f[k].dy, v[5]);
                             }
                         }
                     }
