@@ -40,22 +40,20 @@ struct Frag {
 // alpha = min(0.99, o 2^e), e = h1 p1^2 + h2 p2^2, p1 = d.u, p2 = d.u_perp,
 // d = pixel centre - mean.  A = (mx, my, ux, uy), B = (h1, h2, +-o, e_min):
 // the sign of B.z is the mask (negative = masked), and e_min (stored by the
-// preprocess, just below log2(1/(255 o))) lets both kernels skip the exp of
-// fragments whose alpha is certainly under the floor; the alpha test itself
-// still decides every other fragment, identically in both kernels.
+// preprocess, just below log2(1/(255 o))) bounds the ellipse the warp-block
+// culling tests; every fragment a warp walks is decided by the alpha test,
+// evaluated identically in both kernels.
 // A thread's two pixels share a column, kRowStep rows apart: the second
 // pixel's offsets follow from the first's (d.y + 4, p1 + 4 uy, p2 + 4 ux).
 constexpr float kRowStep = 4.0f;
 
 __device__ __forceinline__ void frag_finish(const float4 &B, Frag &f) {
     f.e = __fmaf_rn(__fmul_rn(B.x, f.p1), f.p1, __fmul_rn(__fmul_rn(B.y, f.p2), f.p2));
-    f.on = false;
-    if (f.e >= B.w) {
-        f.G = ex2_approx(f.e);
-        f.araw = __fmul_rn(fabsf(B.z), f.G);
-        f.alpha = fminf(kAlphaMax, f.araw);
-        f.on = f.alpha >= kAlphaMin;
-    }
+    // straight-line: the exp unit has room, a branch per pixel costs more
+    f.G = ex2_approx(f.e);
+    f.araw = __fmul_rn(fabsf(B.z), f.G);
+    f.alpha = fminf(kAlphaMax, f.araw);
+    f.on = f.alpha >= kAlphaMin;
 }
 
 __device__ __forceinline__ void frag_alpha_pair(const float4 &A, const float4 &B, float fpx,
