@@ -437,6 +437,14 @@ mg_status mg_read_status(const mg_status_word *d_status, mg_status_word *h_out,
 const char *mg_status_string(int32_t status);
 const char *mg_version(void);
 
+/* Self-test of the bounded device-side waits (the paper has no counterpart):
+ * one thread runs the library's decoupled look-back on a flag that nothing
+ * ever sets; after max_polls polls (0..2^24, each with a short sleep) it gives
+ * up and raises MG_ERR_TIMEOUT with detail 4 in *d_status.  The context stays
+ * usable; read the word with mg_read_status. */
+mg_status mg_selftest_wait_timeout(int32_t max_polls, mg_status_word *d_status,
+                                   mg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,15 +112,17 @@ def log32(x):
 
 
 def exp32(x):
-    """exp(x) for float32 x, input clamped to [-80, 80].
+    """exp(x) for float32 x, input clamped to [-80, 80] (by comparisons, so
+    a NaN stays NaN and the Gaussian is culled downstream).
 
     Cody-Waite reduction x = k ln2 + r, k = rint(x / ln2), |r| <= ln2/2,
     exp(r) by its Taylor series to r^7/7! in Horner form, then scaled by 2^k
     (built exactly from the exponent bits).
     """
     x = np.asarray(x, dtype=np.float32)
-    x = np.minimum(np.maximum(x, f32(-80.0)), f32(80.0))
-    k = np.rint(x * INV_LN2).astype(np.float32)
+    x = np.where(x < f32(-80.0), f32(-80.0), np.where(x > f32(80.0), f32(80.0), x))
+    nan = np.isnan(x)
+    k = np.rint(np.where(nan, f32(0.0), x) * INV_LN2).astype(np.float32)
     r = (x - k * LN2_HI) - k * LN2_LO
     p = INV_FACT[7]
     for j in range(6, -1, -1):
@@ -128,7 +130,7 @@ def exp32(x):
         p = p + INV_FACT[j]
     ki = k.astype(np.int32)
     two_k = ((ki + 127).astype(np.uint32) << u32(23)).view(np.float32)
-    return (p * two_k).astype(np.float32)
+    return np.where(nan, np.float32(np.nan), p * two_k).astype(np.float32)
 
 
 # ---------------------------------------------------------------------------

@@ -87,3 +87,27 @@ const char *mg_status_string(int32_t status) {
 const char *mg_version(void) { return "maskgs 0.1.0 (sm_103a)"; }
 
 }  // extern "C"
+
+// Self-test of the bounded device-side waits: one thread runs the look-back
+// every cross-block wait of the library uses, for partition 1 of a status
+// array whose partition 0 never publishes; after max_polls polls it gives up
+// and raises MG_ERR_TIMEOUT (detail 4) in the status word.
+namespace mg {
+__global__ void selftest_wait_kernel(int max_polls, mg_status_word *st) {
+    __shared__ uint64_t status[2];
+    status[0] = 0;                    // partition 0: nothing ever published
+    status[1] = 0;
+    lookback<uint64_t, 62>(status, 1, 1, st, 4, max_polls);
+}
+}  // namespace mg
+
+extern "C" {
+
+mg_status mg_selftest_wait_timeout(int32_t max_polls, mg_status_word *d_status,
+                                   mg_stream_t stream) {
+    if (d_status == nullptr || max_polls < 0 || max_polls > (1 << 24)) return MG_ERR_INVALID_ARG;
+    mg::selftest_wait_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(max_polls, d_status);
+    return mg_host::launch_status();
+}
+
+}  // extern "C"

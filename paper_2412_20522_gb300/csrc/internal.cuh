@@ -88,7 +88,8 @@ constexpr int kLookbackWindow = 8;
 
 template <typename W, int FLAG_SHIFT>
 __device__ __forceinline__ W lookback(const W *status, int64_t stride, int64_t part,
-                                      mg_status_word *st, int32_t detail) {
+                                      mg_status_word *st, int32_t detail,
+                                      int max_spins = kMaxTimeoutSpins) {
     constexpr W kMask = (W(1) << FLAG_SHIFT) - W(1);
     W excl = 0;
     int64_t q = part - 1;
@@ -101,7 +102,7 @@ __device__ __forceinline__ W lookback(const W *status, int64_t stride, int64_t p
         for (int k = 0; k < kLookbackWindow; ++k) {
             if (q - k < 0) return excl;
             int spins = 0;
-            while ((s[k] >> FLAG_SHIFT) == 0 && spins < kMaxTimeoutSpins) {
+            while ((s[k] >> FLAG_SHIFT) == 0 && spins < max_spins) {
                 __nanosleep(20);
                 s[k] = ld_volatile(status + (q - k) * stride);
                 ++spins;
@@ -169,7 +170,8 @@ __device__ __forceinline__ float log32(float x) {
 }
 
 __device__ __forceinline__ float exp32(float x) {
-    x = fminf(fmaxf(x, -80.0f), 80.0f);
+    // clamp to [-80, 80] by comparisons: a NaN stays NaN (fminf/fmaxf drop it)
+    x = x < -80.0f ? -80.0f : (x > 80.0f ? 80.0f : x);
     const float k = rintf(__fmul_rn(x, 0x1.715476p+0f));
     const float r = __fadd_rn(__fadd_rn(x, -__fmul_rn(k, 0x1.62e4p-1f)), -__fmul_rn(k, 0x1.7f7d1cp-20f));
     float p = 0x1.a01a02p-13f;

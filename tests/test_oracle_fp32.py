@@ -114,3 +114,23 @@ def test_mask_draws_depend_on_seed_and_iteration():
     assert abs(np.corrcoef(a, b)[0, 1]) < 0.03
     assert abs(np.corrcoef(a, c)[0, 1]) < 0.03
     assert (fp.sample_mask(l, 1, 0)[0] == a).all()    # deterministic
+
+
+def test_non_finite_inputs_are_culled():
+    """NaN / inf means, NaN scales, a zero or NaN quaternion: the decision path
+    culls the Gaussian (no tile), the others are untouched."""
+    from paper_2412_20522_gb300 import scenes
+    g, cams, _ = scenes.tiny_workload(500)
+    ref = fp.project32(g.means, g.log_scales, g.quats, cams[0], 16, 16)
+    m, s, q = g.means.copy(), g.log_scales.copy(), g.quats.copy()
+    m[5] = np.nan
+    m[9, 2] = np.inf
+    s[17] = np.nan
+    q[23] = 0.0
+    q[31] = np.nan
+    with np.errstate(invalid="ignore"):
+        out = fp.project32(m, s, q, cams[0], 16, 16)
+    bad = [5, 9, 17, 23, 31]
+    assert (out["tiles"][bad] == 0).all() and (out["radius"][bad] == 0).all()
+    good = np.setdiff1d(np.arange(500), bad)
+    assert np.array_equal(out["tiles"][good], ref["tiles"][good])
