@@ -374,7 +374,9 @@ def run_ours(args):
         "gpu_launches": gpu_launches_per_step * args.steps,
         "clocks": clk,
     }
-    if not args.no_forms:
+    if not args.no_forms and ws == 1:
+        # the single-GPU forms (multi-view graph, storage, scene batch, next
+        # rows); a multi-rank run times the replicated step only
         line["forms"] = run_forms(dev, g, cams, target, ms, W * H)
         line["forms"]["next_rows"] = run_next_rows(dev, g, cams, target, ms, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
