@@ -337,7 +337,8 @@ mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
 /* ---- 5. L1 render loss ------------------------------------------------------ */
 /* For count = sum_v 3 W_v H_v values: dL_dimage[i] = sign(image[i] - target[i])
  * / (3 W_v H_v) of the view holding i (sign(0) = 0), and *loss (device f32)
- * += sum_v mean |image_v - target_v|.  The caller zeroes *loss. */
+ * += sum_v mean |image_v - target_v|.  The caller zeroes *loss.  image, target
+ * and dL_dimage: 16-byte aligned. */
 mg_status mg_l1_loss_grad(const float *image, const float *target, const mg_view *views,
                           int32_t n_views, float *dL_dimage, float *loss,
                           mg_stream_t stream);

@@ -584,6 +584,12 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     }
 }
 
+__device__ __forceinline__ float l1_sign(float d, float inv) {
+    return d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+}
+
+// One view per blockIdx.y; 128-bit loads and stores over the view's aligned
+// body, scalar over its (at most 3 + 3) unaligned ends.
 __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ image,
                                     const float *__restrict__ target, float *__restrict__ grad,
                                     float *loss) {
@@ -592,21 +598,32 @@ __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ imag
     const int64_t o = 3 * vt.pix_off[v];
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
-        float a[4], b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            a[u] = i0 + u < n ? image[o + i0 + u] : 0.0f;
-            b[u] = i0 + u < n ? target[o + i0 + u] : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (i0 + u >= n) break;
-            const float d = a[u] - b[u];
-            grad[o + i0 + u] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
-            acc += fabsf(d);
-        }
+    const int64_t h0 = (4 - (o & 3)) & 3;                                  // to a 16-byte boundary
+    const int64_t head = h0 < n ? h0 : n;
+    const int64_t nb = (n - head) >> 2;                                    // float4 body
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const float4 *a4 = reinterpret_cast<const float4 *>(image + o + head);
+    const float4 *b4 = reinterpret_cast<const float4 *>(target + o + head);
+    float4 *g4 = reinterpret_cast<float4 *>(grad + o + head);
+    for (int64_t q = tid; q < nb; q += nthr) {
+        const float4 a = a4[q], b = b4[q];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        g4[q] = make_float4(l1_sign(d0, inv), l1_sign(d1, inv), l1_sign(d2, inv), l1_sign(d3, inv));
+        acc += (fabsf(d0) + fabsf(d1)) + (fabsf(d2) + fabsf(d3));
+    }
+    // the unaligned head and tail
+    const int64_t tail0 = head + (nb << 2);
+    if (tid < head) {
+        const float d = image[o + tid] - target[o + tid];
+        grad[o + tid] = l1_sign(d, inv);
+        acc += fabsf(d);
+    }
+    if (tid < n - tail0) {
+        const int64_t i = o + tail0 + tid;
+        const float d = image[i] - target[i];
+        grad[i] = l1_sign(d, inv);
+        acc += fabsf(d);
     }
     acc = warp_sum(acc);
     __shared__ float s[32];
@@ -705,6 +722,9 @@ extern "C" mg_status mg_l1_loss_grad(const float *image, const float *target,
                                      const mg_view *views, int32_t n_views, float *dL_dimage,
                                      float *loss, mg_stream_t stream) {
     if (!image || !target || !dL_dimage) return MG_ERR_INVALID_ARG;
+    if (((reinterpret_cast<uintptr_t>(image) | reinterpret_cast<uintptr_t>(target) |
+          reinterpret_cast<uintptr_t>(dL_dimage)) & 15u) != 0)
+        return MG_ERR_INVALID_ARG;
     mg_raster_cfg cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.tile_w = cfg.tile_h = 16;

@@ -124,3 +124,38 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     assert best in autotune.TILE_SHAPES
     assert (tmp_path / "tune.json").exists()
     assert autotune.autotune_tile(p, cams, t, steps=2) == best      # from the cache
+
+
+def test_l1_loss_grad_views_at_every_alignment():
+    """dL/dimage = sign(C - target) / (3 W H) per view, sign(0) = 0, and the
+    summed per-view mean |C - target|, for views whose offsets leave each of
+    the four 16-byte alignments (vector body, scalar head and tail)."""
+    from paper_2412_20522_gb300 import abi
+    from paper_2412_20522_gb300.rasterize import make_views
+    sizes = [(5, 3), (7, 5), (33, 17), (2, 1), (64, 48)]
+    cams = [scenes.look_at_camera((0, 0, -3), (0, 0, 0), w, h, 30.0) for w, h in sizes]
+    n = sum(3 * w * h for w, h in sizes)
+    rng = np.random.default_rng(3)
+    img = rng.random(n).astype(np.float32)
+    tgt = rng.random(n).astype(np.float32)
+    tgt[::7] = img[::7]                                   # exact zeros of the difference
+    views = make_views(cams, [(0, 1)] * len(cams))
+    gi, gt = torch.as_tensor(img).cuda(), torch.as_tensor(tgt).cuda()
+    grad = torch.full((n,), 7.0, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    import ctypes as C
+    abi.mg_l1_loss_grad(gi, gt, views, len(cams), grad, loss, C.c_void_p(stream))
+    torch.cuda.synchronize()
+    exp = np.empty(n, np.float32)
+    o = 0
+    tot = 0.0
+    for w, h in sizes:
+        m = 3 * w * h
+        d = img[o:o + m] - tgt[o:o + m]
+        inv = np.float32(1.0) / np.float32(m)
+        exp[o:o + m] = np.where(d > 0, inv, np.where(d < 0, -inv, np.float32(0.0)))
+        tot += float(np.abs(d.astype(np.float64)).mean())
+        o += m
+    assert np.array_equal(grad.cpu().numpy(), exp)
+    assert float(loss.item()) == pytest.approx(tot, rel=1e-5)
