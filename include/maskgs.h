@@ -295,7 +295,9 @@ mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views, int32_t 
  * *d_num_instances exceeds capacity (mg_bin raised MG_ERR_CAPACITY) nothing is
  * sorted and every range is empty.  workspace: mg_sort_workspace_bytes(
  * capacity, key_bits) bytes, any content.  key_bits: 1..32 with
- * n_tiles_total <= 2^key_bits; capacity < 2^30. */
+ * n_tiles_total <= 2^key_bits; capacity < 2^30.  The first call on a device
+ * (of this or of mg_depth_order) sets the sort kernels' shared-memory limit:
+ * make it outside stream capture. */
 mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                   const uint64_t *d_num_instances, uint64_t capacity, int32_t key_bits,
                   uint32_t *ranges, int64_t n_tiles_total, void *workspace,

@@ -32,7 +32,11 @@
 namespace mg {
 
 constexpr int kScanThreads = 256, kScanItems = 8, kScanPart = kScanThreads * kScanItems;
-constexpr int kSortThreads = 256, kSortItems = 12, kSortPart = kSortThreads * kSortItems;
+// 512 threads x 12 keys: with every partition of a small sort running at
+// once, a partition's look-back ends at the nearest inclusive prefix, which
+// spreads about a window per round trip -- fewer, larger partitions shorten
+// that chain (one digit per thread for the first 256 threads).
+constexpr int kSortThreads = 512, kSortItems = 12, kSortPart = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValMask = (1u << 30) - 1u;
 constexpr int kMaxPasses = 8;
@@ -290,13 +294,16 @@ __global__ void sort_offsets_kernel(SortWS *ws) {
 }
 
 template <typename K, bool DROP>
-__global__ void __launch_bounds__(kSortThreads, 4)
+__global__ void __launch_bounds__(kSortThreads, 2048 / kSortThreads / 2)
 onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint64_t *d_n,
                 uint64_t capacity, int pass, int shift, SortWS *ws, int64_t max_parts,
                 mg_status_word *st) {
-    __shared__ K sk[kSortPart];
-    __shared__ uint32_t sv[kSortPart];
+    // staged keys and values of the partition: dynamic shared memory (above
+    // the 48 KB a kernel may declare statically)
+    extern __shared__ __align__(16) unsigned char sort_stage[];
+    K *sk = reinterpret_cast<K *>(sort_stage);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sort_stage + sizeof(K) * kSortPart);
     __shared__ uint32_t whist[kSortWarps][256];
     __shared__ uint32_t dstart[256];
     __shared__ int64_t gbase[256];
@@ -317,7 +324,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
         __syncthreads();
         const int64_t part = sm_part;
         if (part >= parts) break;
-        status_next[part * 256 + threadIdx.x] = 0u;   // ready for the next pass
+        if (threadIdx.x < 256) status_next[part * 256 + threadIdx.x] = 0u;   // for the next pass
 
         // ---- load and rank within the warp (stable: slot-major, lane-minor)
         const int64_t wbase = part * kSortPart + (int64_t)warp * (32 * kSortItems);
@@ -350,28 +357,32 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
 
         // ---- block digit counts, per-warp offsets, local digit starts
         const int d = threadIdx.x;
+        const bool digit_thread = d < 256;
         uint32_t tot = 0;
+        if (digit_thread) {
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t c = whist[w][d];
-            whist[w][d] = tot;
-            tot += c;
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = whist[w][d];
+                whist[w][d] = tot;
+                tot += c;
+            }
+            if (part == 0)
+                atomicExch(&status[d], kFlagPrefix | tot);
+            else
+                atomicExch(&status[part * 256 + d], kFlagAgg | tot);
         }
-        if (part == 0)
-            atomicExch(&status[d], kFlagPrefix | tot);
-        else
-            atomicExch(&status[part * 256 + d], kFlagAgg | tot);
         uint64_t dummy;
         const uint64_t ds = block_exclusive_scan_u64(tot, sm_warp, dummy);
-        dstart[d] = (uint32_t)ds;
-
-        // ---- decoupled look-back per digit
-        uint32_t excl = 0;
-        if (part > 0) {
-            excl = lookback<uint32_t, 30>(status + d, 256, part, st, 2);
-            atomicExch(&status[part * 256 + d], kFlagPrefix | ((excl + tot) & kValMask));
+        if (digit_thread) {
+            dstart[d] = (uint32_t)ds;
+            // ---- decoupled look-back per digit
+            uint32_t excl = 0;
+            if (part > 0) {
+                excl = lookback<uint32_t, 30>(status + d, 256, part, st, 2);
+                atomicExch(&status[part * 256 + d], kFlagPrefix | ((excl + tot) & kValMask));
+            }
+            gbase[d] = (int64_t)ws->hist[pass][d] + excl - (int64_t)ds;
         }
-        gbase[d] = (int64_t)ws->hist[pass][d] + excl - (int64_t)ds;
         __syncthreads();
 
         // ---- scatter into shared memory in block order, then out
@@ -455,6 +466,28 @@ static size_t sort_ws_bytes(uint64_t capacity) {
 
 // Enqueue a radix sort of the first *d_n pairs by key bits [begin_bit,
 // begin_bit + 8 passes); tells whether the result is in the alt buffers.
+// Opt the sort kernels in to their dynamic shared memory, once per device
+// (the first call on a device should come before any stream capture).
+template <typename K>
+static mg_status sort_smem_optin(size_t bytes) {
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(onesweep_kernel<K, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(onesweep_kernel<K, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess)
+            return MG_ERR_CUDA;
+        done[dev] = true;
+    }
+    return MG_OK;
+}
+
 // With `drop`, elements whose key is kDroppedKey leave in the first pass; the
 // count kept is ws->n_kept (device), the count the later passes use.
 template <typename K>
@@ -475,9 +508,11 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
                                512, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws, max_parts,
                                             drop);
     sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
+    const size_t stage_bytes = (sizeof(K) + sizeof(uint32_t)) * (size_t)kSortPart;
+    if (sort_smem_optin<K>(stage_bytes) != MG_OK) return MG_ERR_CUDA;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<K, false>, kSortThreads,
-                                                  0);
+                                                  stage_bytes);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = (int64_t)sms * per_sm < max_parts ? (int64_t)sms * per_sm : max_parts;
     K *kin = keys, *kout = keys_alt;
@@ -486,10 +521,10 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
         // after a dropping first pass the later ones sort the kept elements
         const uint64_t *np_ = (drop && p > 0) ? &ws->n_kept : d_n;
         if (drop && p == 0)
-            onesweep_kernel<K, true><<<(unsigned)grid, kSortThreads, 0, s>>>(
+            onesweep_kernel<K, true><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
                 kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
         else
-            onesweep_kernel<K, false><<<(unsigned)grid, kSortThreads, 0, s>>>(
+            onesweep_kernel<K, false><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
                 kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
         K *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
