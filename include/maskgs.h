@@ -42,8 +42,11 @@
  *     splat records start at record index R_v = sum_{u<v} gaussian_count_u,
  *     its tiles at T_v = sum_{u<v} tiles_x_u * tiles_y_u, its pixels at
  *     P_v = sum_{u<v} W_u * H_u.
- *   - Thread safety: no global state; concurrent calls on distinct buffers
- *     are independent.
+ *   - Thread safety: concurrent calls on distinct buffers are independent.
+ *     The library's only process-wide state is set once per device under a
+ *     lock (the sort kernels' shared-memory limit; the address of the scratch
+ *     array of mg_bin_noalloc, which itself must not be shared by overlapping
+ *     calls); make the first call on a device outside stream capture.
  */
 #ifndef MASKGS_H
 #define MASKGS_H
