@@ -347,6 +347,32 @@ def run_ours(args):
                 "frac": achieved / float(peaks["hbm_gbs"]), "traffic": _profiled_traffic(dom),
                 "peak_source": peak_src}
 
+    # algorithmic bytes of the memory-bound stages (FP32 storage; per-unit
+    # figures of the design notes): achieved GB/s against the measured copy peak
+    n_g, R_ = g.n, g.n
+    tiles_total = int(rast._state["tiles"])
+    sh_b = 3 * 16 * 4
+    stage_bytes = {
+        # read means, scales, quats, opacity, mask scores (all) + SH (visible);
+        # write tiles, radius, clamp, mask, soft mask (all) + render and bin records
+        "preprocess": n_g * (12 + 12 + 16 + 4 + 8) + visible * sh_b +
+                      n_g * (4 + 4 + 1 + 1 + 4) + visible * (48 + 48),
+        # depth keys (read depth, write key + index), 4 passes of key + index,
+        # scan (tiles, order in; offsets out), duplicate (order, offset, tiles,
+        # binning record per visible record; key + value per candidate)
+        "bin": R_ * (4 + 8) + 4 * R_ * 16 + R_ * 12 + visible * (4 + 4 + 4 + 48) + K * 8,
+        # histogram (keys), first pass (all candidates in, kept out), second
+        # pass (kept in and out), ranges (kept keys in, tile ranges out)
+        "sort": K * 4 + K * 8 + K_kept * 8 + K_kept * 16 + K_kept * 4 + tiles_total * 8,
+        # read parameters (all) + 2D gradients, SH (visible); write every gradient
+        "preprocess_bwd": n_g * (12 + 12 + 16 + 4 + 4) + visible * (48 + sh_b + 4 + 1) +
+                          n_g * (12 + 12 + 16 + 4 + 8 + sh_b),
+    }
+    hbm = float(_peaks()[0]["hbm_gbs"])
+    stage_roof = {k: {"bytes": int(b), "achieved_gbs": b / (stage_ms[k] * 1e-3) / 1e9,
+                      "frac_of_measured_hbm": b / (stage_ms[k] * 1e-3) / 1e9 / hbm}
+                  for k, b in stage_bytes.items()}
+
     line = {
         "metric": METRIC, "value": _whole_job_value(mpix, ws, ms), "unit": "Mpix/s", "n_gpus": ws,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
@@ -366,6 +392,7 @@ def run_ours(args):
                    "visible": visible, "mask_on_fraction": mask_on},
         "stage_ms": stage_ms,
         "roofline": roof,
+        "stage_roofline_hbm": stage_roof,
         "e2e": {"value": _whole_job_value(mpix, ws, e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "copies": "pinned host <-> device every step, overlapped with the neighbouring "
