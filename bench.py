@@ -240,6 +240,10 @@ def run_ours(args):
     clk = clocks.stop()
     ms = _max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, dev)
     stage_ms = {k: statistics.mean(e[k][0].elapsed_time(e[k][1]) for e in evs) for k in stage_names}
+    # per-step distribution: first stage's start to last stage's end of each step
+    per_step = sorted(e["preprocess"][0].elapsed_time(e["preprocess_bwd"][1]) for e in evs)
+    q = lambda f: per_step[min(len(per_step) - 1, int(f * len(per_step)))]
+    step_dist = {"p10": q(0.10), "median": q(0.50), "p90": q(0.90), "n": len(per_step)}
 
     # counts of this workload (extra counted steps, outside the timed region):
     # the method's fragments over its own tile lists (whole 3-sigma
@@ -391,6 +395,7 @@ def run_ours(args):
                                               bwd_counts)),
                    "visible": visible, "mask_on_fraction": mask_on},
         "stage_ms": stage_ms,
+        "step_ms_distribution": step_dist,
         "roofline": roof,
         "stage_roofline_hbm": stage_roof,
         "e2e": {"value": _whole_job_value(mpix, ws, e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
@@ -406,6 +411,7 @@ def run_ours(args):
         # rows); a multi-rank run times the replicated step only
         line["forms"] = run_forms(dev, g, cams, target, ms, W * H)
         line["forms"]["next_rows"] = run_next_rows(dev, g, cams, target, ms, peaks)
+        line["forms"]["tiny_c1"] = tiny_workload_times(dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(steps=1)
     if clk is not None and clk["samples"] < 3:
@@ -659,9 +665,53 @@ def cpu_baseline_sample(steps=1, crop=None):
     t = statistics.median(times)
     what = "the full 1557x1038 view" if crop is None else f"the centre {cam.width}x{cam.height} crop of the 1557x1038 view"
     return {"value": cam.width * cam.height / 1e6 / t, "unit": "Mpix/s", "cores": os.cpu_count(),
-            "kind": "oracle", "seconds_per_step": t,
+            "cpu": _cpu_model(), "kind": "oracle", "seconds_per_step": t,
             "sample": f"{what}: masked fwd+bwd of the 1.2M-Gaussian scene, all Gaussians "
                       f"preprocessed, FP64, OpenMP over tiles; median of {steps} step(s)"}
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def tiny_workload_times(dev, steps=50):
+    """The tiny configuration (10 000 Gaussians, 128x128): the GPU step (eager
+    and captured) and the oracle on the host cores."""
+    import torch
+    from oracle import pipeline
+    from paper_2412_20522_gb300 import scenes
+    from paper_2412_20522_gb300.autotune import GraphStep, time_step
+    from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
+    g, cams, tgt = scenes.tiny_workload()
+    p = _device_params(g, dev)
+    t = torch.as_tensor(tgt).to(dev).reshape(-1)
+    rast = Rasterizer(dev)
+    cfg = RasterConfig()
+    rast.forward(p, cams, cfg, check=True)
+
+    def eager():
+        img = rast.forward(p, cams, cfg, check=False)
+        _, dimg = rast.l1_loss_grad(img, t)
+        rast.backward(dimg)
+    ms_eager = time_step(eager, steps=steps)
+    gs = GraphStep(p, cams, cfg, t)
+    ms_graph = time_step(gs.replay, steps=steps)
+    t0 = time.perf_counter()
+    pipeline.forward_backward_l1(g, cams, [tgt], pipeline.OracleConfig())
+    cpu_s = time.perf_counter() - t0
+    return {"gaussians": g.n, "resolution": "128x128", "gpu_ms_eager": ms_eager,
+            "gpu_ms_graph": ms_graph, "oracle_s": cpu_s, "oracle_cores": os.cpu_count()}
 
 
 def run_reference(args):
