@@ -32,10 +32,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-struct Frag {
-    float dx, dy, p1, p2, e, G, araw, alpha;
-    bool on;             // alpha reaches the 1/255 floor
-};
+// Paired FP32 arithmetic for the alpha of a thread's two pixels (.x = the
+// first pixel, .y = the one kRowStep rows below): one instruction for both,
+// per component the correctly rounded scalar operation.
+__device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // alpha = min(0.99, o 2^e), e = h1 p1^2 + h2 p2^2, p1 = d.u, p2 = d.u_perp,
 // d = pixel centre - mean.  A = (mx, my, ux, uy), B = (h1, h2, +-o, e_min):
@@ -47,27 +49,31 @@ struct Frag {
 // pixel's offsets follow from the first's (d.y + 4, p1 + 4 uy, p2 + 4 ux).
 constexpr float kRowStep = 4.0f;
 
-__device__ __forceinline__ void frag_finish(const float4 &B, Frag &f) {
-    f.e = __fmaf_rn(__fmul_rn(B.x, f.p1), f.p1, __fmul_rn(__fmul_rn(B.y, f.p2), f.p2));
-    // straight-line: the exp unit has room, a branch per pixel costs more
-    f.G = ex2_approx(f.e);
-    f.araw = __fmul_rn(fabsf(B.z), f.G);
-    f.alpha = fminf(kAlphaMax, f.araw);
-    f.on = f.alpha >= kAlphaMin;
-}
+struct FragPair {
+    float dx;            // pixel centre - mean, x (one column: shared by the pair)
+    float dy0;           // y offset of the first pixel; the second's is dy0 + kRowStep
+    float2 araw, alpha;  // o 2^e and min(0.99, o 2^e) of both pixels
+    bool on0, on1;       // alpha reaches the 1/255 floor
+};
 
-__device__ __forceinline__ void frag_alpha_pair(const float4 &A, const float4 &B, float fpx,
-                                                float fpy0, Frag f[2]) {
-    f[0].dx = __fsub_rn(fpx, A.x);
-    f[0].dy = __fsub_rn(fpy0, A.y);
-    f[0].p1 = __fmaf_rn(f[0].dy, A.w, __fmul_rn(f[0].dx, A.z));
-    f[0].p2 = __fmaf_rn(f[0].dy, A.z, -__fmul_rn(f[0].dx, A.w));
-    f[1].dx = f[0].dx;
-    f[1].dy = __fadd_rn(f[0].dy, kRowStep);
-    f[1].p1 = __fmaf_rn(kRowStep, A.w, f[0].p1);
-    f[1].p2 = __fmaf_rn(kRowStep, A.z, f[0].p2);
-    frag_finish(B, f[0]);
-    frag_finish(B, f[1]);
+__device__ __forceinline__ FragPair frag_alpha_pair(const float4 &A, const float4 &B, float fpx,
+                                                    float fpy0) {
+    FragPair f;
+    f.dx = __fsub_rn(fpx, A.x);
+    f.dy0 = __fsub_rn(fpy0, A.y);
+    const float p10 = __fmaf_rn(f.dy0, A.w, __fmul_rn(f.dx, A.z));
+    const float p20 = __fmaf_rn(f.dy0, A.z, -__fmul_rn(f.dx, A.w));
+    const float2 p1 = make_float2(p10, __fmaf_rn(kRowStep, A.w, p10));
+    const float2 p2 = make_float2(p20, __fmaf_rn(kRowStep, A.z, p20));
+    // e = (h1 p1) p1 + (h2 p2) p2, the products rounded, the sum fused
+    const float2 e = fma2(mul2(bcast2(B.x), p1), p1, mul2(mul2(bcast2(B.y), p2), p2));
+    // straight-line: the exp unit has room, a branch per pixel costs more
+    const float2 G = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+    f.araw = mul2(bcast2(fabsf(B.z)), G);
+    f.alpha = make_float2(fminf(kAlphaMax, f.araw.x), fminf(kAlphaMax, f.araw.y));
+    f.on0 = f.alpha.x >= kAlphaMin;
+    f.on1 = f.alpha.y >= kAlphaMin;
+    return f;
 }
 
 // Tile of the CTA and the kPix pixels of this thread.  Each warp owns one
@@ -213,16 +219,16 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 float Tc = T[k];
                 for (int j = 0; j < cnt; ++j) {
                     const float4 B = sB[j];
-                    Frag fp[kPix];
-                    frag_alpha_pair(sA[j], B, fpx[0], fpy[0], fp);
-                    const Frag &f = fp[k];
+                    const FragPair f = frag_alpha_pair(sA[j], B, fpx[0], fpy[0]);
+                    const bool on = k == 0 ? f.on0 : f.on1;
+                    const float alpha = k == 0 ? f.alpha.x : f.alpha.y;
                     if (B.z < 0.0f) {
-                        c_masked += f.on;
+                        c_masked += on;
                         continue;
                     }
                     ++c_unmasked;
-                    if (!f.on) continue;
-                    const float tT = Tc * (1.0f - f.alpha);
+                    if (!on) continue;
+                    const float tT = Tc * (1.0f - alpha);
                     if (tT < kTMin) {
                         --c_unmasked;
                         break;
@@ -241,20 +247,20 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                 const int j = (ch << 5) + __ffs(word) - 1;
                 word &= word - 1;
                 const float4 A = sA[j], B = sB[j], c = sC[j];
-                Frag fp[kPix];
-                frag_alpha_pair(A, B, fpx[0], fpy[0], fp);
+                const FragPair f = frag_alpha_pair(A, B, fpx[0], fpy[0]);
+                const bool on[kPix] = {f.on0, f.on1};
+                const float al[kPix] = {f.alpha.x, f.alpha.y};
 #pragma unroll
                 for (int k = 0; k < kPix; ++k) {
                     if (done[k]) continue;
-                    const Frag &f = fp[k];
-                    if (!f.on) continue;
-                    const float testT = T[k] * (1.0f - f.alpha);
+                    if (!on[k]) continue;
+                    const float testT = T[k] * (1.0f - al[k]);
                     if (testT < kTMin) {
                         done[k] = true;
                         stop[k] = (b0 - start) + j;
                         continue;
                     }
-                    const float w = f.alpha * T[k];
+                    const float w = al[k] * T[k];
                     C0[k] = fmaf(w, c.x, C0[k]);
                     C1[k] = fmaf(w, c.y, C1[k]);
                     C2[k] = fmaf(w, c.z, C2[k]);
@@ -378,8 +384,10 @@ constexpr int kAcc = 10;
 // [0] (warp, splat) list iterations, [1] of which masked, [2] unmasked with a
 // contributing pixel, [3] masked with a contributing pixel, [4] contributing
 // pixels over [2], [5] staged batches.
+// Nine CTAs per SM (36 warps): the register cap this asks for (56) holds
+// without spills, and nine copies of the 23.8 KB of shared memory fit.
 template <bool COUNT>
-__global__ void __launch_bounds__(kRenderThreads, 768 / kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, 1152 / kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                        const uint32_t *__restrict__ tile_order,
@@ -399,15 +407,14 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     bool red_writer;
     const int red_t = red_term(lane, red_writer);   // term this lane flushes
 
-    float fpx[kPix], fpy[kPix], T[kPix], g0[kPix], g1[kPix], g2[kPix], bc0[kPix], bc1[kPix],
-        bc2[kPix];
+    static_assert(kPix == 2, "the backward's moment sums assume a column pair");
+    const float fpx = (float)ti.px[0] + 0.5f, fpy0 = (float)ti.py[0] + 0.5f;
+    float T[kPix], g0[kPix], g1[kPix], g2[kPix], bc0[kPix], bc1[kPix], bc2[kPix];
     uint32_t stop[kPix];
     const mg_camera &Cm = vt.cam[ti.v];
     const int64_t HW = (int64_t)Cm.width * Cm.height;
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
-        fpx[k] = (float)ti.px[k] + 0.5f;
-        fpy[k] = (float)ti.py[k] + 0.5f;
         T[k] = 1.0f;
         g0[k] = g1[k] = g2[k] = 0.0f;
         stop[k] = 0;
@@ -471,15 +478,12 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     const int j = (ch << 5) + hb;
                     const float4 A = sA[j], B = sB[j];
                     const bool masked = B.z < 0.0f;
-                    // alpha of every pixel first: independent, so they interleave
-                    Frag f[kPix];
-                    bool on[kPix];
-                    frag_alpha_pair(A, B, fpx[0], fpy[0], f);
-#pragma unroll
-                    for (int k = 0; k < kPix; ++k) on[k] = pos0 + j < stop[k] && f[k].on;
-                    int ncontrib = 0;
-#pragma unroll
-                    for (int k = 0; k < kPix; ++k) ncontrib += (int)on[k];
+                    const FragPair f = frag_alpha_pair(A, B, fpx, fpy0);
+                    const bool on[kPix] = {pos0 + j < stop[0] && f.on0,
+                                           pos0 + j < stop[1] && f.on1};
+                    const float al[kPix] = {f.alpha.x, f.alpha.y};
+                    const float ar[kPix] = {f.araw.x, f.araw.y};
+                    const int ncontrib = (int)on[0] + (int)on[1];
                     if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) continue;
                     const float4 c = sC[j];
                     // the mask is uniform over the warp: two straight-line paths
@@ -493,13 +497,14 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                             if (!on[k]) continue;
                             const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
                                               g2[k] * (c.z - bc2[k]);
-                            v[9] = fmaf(f[k].alpha * T[k], gcb, v[9]);   // Eq. 6 + Appendix A
+                            v[9] = fmaf(al[k] * T[k], gcb, v[9]);   // Eq. 6 + Appendix A
                         }
                     } else {
+                        float s1 = 0.0f;
 #pragma unroll
                         for (int k = 0; k < kPix; ++k) {
                             if (!on[k]) continue;
-                            const float alpha = f[k].alpha;
+                            const float alpha = al[k];
                             const float Tj = __fdividef(T[k], 1.0f - alpha);
                             const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
                                               g2[k] * (c.z - bc2[k]);
@@ -513,17 +518,18 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                             bc1[k] = fmaf(alpha, c.y - bc1[k], bc1[k]);
                             bc2[k] = fmaf(alpha, c.z - bc2[k], bc2[k]);
                             T[k] = Tj;
-                            if (f[k].araw < kAlphaMax) {
-                                // dL/dalpha * alpha (0 through the 0.99 clamp)
-                                const float pdx = dm * f[k].dx, pdy = dm * f[k].dy;
-                                v[0] += dm;
-                                v[1] += pdx;
-                                v[2] += pdy;
-                                v[3] = fmaf(pdx, f[k].dx, v[3]);
-                                v[4] = fmaf(pdx, f[k].dy, v[4]);
-                                v[5] = fmaf(pdy, f[k].dy, v[5]);
-                            }
+                            // dL/dalpha * alpha (0 through the 0.99 clamp)
+                            const float m = ar[k] < kAlphaMax ? dm : 0.0f;
+                            v[0] += m;
+                            if (k == 1) s1 = kRowStep * m;
                         }
+                        // the pair shares dx and its dy differ by kRowStep: the
+                        // moments follow from the sum of m and the second's m
+                        v[1] = v[0] * f.dx;                               // sum m dx
+                        v[2] = fmaf(f.dy0, v[0], s1);                     // sum m dy
+                        v[3] = v[1] * f.dx;                               // sum m dx^2
+                        v[4] = v[2] * f.dx;                               // sum m dx dy
+                        v[5] = fmaf(v[2], f.dy0, s1 * __fadd_rn(f.dy0, kRowStep));  // sum m dy^2
                     }
                     if (COUNT) {
                         const unsigned cb = __ballot_sync(0xffffffffu, ncontrib > 0);
