@@ -1,19 +1,20 @@
 // Masked rasterisation, forward (Eq. 3-4) and backward (Eq. 6, Appendix A),
 // and the L1 render loss.
 //
-// One CTA of 128 threads per tile, two pixels per thread: warp w owns a
-// compact block of 64 pixels (4 rows of a 16x16 tile).  The tile's
-// depth-sorted splats are staged through shared memory in batches of 256
-// (each thread gathers two 48-byte records and culls each splat against the
+// One CTA of 128 threads per tile, two pixels per thread: warp w owns an 8x8
+// block of the tile, a lane one column of it at two rows 4 apart.  The
+// tile's depth-sorted splats are staged through shared memory in batches
+// (each thread gathers 48-byte records and culls each splat against the
 // four warp blocks), then every warp walks only the splats that can reach its
 // block, applying each to both of a thread's pixels.  The forward skips
 // masked splats outright: with M_i = 0 they neither add colour nor attenuate
 // T (Eq. 3-4).  The backward walks the same lists back to front from each
 // pixel's stop index, recovers T_i = T_{i+1}/(1 - M_i alpha_i), sums each
 // splat's ten gradient terms over a thread's two pixels, then over the warp
-// with a halving shuffle exchange, over the CTA with shared-memory atomics,
-// and issues three vector atomics per splat and tile.  Masked splats carry
-// only dL/dM (one scalar reduction and atomic).
+// with a halving shuffle exchange into the warp's own shared-memory slot,
+// adds the warps' slots when the batch is flushed, and issues three vector
+// atomics per splat and tile.  Masked splats carry only dL/dM (one scalar
+// reduction and atomic).
 //
 // alpha is evaluated by the same explicitly rounded sequence in both kernels
 // so that the forward's and the backward's per-fragment decisions agree.
@@ -386,8 +387,9 @@ constexpr int kAcc = 10;
 // pixels over [2], [5] staged batches.
 // Nine CTAs per SM (36 warps): the register cap this asks for (56) holds
 // without spills, and nine copies of the 23.8 KB of shared memory fit.
+constexpr int kBatchB = 128;                    // splats staged per backward batch
 template <bool COUNT>
-__global__ void __launch_bounds__(kRenderThreads, 1152 / kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, 1024 / kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                        const uint32_t *__restrict__ tile_order,
@@ -395,11 +397,12 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ n_contrib, const float *__restrict__ dL_dimage,
                        float *__restrict__ grad2d, unsigned long long *counters) {
     unsigned long long cnt_it = 0, cnt_m = 0, cnt_cu = 0, cnt_cm = 0, cnt_pix = 0, cnt_b = 0;
-    __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
-    __shared__ uint32_t sR[kBatch];
-    __shared__ uint8_t sM[kBatch];
-    __shared__ float sG[kBatch][kAcc];
+    __shared__ float4 sA[kBatchB], sB[kBatchB], sC[kBatchB];
+    __shared__ uint32_t sR[kBatchB];
+    __shared__ uint8_t sM[kBatchB];
+    __shared__ float sG[kRenderWarps][kBatchB][kAcc];   // per-warp sums: plain stores
     __shared__ uint32_t s_maxstop;
+    __shared__ uint32_t s_wstop[kRenderWarps];
     const int64_t t = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
     const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
@@ -440,18 +443,19 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     __syncthreads();
     const uint32_t maxstop = min(s_maxstop, end - start);
     if (maxstop == 0) return;
-    const int nb = (int)((maxstop + kBatch - 1) / kBatch);
+    const int nb = (int)((maxstop + kBatchB - 1) / kBatchB);
     if (COUNT) cnt_b = nb;
     uint32_t wstop = tstop;                                    // warp's largest stop
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wstop = max(wstop, __shfl_xor_sync(0xffffffffu, wstop, o));
+    if (lane == 0) s_wstop[warp] = wstop;
 
     for (int bi = nb - 1; bi >= 0; --bi) {
-        const uint32_t pos0 = (uint32_t)bi * kBatch;
-        const int cnt = (int)min(maxstop - pos0, (uint32_t)kBatch);
+        const uint32_t pos0 = (uint32_t)bi * kBatchB;
+        const int cnt = (int)min(maxstop - pos0, (uint32_t)kBatchB);
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < kBatch / kRenderThreads; ++h) {
+        for (int h = 0; h < kBatchB / kRenderThreads; ++h) {
             const int i = threadIdx.x + h * kRenderThreads;
             if (i < cnt) {
                 const uint32_t r = vals[start + pos0 + i];
@@ -462,8 +466,6 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                 sC[i] = rec[3 * (int64_t)r + 2];
                 sM[i] = (uint8_t)block_mask(A, B, (float)ti.x0, (float)ti.y0, ti.nbx);
             }
-#pragma unroll
-            for (int k = 0; k < kAcc; ++k) sG[i][k] = 0.0f;
         }
         __syncthreads();
 
@@ -484,7 +486,11 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                     const float al[kPix] = {f.alpha.x, f.alpha.y};
                     const float ar[kPix] = {f.araw.x, f.araw.y};
                     const int ncontrib = (int)on[0] + (int)on[1];
-                    if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) continue;
+                    if (!COUNT && !__any_sync(0xffffffffu, ncontrib > 0)) {
+                        // every (warp, splat) of the warp's list leaves its sums
+                        if (masked ? lane == 0 : red_writer) sG[warp][j][masked ? 9 : red_t] = 0.0f;
+                        continue;
+                    }
                     const float4 c = sC[j];
                     // the mask is uniform over the warp: two straight-line paths
                     float v[10];
@@ -540,26 +546,43 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                         cnt_cm += (masked && cb);
                         cnt_pix += masked ? 0 : tot;
                     }
-                    if (__any_sync(0xffffffffu, ncontrib > 0)) {
-                        if (masked) {
-                            const float dm = warp_sum(v[9]);
-                            if (lane == 0) atomicAdd(&sG[j][9], dm);
-                        } else {
-                            const float r = warp_transpose_sum10(v, lane);
-                            if (red_writer) atomicAdd(&sG[j][red_t], r);
-                        }
+                    if (masked) {
+                        const float dm = warp_sum(v[9]);
+                        if (lane == 0) sG[warp][j][9] = dm;
+                    } else {
+                        const float r = warp_transpose_sum10(v, lane);
+                        if (red_writer) sG[warp][j][red_t] = r;
                     }
                 }
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < kBatch / kRenderThreads; ++h) {
+        for (int h = 0; h < kBatchB / kRenderThreads; ++h) {
             const int i = threadIdx.x + h * kRenderThreads;
             if (i >= cnt) continue;
-            const float *S = sG[i];
             float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[i];
             const float4 B = sB[i];
+            // sum the slots of the warps whose list held the splat
+            // (a warp whose pixels all stop before this batch skipped it)
+            uint32_t wm = sM[i];
+#pragma unroll
+            for (int w = 0; w < kRenderWarps; ++w)
+                if (pos0 >= s_wstop[w]) wm &= ~(1u << w);
+            float S[kAcc];
+#pragma unroll
+            for (int q = 0; q < kAcc; ++q) S[q] = 0.0f;
+            if (B.z < 0.0f) {
+#pragma unroll
+                for (int w = 0; w < kRenderWarps; ++w)
+                    if ((wm >> w) & 1u) S[9] += sG[w][i][9];
+            } else {
+#pragma unroll
+                for (int w = 0; w < kRenderWarps; ++w)
+                    if ((wm >> w) & 1u)
+#pragma unroll
+                        for (int q = 0; q < kAcc; ++q) S[q] += sG[w][i][q];
+            }
             if (B.z < 0.0f) {
                 if (S[9] != 0.0f) atomicAdd(&G4[2].y, S[9]);
             } else {
