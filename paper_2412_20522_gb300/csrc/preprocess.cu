@@ -493,6 +493,10 @@ __device__ __forceinline__ void cov_backward(const CovState<F> &S, const mg_came
     if (!clampy) dL_dt[1] += (float)(-dJ12 * fy * itz2);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // dL/dsh accumulates over views in a per-warp shared-memory tile (one row
 // per lane, odd row stride) and leaves with coalesced 128-bit stores; SH rows
 // are read only for Gaussians visible in some view.
@@ -513,6 +517,25 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
     __syncwarp();
     const int64_t i = gw0 + lane;
     if (lane < nrows) {
+        // a Gaussian visible in some view: start its 2D gradients and its SH
+        // row towards L2 before the dependent work that reads them
+        bool vis = false;
+        for (int v = 0; v < vt.n_views; ++v) {
+            if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
+            const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
+            if (sp.radius[r] == 0) continue;
+            vis = true;
+            const char *gp = reinterpret_cast<const char *>(grad2d + 12 * r);
+            prefetch_l2(gp);
+            prefetch_l2(gp + 47);
+        }
+        if (vis) {
+            constexpr int RB = ROW * (int)sizeof(ST);
+            const char *sp0 = reinterpret_cast<const char *>(g.sh) + i * RB;
+#pragma unroll
+            for (int o = 0; o < RB; o += 128) prefetch_l2(sp0 + o);
+            prefetch_l2(sp0 + RB - 1);
+        }
         float *drow = dsh + lane * S_;
         const float *means = reinterpret_cast<const float *>(g.means);
         const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
