@@ -358,13 +358,16 @@ def run_ours(args):
     sh_b = 3 * 16 * 4
     stage_bytes = {
         # read means, scales, quats, opacity, mask scores (all) + SH (visible);
-        # write tiles, radius, clamp, mask, soft mask (all) + render and bin records
+        # write tiles, radius, clamp, mask, soft mask, depth key (all) +
+        # render and bin records (visible)
         "preprocess": n_g * (12 + 12 + 16 + 4 + 8) + visible * sh_b +
-                      n_g * (4 + 4 + 1 + 1 + 4) + visible * (48 + 48),
-        # depth keys (read depth, write key + index), 4 passes of key + index,
-        # scan (tiles, order in; offsets out), duplicate (order, offset, tiles,
-        # binning record per visible record; key + value per candidate)
-        "bin": R_ * (4 + 8) + 4 * R_ * 16 + R_ * 12 + visible * (4 + 4 + 4 + 48) + K * 8,
+                      n_g * (4 + 4 + 1 + 1 + 4 + 4) + visible * (48 + 48),
+        # depth order (histogram and first pass read the keys, the first pass
+        # writes key + index, 3 passes of key + index), scan (tiles, order in;
+        # offsets out), duplicate (order, offset, tiles, binning record per
+        # visible record; key + value per candidate)
+        "bin": R_ * 4 + R_ * (4 + 8) + 3 * R_ * 16 + R_ * 12 + visible * (4 + 4 + 4 + 48) +
+               K * 8,
         # histogram (keys), first pass (all candidates in, kept out), second
         # pass (kept in and out), ranges (kept keys in, tile ranges out)
         "sort": K * 4 + K * 8 + K_kept * 8 + K_kept * 16 + K_kept * 4 + tiles_total * 8,

@@ -196,7 +196,11 @@ typedef struct {
  *   given masks).
  * Per view (n_views), nullable: mask_count[v] u32 = sum of M_i over view v's
  *   Gaussian range (written by mg_preprocess; needed by mg_mask_loss and by
- *   mg_preprocess_backward when lambda_m != 0). */
+ *   mg_preprocess_backward when lambda_m != 0).
+ * Nullable: depth_key[R] u32, the depth-order key of each record (the float
+ *   bits of tz, 0xFFFFFFFF for a record that touches no tile); written by
+ *   mg_preprocess when non-null, and then read by mg_depth_order instead of
+ *   deriving the keys from record and tiles_touched. */
 typedef struct {
     float *record;
     uint32_t *tiles_touched;
@@ -206,6 +210,7 @@ typedef struct {
     uint8_t *mask;
     float *mask_soft;
     uint32_t *mask_count;
+    uint32_t *depth_key;
 } mg_splats;
 
 /* Gradients w.r.t. the per-view splats, grad2d[R][12] FP32:
@@ -237,8 +242,10 @@ mg_status mg_preprocess(const mg_gaussians *g, const mg_view *views, int32_t n_v
 /* ---- 2. depth order and bin (Sec. 3.1) ------------------------------------ */
 /* Stable radix sort of the R splat records (all views) by the float bits of
  * their depth, records that touch no tile last: order[R] (u32 record indices).
- * Depth ties keep record order.  keys, keys_alt, order_alt: u32[R] scratch.
- * workspace: mg_depth_order_workspace_bytes(R) bytes, any content. */
+ * Depth ties keep record order.  The keys are splats->depth_key when non-null
+ * (as mg_preprocess wrote them), else derived from record and tiles_touched.
+ * keys, keys_alt, order_alt: u32[R] scratch.  workspace:
+ * mg_depth_order_workspace_bytes(R) bytes, any content. */
 mg_status mg_depth_order(const mg_splats *splats, const mg_view *views, int32_t n_views,
                          const mg_raster_cfg *cfg, uint32_t *order, uint32_t *order_alt,
                          uint32_t *keys, uint32_t *keys_alt, void *workspace,

@@ -70,7 +70,7 @@ class mg_raster_cfg(C.Structure):
 class mg_splats(C.Structure):
     _fields_ = [("record", C.c_void_p), ("tiles_touched", C.c_void_p), ("radius", C.c_void_p),
                 ("clamp", C.c_void_p), ("bin_record", C.c_void_p), ("mask", C.c_void_p),
-                ("mask_soft", C.c_void_p), ("mask_count", C.c_void_p)]
+                ("mask_soft", C.c_void_p), ("mask_count", C.c_void_p), ("depth_key", C.c_void_p)]
 
 
 class mg_gaussian_arrays(C.Structure):

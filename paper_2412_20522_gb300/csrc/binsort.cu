@@ -219,7 +219,10 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
 // --------------------------------------------------------------------------
 // Instances to sort: all of them, or none when they overflowed the capacity
 // (the buffers then hold an incomplete list; the status word says so).
+// Element count of a sort: *d_n (0 if it exceeds capacity), or capacity when
+// the count is known on the host (d_n null).
 __device__ __forceinline__ int64_t sort_count(const uint64_t *d_n, uint64_t capacity) {
+    if (d_n == nullptr) return (int64_t)capacity;
     const uint64_t n = *d_n;
     return n <= capacity ? (int64_t)n : 0;
 }
@@ -293,7 +296,8 @@ __global__ void sort_offsets_kernel(SortWS *ws) {
     if (p == 0 && threadIdx.x == 0) ws->n_kept = tot;      // elements the sort keeps
 }
 
-template <typename K, bool DROP>
+// IDX = true: no value array; the values are the input positions.
+template <typename K, bool DROP, bool IDX = false>
 __global__ void __launch_bounds__(kSortThreads, 2048 / kSortThreads / 2)
 onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint64_t *d_n,
@@ -336,7 +340,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
             const int64_t idx = wbase + i * 32 + lane;
             const bool valid = idx < n;
             k[i] = valid ? keys_in[idx] : (K)0;
-            val[i] = valid ? vals_in[idx] : 0u;
+            val[i] = valid ? (IDX ? (uint32_t)idx : vals_in[idx]) : 0u;
             const bool kept = valid && !(DROP && (uint32_t)k[i] == kDroppedKey);
             dig[i] = kept ? (int)(((uint64_t)k[i] >> shift) & 0xFF) : 256;
         }
@@ -481,6 +485,9 @@ static mg_status sort_smem_optin(size_t bytes) {
                 cudaSuccess ||
             cudaFuncSetAttribute(onesweep_kernel<K, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(onesweep_kernel<K, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
                 cudaSuccess)
             return MG_ERR_CUDA;
         done[dev] = true;
@@ -490,11 +497,13 @@ static mg_status sort_smem_optin(size_t bytes) {
 
 // With `drop`, elements whose key is kDroppedKey leave in the first pass; the
 // count kept is ws->n_kept (device), the count the later passes use.
+// src_keys (nullable): the first pass reads these keys, with the input
+// positions 0, 1, 2, ... as values, instead of (keys, vals).
 template <typename K>
 static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
                             const uint64_t *d_n, uint64_t capacity, int begin_bit, int passes,
                             bool drop, SortWS *ws, mg_status_word *st, cudaStream_t s,
-                            bool *in_alt) {
+                            bool *in_alt, const K *src_keys = nullptr) {
     *in_alt = (passes & 1) != 0;
     if (cudaMemsetAsync(&ws->hist[0][0], 0, sizeof(ws->hist) + sizeof(ws->counter), s) !=
         cudaSuccess)
@@ -504,8 +513,9 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     const int64_t max_parts = sort_max_parts(capacity);
     const int64_t hblocks = (int64_t)((capacity + 4095) / 4096);
     const int64_t hcap = (int64_t)sms * 2;
+    const K *k0 = src_keys != nullptr ? src_keys : keys;
     sort_histogram_kernel<K><<<(unsigned)(hblocks < hcap ? (hblocks > 0 ? hblocks : 1) : hcap),
-                               512, 0, s>>>(keys, d_n, capacity, begin_bit, passes, ws, max_parts,
+                               512, 0, s>>>(k0, d_n, capacity, begin_bit, passes, ws, max_parts,
                                             drop);
     sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
     const size_t stage_bytes = (sizeof(K) + sizeof(uint32_t)) * (size_t)kSortPart;
@@ -520,7 +530,10 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     for (int p = 0; p < passes; ++p) {
         // after a dropping first pass the later ones sort the kept elements
         const uint64_t *np_ = (drop && p > 0) ? &ws->n_kept : d_n;
-        if (drop && p == 0)
+        if (p == 0 && src_keys != nullptr)
+            onesweep_kernel<K, false, true><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
+                src_keys, nullptr, kout, vout, np_, capacity, p, begin_bit, ws, max_parts, st);
+        else if (drop && p == 0)
             onesweep_kernel<K, true><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
                 kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
         else
@@ -557,12 +570,19 @@ extern "C" mg_status mg_depth_order(const mg_splats *splats, const mg_view *view
     if (workspace_bytes < mg_depth_order_workspace_bytes(R)) return MG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     SortWS *ws = reinterpret_cast<SortWS *>(workspace);
-    depth_keys_kernel<<<sm_count() * 4, 256, 0, s>>>(splats->record, splats->tiles_touched, R,
-                                                      keys, order, &ws->n);
     bool in_alt = false;
     // 4 passes (an even number): the result is back in (keys, order)
-    st = radix_sort<uint32_t>(keys, order, keys_alt, order_alt, &ws->n, (uint64_t)R, 0, 4, false,
-                              ws, d_status, s, &in_alt);
+    if (splats->depth_key != nullptr) {
+        // keys written by the preprocess; the first pass takes the record
+        // indices as values
+        st = radix_sort<uint32_t>(keys, order, keys_alt, order_alt, nullptr, (uint64_t)R, 0, 4,
+                                  false, ws, d_status, s, &in_alt, splats->depth_key);
+    } else {
+        depth_keys_kernel<<<sm_count() * 4, 256, 0, s>>>(splats->record, splats->tiles_touched,
+                                                          R, keys, order, &ws->n);
+        st = radix_sort<uint32_t>(keys, order, keys_alt, order_alt, &ws->n, (uint64_t)R, 0, 4,
+                                  false, ws, d_status, s, &in_alt);
+    }
     if (st != MG_OK) return st;
     return mg_host::launch_status();
 }

@@ -265,9 +265,12 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
             out.tiles_touched[r] = 0u;
             out.radius[r] = 0;
             out.clamp[r] = 0;
+            if (out.depth_key != nullptr) out.depth_key[r] = 0xFFFFFFFFu;
             continue;
         }
         out.tiles_touched[r] = (uint32_t)((S.x1 - S.x0 + 1) * (S.y1 - S.y0 + 1));
+        // depth-order key: the float bits of tz > 0 order like the values
+        if (out.depth_key != nullptr) out.depth_key[r] = __float_as_uint(S.tz);
         // binning record: tile-filter inputs (decision path) and the rectangle
         float4 *br = reinterpret_cast<float4 *>(out.bin_record) + 3 * r;
         br[0] = make_float4(S.px, S.py, S.a, S.b);

@@ -158,6 +158,7 @@ class Rasterizer:
         s.bin_record = self._get("bin_record", 12 * R, torch.float32).data_ptr()
         s.mask = self._get("mask", n, torch.uint8).data_ptr()
         s.mask_soft = self._get("mask_soft", n, torch.float32).data_ptr()
+        s.depth_key = self._get("depth_key", R, torch.int32).data_ptr()
         return s
 
     def _ensure_sort_buffers(self, cap, key_bits):
@@ -245,7 +246,7 @@ class Rasterizer:
             abi.mg_render_inference(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg,
                                     image, stream)
             ev.end("render")
-            self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
+            self._fwd_launches = 1 + 6 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
             self._state = None
             if check:
                 st = abi.mg_read_status(self.status, stream)
@@ -260,10 +261,10 @@ class Rasterizer:
         abi.mg_render(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image, final_T,
                       n_contrib, self.frag_count if count_fragments else None, stream)
         ev.end("render")
-        # kernels of ours per forward: preprocess; depth keys, histogram,
-        # offsets, 4 digit passes; scan, duplicate; histogram, offsets, one per
-        # tile digit pass, ranges; render
-        self._fwd_launches = 1 + 7 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
+        # kernels of ours per forward: preprocess (with the depth keys);
+        # histogram, offsets, 4 digit passes; scan, duplicate; histogram,
+        # offsets, one per tile digit pass, ranges; tile order; render
+        self._fwd_launches = 1 + 6 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
         self._state = dict(g=g, views=views, V=V, cfg=ccfg, splats=splats, R=R, n=n, pix=pix,
                            sorted_vals=sorted_vals, ranges=ranges_buf, tiles=tiles,
                            tile_order=tile_order,
