@@ -520,10 +520,13 @@ def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
     return forms
 
 
+PRUNE_OPS_PER_DRAW = 98 + 10 + 4 * 29 + 3
+
+
 def run_next_rows(dev, g, cams, target, plain_ms, peaks, steps=10):
     """The rows after the hot path, on the same 1.2M-Gaussian view: the mask
     loss (Eq. 7-8) and the ablations of Sec. 4.3 in the training step; the
-    pruning of Sec. 3.5 (sampler and compaction, HBM-bound); the inference
+    pruning of Sec. 3.5 (the sampler ALU-bound, the compaction HBM-bound); the inference
     renderer of the pruned model (rendering speed, Sec. 4.2)."""
     import torch
     from paper_2412_20522_gb300 import prune, scenes
@@ -574,13 +577,23 @@ def run_next_rows(dev, g, cams, target, plain_ms, peaks, steps=10):
     sample_bytes = n * (8 + 1)
     compact_bytes = n * (1 + 4 + 4) + 2 * kept * row
     hbm = float(peaks["hbm_gbs"])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     ms_s, ms_c = statistics.median(t_s), statistics.median(t_c)
     out["prune"] = {
         "gaussians": n, "kept": kept, "pruned_fraction": 1 - kept / n, "draws": 10,
         "sample_ms": ms_s, "compact_ms": ms_c,
-        "roofline_sample": {"bound": "hbm", "achieved": sample_bytes / (ms_s * 1e-3) / 1e9,
-                            "peak": hbm, "unit": "GB/s",
-                            "frac": sample_bytes / (ms_s * 1e-3) / 1e9 / hbm},
+        # the sampler is bound by its arithmetic: per draw a Philox4x32-10 block
+        # (98 integer ops), two uniforms (10), four correctly rounded logs (29
+        # ops each, the division counted once) and the margin (3); every warp
+        # runs all ten draws (it holds a Gaussian absent in every draw)
+        "roofline_sample": {"bound": "alu",
+                            "achieved": n * 10 * PRUNE_OPS_PER_DRAW / (ms_s * 1e-3) / 1e12,
+                            "peak": alu_peak, "unit": "Tops/s",
+                            "frac": n * 10 * PRUNE_OPS_PER_DRAW / (ms_s * 1e-3) / 1e12 / alu_peak,
+                            "basis": f"{PRUNE_OPS_PER_DRAW} 32-bit ops per draw x 10 draws per "
+                                     "lane; peak: one op per FP32 lane per clock",
+                            "hbm_frac": sample_bytes / (ms_s * 1e-3) / 1e9 / hbm},
         "roofline_compact": {"bound": "hbm", "achieved": compact_bytes / (ms_c * 1e-3) / 1e9,
                              "peak": hbm, "unit": "GB/s",
                              "frac": compact_bytes / (ms_c * 1e-3) / 1e9 / hbm},

@@ -245,3 +245,66 @@ def test_all_culled_scene(rz):
     out = rast.backward(torch.ones_like(img))
     for k in ("means", "sh", "opacity_logit"):
         assert float(out[k].abs().max()) == 0.0
+
+
+def _degenerate_scene():
+    """A small cloud plus the method's corner cases, each placed at a chosen
+    pixel and camera depth (input placement only)."""
+    g = scenes.uniform_gaussians(2000, seed=41)
+    cam = scenes.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 96, 80, 80.0)
+    Rm = cam.viewmat[:, :3].astype(np.float64)
+    tv = cam.viewmat[:, 3].astype(np.float64)
+
+    def world(u, v, z):
+        t = np.array([(u - cam.cx) * z / cam.fx, (v - cam.cy) * z / cam.fy, z])
+        return Rm.T @ (t - tv)
+
+    rows = []          # (mean, scale, opacity logit)
+    # an opaque stack on one pixel centre: 8 depths x 5 exact copies (depth
+    # ties broken by index), opacity ~1 (alpha clamped at 0.99), the pixel
+    # terminating after two blends
+    for k in range(8):
+        for _ in range(5):
+            rows.append((world(40.5, 36.5, 2.0 + 0.1 * k), 0.03, 9.0))
+    rows.append((world(48.0, 40.0, 3.0), 2.5, -1.0))          # covers every tile
+    for u in (16, 32, 48, 64, 80):                            # on tile corners
+        for v in (16, 32, 48, 64):
+            rows.append((world(u, v, 2.5), 0.01, 2.0))
+    for k in range(10):                                       # opacity under 1/255
+        rows.append((world(10.0 + 7 * k, 70.0, 2.2), 0.05, -7.0))
+    rows.append((world(60.0, 20.0, 0.2005), 0.002, 1.0))      # just past the near plane
+    rows.append((world(62.0, 22.0, 0.1995), 0.002, 1.0))      # just before it: culled
+    m = len(rows)
+    g.means[:m] = np.array([r[0] for r in rows], np.float32)
+    g.log_scales[:m] = np.log(np.array([[r[1]] * 3 for r in rows], np.float64)).astype(np.float32)
+    g.opacity_logit[:m] = np.array([r[2] for r in rows], np.float32)
+    return g, [cam]
+
+
+def test_degenerate_cases(rz):
+    """Early termination, the 0.99 clamp, exact depth ties, a frame-filling
+    splat, splats on tile corners, opacities under the floor and the near
+    plane, against the oracle."""
+    g, cams = _degenerate_scene()
+    tgt = scenes.target_image(80, 96, seed=43)
+    rast, views = _full_check(rz, g, cams, [tgt], dict(bg=(0.2, 0.4, 0.6)))
+    fp = views[0].fp32
+    assert fp["visible"][40] and fp["tiles"][40] == 30          # the frame-filling splat
+    assert fp["visible"][71] and not fp["visible"][72]          # the near plane
+    final_T = rast.splat_outputs()["final_T"].cpu().numpy().reshape(80, 96)
+    assert final_T[36, 40] <= 0.0101                            # one clamped blend, then stop
+
+
+def test_every_gaussian_masked(rz):
+    """M = 0 everywhere: the image is the background and only dL/dM (hence
+    the mask scores' gradient) is non-zero."""
+    g, cams, tgt = scenes.tiny_workload(3000)
+    gm = torch.zeros(g.n, dtype=torch.uint8, device="cuda")
+    rast, _ = _full_check(rz, g, cams, [tgt], dict(mask_mode=2, given_mask=gm,
+                                                   bg=(0.3, 0.6, 0.9)))
+    img = rast.forward(to_device(g), cams, rz.RasterConfig(mask_mode=2, given_mask=gm,
+                                                           bg=(0.3, 0.6, 0.9)))
+    torch.cuda.synchronize()
+    im = img.cpu().numpy().reshape(3, -1)
+    for c, b in enumerate((0.3, 0.6, 0.9)):
+        assert np.all(im[c] == np.float32(b))
