@@ -473,7 +473,9 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
             const int nchunks = (cnt + 31) >> 5;
             for (int ch = nchunks - 1; ch >= 0; --ch) {
                 const int jj = (ch << 5) + lane;
-                unsigned word = __ballot_sync(0xffffffffu, jj < cnt && ((sM[jj] >> warp) & 1u));
+                // the warp's splats of this chunk, up to its largest stop index
+                unsigned word = __ballot_sync(0xffffffffu, jj < cnt && pos0 + jj < wstop &&
+                                                               ((sM[jj] >> warp) & 1u));
                 while (word) {
                     const int hb = 31 - __clz(word);
                     word &= ~(1u << hb);
@@ -563,12 +565,12 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
             if (i >= cnt) continue;
             float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[i];
             const float4 B = sB[i];
-            // sum the slots of the warps whose list held the splat
-            // (a warp whose pixels all stop before this batch skipped it)
+            // sum the slots of the warps whose list held the splat (a warp
+            // skips the splats at or past its pixels' largest stop index)
             uint32_t wm = sM[i];
 #pragma unroll
             for (int w = 0; w < kRenderWarps; ++w)
-                if (pos0 >= s_wstop[w]) wm &= ~(1u << w);
+                if (pos0 + (uint32_t)i >= s_wstop[w]) wm &= ~(1u << w);
             float S[kAcc];
 #pragma unroll
             for (int q = 0; q < kAcc; ++q) S[q] = 0.0f;
