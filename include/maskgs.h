@@ -180,14 +180,20 @@ typedef struct {
  *     o if M = 1, -o if M = 0 (opacity o > 0, the mask in the sign);
  *     e_min, a skip threshold just below log2(1/(255 o)) for the exponent
  *     (1 if o < 1/255: the splat never reaches the floor); r, g, b; depth tz.
- *   tiles_touched[R] u32 (0 = culled), radius[R] i32 (pixels, 0 = culled),
+ *   tiles_touched[R] u32, the record's candidate tiles for the binning: its
+ *     whole 3-sigma rectangle (MG_BIN_RECT), or (MG_BIN_FILTERED) the tiles of
+ *     that rectangle that meet the bounding box of the region where the tile
+ *     filter can keep a tile -- a box computed in correctly rounded FP64 that
+ *     provably holds every tile the filter keeps, so no list changes; 0 = no
+ *     candidate (culled, or nothing of it can reach the floor in a tile);
+ *   radius[R] i32 (pixels, 0 = culled),
  *   clamp[R] u8 (bit c: colour channel c was clamped at 0),
  *   bin_record[R][12] (48 bytes, 16-byte aligned) of a visible record, for
  *   the binning: FP32 px, py, a, b, c (the 2D covariance [[a, b], [b, c]]),
  *   11.1 det, b / a, b / c (decision-path values), then u32 x0 | y0 << 16
- *   (first tile column and row of the rectangle), w (its width), the global
- *   id of its first tile, and the view's tiles per row gx; tile m of the
- *   rectangle (row-major) is first + (m / w) gx + m % w.
+ *   (first tile column and row of the candidate rectangle), w (its width),
+ *   the global id of its first tile, and the view's tiles per row gx; tile m
+ *   of the rectangle (row-major) is first + (m / w) gx + m % w.
  *   With MG_APPLY_OPACITY the stored opacity is M o (+0 for a masked splat,
  *   e_min = 1).
  * Per-Gaussian (n):
@@ -254,15 +260,16 @@ size_t mg_depth_order_workspace_bytes(int64_t n_records);
 
 /* Visits the R records in `order` (nullable: record order) and writes, for
  * position i, offsets[i] = sum_{j<i} tiles_touched[order[j]] (u32) and the
- * total K into *d_num_instances (device u64); then, for every visible record
- * r = order[i] and every tile of its rectangle (row-major), the key = global
- * tile id (u32) and the value r at offsets[i] + k -- or, with bin_mode
- * MG_BIN_FILTERED, the key 0xFFFFFFFF when the record's Gaussian stays under
- * the alpha floor at every pixel of that tile (its quadratic form above
- * 2 ln 255 at every pixel centre, tested in correctly rounded FP32 from
- * bin_record): such a pair is a no-op, and mg_sort drops it.  Instances beyond `capacity` are not written and raise
- * MG_ERR_CAPACITY with `required` = K.  workspace: device scratch of
- * mg_bin_workspace_bytes(R) bytes, any content. */
+ * total K into *d_num_instances (device u64); then, for every record
+ * r = order[i] and every tile of its candidate rectangle (row-major), the key
+ * = global tile id (u32) and the value r at offsets[i] + k -- or, with
+ * bin_mode MG_BIN_FILTERED, the key 0xFFFFFFFF when the record's Gaussian
+ * stays under the alpha floor at every pixel of that tile (its quadratic form
+ * above 2 ln 255 at every pixel centre, tested in correctly rounded FP32 from
+ * bin_record): such a pair is a no-op, and mg_sort drops it.  Instances
+ * beyond `capacity` are not written and raise MG_ERR_CAPACITY with
+ * `required` = K.  workspace: device scratch of mg_bin_workspace_bytes(R)
+ * bytes, any content. */
 mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32_t n_views,
                  const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
                  uint32_t *keys, uint32_t *vals, uint64_t capacity, uint64_t *d_num_instances,

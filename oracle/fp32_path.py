@@ -321,6 +321,67 @@ T_BIN = f32(11.1)
 REL_BIN = f32(1e-4)
 
 
+# ---------------------------------------------------------------------------
+# Candidate rectangle of the filtered binning.  A tile the filter keeps holds
+# a point d (pixel-centre offset from the mean) with computed
+# N <= 11.1 det + 1e-4 S, S = t1 + |2 t2| + t3.  N's rounding moves it by at
+# most 4 eps S (eps = 2^-24), and S <= 2 (c dx^2 + a dy^2) because b^2 < a c;
+# so every kept point satisfies d^T M d <= T with
+# M = [[c (1 - 2k), -b], [-b, a (1 - 2k)]], k = 1.0025e-4, T = 11.1 det
+# (1 + 1e-7).  With kappa = 0.9995 <= (1 - 2k)^2 the ellipse d^T M' d <= T,
+# M' = [[c sqrt(kappa), -b], [-b, a sqrt(kappa)]], contains it, and its
+# bounding box has half-widths sqrt(T a sqrt(kappa) / det') <=
+# sqrt(T a / det'), det' = kappa a c - b^2 (likewise y with c).  Evaluated in
+# correctly rounded FP32 in this order: det' only where it is at least 1e-3
+# a c (there its rounding error is below 2e-4 of it), the half-widths grown by
+# 1e-3 relative and 0.05 px (the rounding of det', of the filter's offsets and
+# of px -+ h), the box holds every kept tile: the candidates are the tiles of
+# the 3-sigma square that meet it.  Elsewhere the square stays.
+# ---------------------------------------------------------------------------
+CAND_KAPPA = f32(0.9995)
+CAND_MIN_DET = f32(1e-3)
+CAND_GROW = f32(1.001)
+CAND_MARGIN = f32(0.05)
+
+
+def candidate_rect(fp, tile_w=16, tile_h=16):
+    """The tiles of each Gaussian's 3-sigma rectangle that the tile filter can
+    keep: dict x0, x1, y0, y1 (inclusive, int64) and tiles (uint32); a
+    Gaussian with none gets tiles 0."""
+    vis = fp["tiles"] > 0
+    one = f32(1.0)
+    a = np.where(vis, fp["a"], one)
+    b = np.where(vis, fp["b"], f32(0.0))
+    c = np.where(vis, fp["c"], one)
+    tdet = T_BIN * np.where(vis, fp["det"], one)
+    px = np.where(vis, fp["px"], f32(0.0))
+    py = np.where(vis, fp["py"], f32(0.0))
+    with np.errstate(all="ignore"):
+        ac = a * c
+        detk = CAND_KAPPA * ac - b * b
+        tight = vis & (detk > CAND_MIN_DET * ac)
+        T = tdet * CAND_GROW
+        dk = np.where(tight, detk, one)
+        hx = np.sqrt((T * a) / dk) * CAND_GROW + CAND_MARGIN
+        hy = np.sqrt((T * c) / dk) * CAND_GROW + CAND_MARGIN
+        lx = np.floor((px - hx) / f32(tile_w))
+        ux = np.floor((px + hx) / f32(tile_w))
+        ly = np.floor((py - hy) / f32(tile_h))
+        uy = np.floor((py + hy) / f32(tile_h))
+    x0, x1, y0, y1 = (fp[k].astype(np.float64) for k in ("x0", "x1", "y0", "y1"))
+    x0 = np.where(tight, np.maximum(x0, lx.astype(np.float64)), x0)
+    x1 = np.where(tight, np.minimum(x1, ux.astype(np.float64)), x1)
+    y0 = np.where(tight, np.maximum(y0, ly.astype(np.float64)), y0)
+    y1 = np.where(tight, np.minimum(y1, uy.astype(np.float64)), y1)
+    ok = vis & (x0 <= x1) & (y0 <= y1)
+    x0i = np.where(ok, x0, 0).astype(np.int64)
+    x1i = np.where(ok, x1, -1).astype(np.int64)
+    y0i = np.where(ok, y0, 0).astype(np.int64)
+    y1i = np.where(ok, y1, -1).astype(np.int64)
+    tiles = ((x1i - x0i + 1) * (y1i - y0i + 1)).astype(np.uint32)
+    return dict(x0=x0i, x1=x1i, y0=y0i, y1=y1i, tiles=tiles)
+
+
 def tile_filter_params(fp):
     """Per Gaussian: (t det, b / a, b / c), correctly rounded FP32."""
     a, b, c, det = fp["a"], fp["b"], fp["c"], fp["det"]

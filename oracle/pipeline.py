@@ -120,6 +120,12 @@ def forward(g, cams, cfg: OracleConfig):
     for cam in cams:
         fp = fp32_path.project32(g.means, g.log_scales, g.quats, cam, cfg.tile_w, cfg.tile_h)
         gx, gy = fp["grid"]
+        # the binning's candidates: the whole 3-sigma rectangle, or (tile
+        # filter) its tiles that the filter can keep; the square stays in
+        # rect_tiles
+        fp["rect_tiles"] = fp["tiles"]
+        if cfg.bin_mode == 0:
+            fp.update(fp32_path.candidate_rect(fp, cfg.tile_w, cfg.tile_h))
         keys, vals, offsets, K, keep = binning.emit_instances(fp, gx, cfg.tile_w, cfg.tile_h)
         if cfg.bin_mode == 1:
             keep = np.ones_like(keep)

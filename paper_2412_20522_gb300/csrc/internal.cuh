@@ -326,6 +326,46 @@ __device__ __forceinline__ bool bin_tile_hit(float px, float py, float a, float 
     return hit;
 }
 
+// Candidate tiles of the filtered binning: the tiles of the 3-sigma
+// rectangle [x0, x1] x [y0, y1] that meet the bounding box of
+// d^T M' d <= T, M' = [[c sqrt(kappa), -b], [-b, a sqrt(kappa)]],
+// T = 11.1 det, an ellipse that holds every point where the filter can keep
+// a tile (its test N <= 11.1 det + 1e-4 S, N rounded by at most 4 eps S,
+// S <= 2 (c dx^2 + a dy^2), so kappa = 0.9995 <= (1 - 2.005e-4)^2 covers the
+// slack).  Box half-widths sqrt(T a / det'), sqrt(T c / det'),
+// det' = kappa a c - b^2, in correctly rounded FP32 in a fixed order
+// (reproducible bit for bit), only where det' >= 1e-3 a c (its rounding then
+// stays below 2e-4 of it), grown by 1e-3 relative and 0.05 px (the rounding
+// of det', of the filter's offsets and of px -+ h); elsewhere the rectangle
+// stays.  False when no tile remains.
+constexpr float kCandKappa = 0.9995f;
+constexpr float kCandMinDet = 1e-3f;
+constexpr float kCandGrow = 1.001f;
+constexpr float kCandMargin = 0.05f;
+
+__device__ __forceinline__ bool candidate_rect(float px, float py, float a, float b, float c,
+                                               float tdet, int tw, int th, int &x0, int &x1,
+                                               int &y0, int &y1) {
+    const float ac = __fmul_rn(a, c);
+    const float detk = __fsub_rn(__fmul_rn(kCandKappa, ac), __fmul_rn(b, b));
+    if (!(detk > __fmul_rn(kCandMinDet, ac))) return true;
+    const float T = __fmul_rn(tdet, kCandGrow);
+    const float hx = __fadd_rn(
+        __fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(T, a), detk)), kCandGrow), kCandMargin);
+    const float hy = __fadd_rn(
+        __fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(T, c), detk)), kCandGrow), kCandMargin);
+    const float fx0 = fmaxf((float)x0, floorf(__fdiv_rn(__fsub_rn(px, hx), (float)tw)));
+    const float fx1 = fminf((float)x1, floorf(__fdiv_rn(__fadd_rn(px, hx), (float)tw)));
+    const float fy0 = fmaxf((float)y0, floorf(__fdiv_rn(__fsub_rn(py, hy), (float)th)));
+    const float fy1 = fminf((float)y1, floorf(__fdiv_rn(__fadd_rn(py, hy), (float)th)));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+    x0 = (int)fx0;
+    x1 = (int)fx1;
+    y0 = (int)fy0;
+    y1 = (int)fy1;
+    return true;
+}
+
 __host__ __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int64_t t) {
     int v = 0;
     while (v + 1 < vt.n_views && vt.tile_off[v + 1] <= t) ++v;

@@ -268,16 +268,24 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
             if (out.depth_key != nullptr) out.depth_key[r] = 0xFFFFFFFFu;
             continue;
         }
-        out.tiles_touched[r] = (uint32_t)((S.x1 - S.x0 + 1) * (S.y1 - S.y0 + 1));
+        // the binning's candidate tiles: the whole 3-sigma rectangle, or (tile
+        // filter) its tiles that the filter can keep
+        int x0 = S.x0, x1 = S.x1, y0 = S.y0, y1 = S.y1;
+        const float tdet = ml(kBinThreshold, S.det);
+        const bool binned = cfg.bin_mode != MG_BIN_FILTERED ||
+                            candidate_rect(S.px, S.py, S.a, S.b, S.c, tdet, vt.tile_w,
+                                           vt.tile_h, x0, x1, y0, y1);
+        out.tiles_touched[r] = binned ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
         // depth-order key: the float bits of tz > 0 order like the values
-        if (out.depth_key != nullptr) out.depth_key[r] = __float_as_uint(S.tz);
+        if (out.depth_key != nullptr)
+            out.depth_key[r] = binned ? __float_as_uint(S.tz) : 0xFFFFFFFFu;
         // binning record: tile-filter inputs (decision path) and the rectangle
         float4 *br = reinterpret_cast<float4 *>(out.bin_record) + 3 * r;
         br[0] = make_float4(S.px, S.py, S.a, S.b);
-        br[1] = make_float4(S.c, ml(kBinThreshold, S.det), dv(S.b, S.a), dv(S.b, S.c));
+        br[1] = make_float4(S.c, tdet, dv(S.b, S.a), dv(S.b, S.c));
         reinterpret_cast<uint4 *>(br)[2] =
-            make_uint4((uint32_t)S.x0 | ((uint32_t)S.y0 << 16), (uint32_t)(S.x1 - S.x0 + 1),
-                       (uint32_t)(vt.tile_off[v] + (int64_t)S.y0 * vt.gx[v] + S.x0),
+            make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)(x1 - x0 + 1),
+                       (uint32_t)(vt.tile_off[v] + (int64_t)y0 * vt.gx[v] + x0),
                        (uint32_t)vt.gx[v]);
         out.radius[r] = (int32_t)S.rf;
         float ux, uy, l1, l2;

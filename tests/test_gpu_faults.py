@@ -65,6 +65,7 @@ def test_non_finite_gaussians_are_culled_like_the_oracle():
     torch.cuda.synchronize()
     with np.errstate(invalid="ignore"):
         fp = fp32_path.project32(g.means, g.log_scales, g.quats, cams[0], 16, 16)
+        fp.update(fp32_path.candidate_rect(fp, 16, 16))
     so = rast.splat_outputs()
     assert np.array_equal(so["tiles"].cpu().numpy().view(np.uint32), fp["tiles"])
     assert np.array_equal(so["radius"].cpu().numpy(), fp["radius"])

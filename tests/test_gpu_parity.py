@@ -58,7 +58,7 @@ def _check_discrete(rast, views, M, cams):
     # depth order of all records (all views), and the scan in that order
     tiles_all = np.concatenate([v.fp32["tiles"] for v in views]).astype(np.int64)
     order = binning.depth_order(np.concatenate([v.fp32["depth_bits"] for v in views]),
-                                np.concatenate([v.fp32["visible"] for v in views]))
+                                np.concatenate([v.fp32["tiles"] > 0 for v in views]))
     assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order), "depth order differs"
     exp_off = np.concatenate([[0], np.cumsum(tiles_all[order])[:-1]]) if order.size else order
     assert np.array_equal(so["offsets"].cpu().numpy().view(np.uint32).astype(np.int64), exp_off), \
@@ -289,7 +289,7 @@ def test_degenerate_cases(rz):
     tgt = scenes.target_image(80, 96, seed=43)
     rast, views = _full_check(rz, g, cams, [tgt], dict(bg=(0.2, 0.4, 0.6)))
     fp = views[0].fp32
-    assert fp["visible"][40] and fp["tiles"][40] == 30          # the frame-filling splat
+    assert fp["visible"][40] and fp["rect_tiles"][40] == 30     # the frame-filling splat
     assert fp["visible"][71] and not fp["visible"][72]          # the near plane
     final_T = rast.splat_outputs()["final_T"].cpu().numpy().reshape(80, 96)
     assert final_T[36, 40] <= 0.0101                            # one clamped blend, then stop

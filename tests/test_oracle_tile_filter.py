@@ -79,3 +79,74 @@ def test_centre_inside_tile_is_kept():
     # a tiny Gaussian two tiles away is dropped
     tx2 = np.full(n, 3)
     assert not fp.tile_hit(px, py, d["a"], d["b"], d["c"], tdet, rba, rbc, tx2, ty, 16, 16).any()
+
+
+def _random_splats(n, seed, tw=16, th=16, gx=12, gy=10):
+    """Random 2D splats (round to needle-like) with their 3-sigma tile
+    rectangles on a gx x gy grid, as the decision path returns them."""
+    d, px, py, _, _ = _random_pairs(n, seed)
+    f32 = np.float32
+    a, b, c = d["a"], d["b"], d["c"]
+    mid = f32(0.5) * (a + c)
+    hd = f32(0.5) * (a - c)
+    lam = mid + np.sqrt(np.maximum(f32(0.1), hd * hd + b * b))
+    rf = np.ceil(f32(3.0) * np.sqrt(lam))
+    x0 = np.maximum(np.floor((px - rf) / f32(tw)), f32(0.0))
+    x1 = np.minimum(np.floor((px + rf) / f32(tw)), f32(gx - 1))
+    y0 = np.maximum(np.floor((py - rf) / f32(th)), f32(0.0))
+    y1 = np.minimum(np.floor((py + rf) / f32(th)), f32(gy - 1))
+    ok = (x0 <= x1) & (y0 <= y1)
+    d.update(px=px, py=py, x0=np.where(ok, x0, 0).astype(np.int64),
+             x1=np.where(ok, x1, -1).astype(np.int64), y0=np.where(ok, y0, 0).astype(np.int64),
+             y1=np.where(ok, y1, -1).astype(np.int64))
+    d["tiles"] = ((d["x1"] - d["x0"] + 1) * (d["y1"] - d["y0"] + 1)).astype(np.uint32)
+    return d
+
+
+def test_candidate_rectangle_holds_every_kept_tile():
+    """Brute force over every tile of each 3-sigma rectangle: the filter keeps
+    no tile outside the candidate rectangle, which lies inside the square."""
+    for tw, th in ((16, 16), (8, 32), (32, 8)):
+        d = _random_splats(3000, seed=11 + tw, tw=tw, th=th, gx=240 // tw + 1, gy=240 // th + 1)
+        cand = fp.candidate_rect(d, tw, th)
+        tdet, rba, rbc = fp.tile_filter_params(d)
+        n_rect = n_cand = n_kept = 0
+        for i in range(len(d["a"])):
+            if d["tiles"][i] == 0:
+                continue
+            tys, txs = np.meshgrid(np.arange(d["y0"][i], d["y1"][i] + 1),
+                                   np.arange(d["x0"][i], d["x1"][i] + 1), indexing="ij")
+            tx, ty = txs.ravel(), tys.ravel()
+            k = np.full(tx.shape, i)
+            hit = fp.tile_hit(d["px"][k], d["py"][k], d["a"][k], d["b"][k], d["c"][k], tdet[k],
+                              rba[k], rbc[k], tx, ty, tw, th)
+            inside = ((tx >= cand["x0"][i]) & (tx <= cand["x1"][i]) &
+                      (ty >= cand["y0"][i]) & (ty <= cand["y1"][i]))
+            assert not (hit & ~inside).any(), (i, tw, th)
+            assert cand["x0"][i] >= d["x0"][i] or cand["tiles"][i] == 0
+            n_rect += tx.size
+            n_cand += int(cand["tiles"][i])
+            n_kept += int(hit.sum())
+        assert n_kept <= n_cand < n_rect
+
+
+def test_candidate_rectangle_of_round_splats_is_the_kept_box():
+    """A round splat's kept region is a disc of radius sqrt(11.1 (a c - b^2)
+    a / det) = sqrt(11.1 a): its candidate rectangle spans the tiles that
+    disc's box meets, plus at most the growth margins."""
+    f32 = np.float32
+    a = np.array([4.0, 25.0, 100.0], f32)
+    d = dict(a=a, b=np.zeros(3, f32), c=a.copy(), det=(a * a).astype(f32),
+             px=np.array([100.3, 64.0, 130.7], f32), py=np.array([90.1, 64.0, 40.2], f32),
+             x0=np.zeros(3, np.int64), x1=np.full(3, 20, np.int64),
+             y0=np.zeros(3, np.int64), y1=np.full(3, 20, np.int64))
+    d["tiles"] = np.full(3, 21 * 21, np.uint32)
+    cand = fp.candidate_rect(d, 16, 16)
+    r = np.sqrt(11.1 * a.astype(np.float64) / 0.9995)
+    for i in range(3):
+        lo = np.floor((d["px"][i] - r[i]) / 16.0)
+        hi = np.floor((d["px"][i] + r[i]) / 16.0)
+        assert cand["x0"][i] <= lo and cand["x1"][i] >= hi
+        grown = r[i] * 1.001 * 1.001 + 0.06                   # the growth margins
+        assert cand["x0"][i] >= np.floor((d["px"][i] - grown) / 16.0)
+        assert cand["x1"][i] <= np.floor((d["px"][i] + grown) / 16.0)
