@@ -412,7 +412,10 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
 
     static_assert(kPix == 2, "the backward's moment sums assume a column pair");
     const float fpx = (float)ti.px[0] + 0.5f, fpy0 = (float)ti.py[0] + 0.5f;
-    float T[kPix], g0[kPix], g1[kPix], g2[kPix], bc0[kPix], bc1[kPix], bc2[kPix];
+    // gb = g . b, g = dL/dC of the pixel and b the colour behind (Appendix A's
+    // b_{i+1} with the background folded in): the backward needs b only in
+    // g . (c_i - b), so the scalar replaces the three channels
+    float T[kPix], g0[kPix], g1[kPix], g2[kPix], gb[kPix];
     uint32_t stop[kPix];
     const mg_camera &Cm = vt.cam[ti.v];
     const int64_t HW = (int64_t)Cm.width * Cm.height;
@@ -430,9 +433,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
             g1[k] = gi[HW + ti.pix[k]];
             g2[k] = gi[2 * HW + ti.pix[k]];
         }
-        bc0[k] = bg0;                          // colour behind, background folded in
-        bc1[k] = bg1;
-        bc2[k] = bg2;
+        gb[k] = fmaf(g2[k], bg2, fmaf(g1[k], bg1, g0[k] * bg0));   // b_{N+1} = background
     }
     uint32_t tstop = 0;
 #pragma unroll
@@ -503,8 +504,8 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
 #pragma unroll
                         for (int k = 0; k < kPix; ++k) {
                             if (!on[k]) continue;
-                            const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
-                                              g2[k] * (c.z - bc2[k]);
+                            const float gcb =
+                                fmaf(g2[k], c.z, fmaf(g1[k], c.y, g0[k] * c.x)) - gb[k];
                             v[9] = fmaf(al[k] * T[k], gcb, v[9]);   // Eq. 6 + Appendix A
                         }
                     } else {
@@ -514,17 +515,15 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                             if (!on[k]) continue;
                             const float alpha = al[k];
                             const float Tj = __fdividef(T[k], 1.0f - alpha);
-                            const float gcb = g0[k] * (c.x - bc0[k]) + g1[k] * (c.y - bc1[k]) +
-                                              g2[k] * (c.z - bc2[k]);
+                            const float gcb =
+                                fmaf(g2[k], c.z, fmaf(g1[k], c.y, g0[k] * c.x)) - gb[k];
                             const float wt = alpha * Tj;
                             const float dm = wt * gcb;
                             v[9] += dm;                                   // Eq. 6 + Appendix A
                             v[6] = fmaf(wt, g0[k], v[6]);
                             v[7] = fmaf(wt, g1[k], v[7]);
                             v[8] = fmaf(wt, g2[k], v[8]);
-                            bc0[k] = fmaf(alpha, c.x - bc0[k], bc0[k]);
-                            bc1[k] = fmaf(alpha, c.y - bc1[k], bc1[k]);
-                            bc2[k] = fmaf(alpha, c.z - bc2[k], bc2[k]);
+                            gb[k] = fmaf(alpha, gcb, gb[k]);  // b_i = b_{i+1} + alpha (c_i - b_{i+1})
                             T[k] = Tj;
                             // dL/dalpha * alpha (0 through the 0.99 clamp)
                             const float m = ar[k] < kAlphaMax ? dm : 0.0f;
