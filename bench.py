@@ -126,9 +126,9 @@ PROFILE_KERNEL = {"render_bwd": ("render_backward", "render.cu"),
                   "preprocess_bwd": ("preprocess_backward", "preprocess.cu")}
 
 
-def _profiled_traffic(stage):
-    """DRAM bytes per launch from the committed ncu summary of the stage's
-    kernel, if that summary was taken on the current source (else None)."""
+def _profile_text(stage):
+    """The committed ncu summary of the stage's kernel, if it was taken on the
+    current source (else None)."""
     import hashlib
     import re
     if stage not in PROFILE_KERNEL:
@@ -139,12 +139,31 @@ def _profiled_traffic(stage):
         return None
     text = open(path).read()
     m = re.search(r"sha256\[:16\] at capture: `([0-9a-f]+)`", text)
-    t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
     cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2412_20522_gb300", "csrc", src), "rb")
                          .read()).hexdigest()[:16]
-    if not m or not t or m.group(1) != cur:
+    return text if m and m.group(1) == cur else None
+
+
+def _profiled_traffic(stage):
+    """DRAM bytes per launch from the committed ncu summary (None if stale)."""
+    import re
+    text = _profile_text(stage)
+    t = re.search(r"traffic_bytes_per_launch \| (\d+)", text) if text else None
+    return int(t.group(1)) if t else None
+
+
+def _profiled_issue(stage, sms):
+    """Warp instructions issued per cycle over all SMs, from the committed ncu
+    summary, as a fraction of the SMs' issue capacity (one per SM sub-partition
+    per cycle, four per SM); None if the summary is stale."""
+    import re
+    text = _profile_text(stage)
+    t = re.search(r"sm__inst_executed\.sum\.per_cycle_active`\) \| ([0-9.]+)", text) if text else None
+    if not t:
         return None
-    return int(t.group(1))
+    ipc = float(t.group(1))
+    return {"warp_inst_per_cycle": ipc, "capacity": 4 * sms, "frac": ipc / (4 * sms),
+            "source": "ncu summary in profiles/ (same source)"}
 
 
 def _peaks():
@@ -362,6 +381,10 @@ def run_ours(args):
                 "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)",
                 "flops_basis": "fragments of the 3-sigma rectangle tile lists up to each "
                                "pixel's stop (the method's walk)"}
+        # the kernels are bound by instruction issue: its utilisation
+        issue = _profiled_issue(dom, sms)
+        if issue is not None:
+            roof["issue"] = issue
         if dom == "render_bwd":
             ex = flops_bwd_exec / (stage_ms[dom] * 1e-3) / 1e12
             roof["executed"] = {"achieved": ex, "frac": ex / fp32_peak_tflops,
