@@ -36,7 +36,7 @@ constexpr int kScanThreads = 256, kScanItems = 8, kScanPart = kScanThreads * kSc
 // once, a partition's look-back ends at the nearest inclusive prefix, which
 // spreads about a window per round trip -- fewer, larger partitions shorten
 // that chain (one digit per thread for the first 256 threads).
-constexpr int kSortThreads = 512, kSortItems = 12, kSortPart = kSortThreads * kSortItems;
+constexpr int kSortThreads = 512, kSortItems = 10, kSortPart = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValMask = (1u << 30) - 1u;
 constexpr int kMaxPasses = 8;

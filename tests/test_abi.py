@@ -61,8 +61,8 @@ def test_host_only_helpers(lib):
     cfg.tile_w, cfg.tile_h = 64, 4
     assert abi.mg_total_tiles(views, 1, cfg) == -1          # no 8x8 warp blocks
     assert abi.mg_bin_workspace_bytes(1_200_000) > 8 * (1_200_000 // 2048)
-    # two look-back status arrays of 256 digits per partition of 6144 keys
-    assert abi.mg_sort_workspace_bytes(10_000_000, 46) > 2 * 256 * 4 * (10_000_000 // 6144)
+    # two look-back status arrays of 256 digits per partition of 5120 keys
+    assert abi.mg_sort_workspace_bytes(10_000_000, 46) > 2 * 256 * 4 * (10_000_000 // 5120)
 
 
 def test_bad_arguments_rejected_on_host(lib):
