@@ -176,6 +176,81 @@ __device__ __forceinline__ void splat_fp32(const mg_camera &C, int tw, int th, i
                 tile_rect(S.px, S.py, rf, tw, th, gx, gy, S.x0, S.x1, S.y0, S.y1);
 }
 
+// The pieces of the splat the backward differentiates through (P = J W R S,
+// its factors, the normalised quaternion, t_z, and Sigma_bar's a, b, c, det,
+// mid, disc), in ordinary contracted FP32 -- the gradient needs no bit-exact
+// rounding.  The one decision on this chain, whether the Jacobian's point was
+// clamped, is taken exactly as in the forward (the correctly rounded ux, uy
+// against the same limits), so both use the same branch.
+__device__ __forceinline__ void splat_grad_pieces(const mg_camera &C, float x, float y, float z,
+                                                  const float ls[3], const float q[4],
+                                                  Splat32 &S) {
+    const float *V = C.viewmat;
+    const float tx = ad(dot3(V[0], x, V[1], y, V[2], z), V[3]);
+    const float ty = ad(dot3(V[4], x, V[5], y, V[6], z), V[7]);
+    S.tz = ad(dot3(V[8], x, V[9], y, V[10], z), V[11]);
+    S.tzs = S.tz > C.near_plane ? S.tz : 1.0f;
+    S.ux = dv(tx, S.tzs);
+    S.uy = dv(ty, S.tzs);
+    const float tanx = dv(ml((float)C.width, 0.5f), C.fx);
+    const float tany = dv(ml((float)C.height, 0.5f), C.fy);
+    const float limx = ml(1.3f, tanx), limy = ml(1.3f, tany);
+    const float cux = fminf(limx, fmaxf(-limx, S.ux));
+    const float cuy = fminf(limy, fmaxf(-limy, S.uy));
+    S.clampx = cux != S.ux;
+    S.clampy = cuy != S.uy;
+
+    S.s[0] = __expf(ls[0]);
+    S.s[1] = __expf(ls[1]);
+    S.s[2] = __expf(ls[2]);
+    const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const float inr = rsqrtf(n2 > 0.0f ? n2 : 1.0f);
+    S.nrm = 1.0f / inr;
+    const float w = q[0] * inr, qx = q[1] * inr, qy = q[2] * inr, qz = q[3] * inr;
+    S.qn[0] = w; S.qn[1] = qx; S.qn[2] = qy; S.qn[3] = qz;
+    S.R[0][0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    S.R[0][1] = 2.0f * (qx * qy - w * qz);
+    S.R[0][2] = 2.0f * (qx * qz + w * qy);
+    S.R[1][0] = 2.0f * (qx * qy + w * qz);
+    S.R[1][1] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    S.R[1][2] = 2.0f * (qy * qz - w * qx);
+    S.R[2][0] = 2.0f * (qx * qz - w * qy);
+    S.R[2][1] = 2.0f * (qy * qz + w * qx);
+    S.R[2][2] = 1.0f - 2.0f * (qx * qx + qy * qy);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) S.M[j][k] = S.R[j][k] * S.s[k];
+
+    S.txc = cux * S.tzs;
+    S.tyc = cuy * S.tzs;
+    const float itz = __fdividef(1.0f, S.tzs);
+    const float j00 = C.fx * itz, j11 = C.fy * itz;
+    const float j02 = -C.fx * S.txc * itz * itz, j12 = -C.fy * S.tyc * itz * itz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        S.T[0][k] = j00 * V[k] + j02 * V[8 + k];
+        S.T[1][k] = j11 * V[4 + k] + j12 * V[8 + k];
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            S.P[i][k] = S.T[i][0] * S.M[0][k] + S.T[i][1] * S.M[1][k] + S.T[i][2] * S.M[2][k];
+    const float n0 = S.P[0][0] * S.P[0][0] + S.P[0][1] * S.P[0][1] + S.P[0][2] * S.P[0][2];
+    const float n1 = S.P[1][0] * S.P[1][0] + S.P[1][1] * S.P[1][1] + S.P[1][2] * S.P[1][2];
+    S.a = n0 + kLowpass;
+    S.b = S.P[0][0] * S.P[1][0] + S.P[0][1] * S.P[1][1] + S.P[0][2] * S.P[1][2];
+    S.c = n1 + kLowpass;
+    const float m01 = S.P[0][0] * S.P[1][1] - S.P[0][1] * S.P[1][0];
+    const float m02 = S.P[0][0] * S.P[1][2] - S.P[0][2] * S.P[1][0];
+    const float m12 = S.P[0][1] * S.P[1][2] - S.P[0][2] * S.P[1][1];
+    S.det = m01 * m01 + m02 * m02 + m12 * m12 + kLowpass * (n0 + n1) + kLowpass * kLowpass;
+    S.mid = 0.5f * (S.a + S.c);
+    const float hd = 0.5f * (S.a - S.c);
+    S.disc = hd * hd + S.b * S.b;
+}
+
 // Major axis (cos, sin) and the two eigenvalues of [[a, b], [b, c]] from the
 // Cauchy-Binet determinant; continuous, so ordinary fast arithmetic.
 __device__ __forceinline__ void eigen2(const Splat32 &S, float &uxo, float &uyo, float &lam1,
@@ -570,7 +645,7 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
             d_op += g1.y;
             const mg_camera &C = vt.cam[v];
             Splat32 S;
-            splat_fp32(C, vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z, ls, q, S);
+            splat_grad_pieces(C, x, y, z, ls, q, S);
             const float *V = C.viewmat;
             float dL_dt[3] = {0, 0, 0};   // camera-space centre
 
