@@ -464,12 +464,12 @@ def run_ours(args):
     if not args.no_forms and ws == 1:
         # the single-GPU forms (multi-view graph, storage, scene batch, next
         # rows); a multi-rank run times the replicated step only
-        line["forms"] = run_forms(dev, g, cams, target, ms, W * H)
+        line["forms"] = run_forms(dev, g, cams, target, eager_ms, W * H)
         line["forms"]["next_rows"] = run_next_rows(dev, g, cams, target, ms, peaks)
         line["forms"]["tiny_c1"] = tiny_workload_times(dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(steps=1)
-        line["cpu_baseline"]["tiny_workload_seconds"] = tiny_workload_oracle_seconds()
+        line["cpu_baseline"]["tiny_workload"] = tiny_workload_oracle_seconds()
     if clk is not None and clk["samples"] < 3:
         line["clocks"]["note"] = "timed region shorter than three 100 ms samples"
     if rank == 0:
@@ -747,13 +747,27 @@ def tiny_workload_times(dev, steps=50):
 
 def tiny_workload_oracle_seconds():
     """The oracle's masked forward+backward of the tiny configuration on the
-    host cores (CPU-baseline leg)."""
+    host cores (CPU-baseline leg), and on one core (a fresh process with one
+    OpenMP thread and one torch thread)."""
     from oracle import pipeline
     from paper_2412_20522_gb300 import scenes
     g, cams, tgt = scenes.tiny_workload()
     t0 = time.perf_counter()
     pipeline.forward_backward_l1(g, cams, [tgt], pipeline.OracleConfig())
-    return time.perf_counter() - t0
+    all_cores = time.perf_counter() - t0
+    code = ("import sys, time; sys.path.insert(0, %r); import torch; torch.set_num_threads(1); "
+            "from oracle import pipeline; from paper_2412_20522_gb300 import scenes; "
+            "g, cams, tgt = scenes.tiny_workload(); t0 = time.perf_counter(); "
+            "pipeline.forward_backward_l1(g, cams, [tgt], pipeline.OracleConfig()); "
+            "print(time.perf_counter() - t0)" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                             timeout=600, env=env)
+        one_core = float(res.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        one_core = None
+    return {"seconds_all_cores": all_cores, "cores": os.cpu_count(), "seconds_one_core": one_core}
 
 
 def run_reference(args):
