@@ -353,6 +353,19 @@ mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
                     int32_t n_views, const mg_raster_cfg *cfg, float *image, float *final_T,
                     uint32_t *n_contrib, uint64_t *frag_count, mg_stream_t stream);
 
+/* mg_render with the L1 render loss taken in the same kernel, from the
+ * colours it has just composited (no second pass over the image): as
+ * mg_render (without fragment counters), plus, for every view v and value i
+ * of its image, dL_dimage[i] = sign(image[i] - target[i]) / (3 W_v H_v)
+ * (sign(0) = 0) and *loss (device f32) += sum_v mean |image_v - target_v| --
+ * the results of mg_l1_loss_grad, the loss summed in another order.  The
+ * caller zeroes *loss.  target, dL_dimage: f32[sum_v 3 W_v H_v]. */
+mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
+                       const uint32_t *ranges, const uint32_t *tile_order,
+                       const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                       float *image, float *final_T, uint32_t *n_contrib, const float *target,
+                       float *dL_dimage, float *loss, mg_stream_t stream);
+
 /* ---- 5. L1 render loss ------------------------------------------------------ */
 /* For count = sum_v 3 W_v H_v values: dL_dimage[i] = sign(image[i] - target[i])
  * / (3 W_v H_v) of the view holding i (sign(0) = 0), and *loss (device f32)

@@ -24,7 +24,7 @@ MG_GRAD2D_FLOATS = 12
 
 EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes", "mg_bin",
             "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
-            "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render",
+            "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render", "mg_render_l1",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
             "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
@@ -122,6 +122,8 @@ def load(build_if_missing: bool = True):
         "mg_total_tiles": (C.c_int64, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_render": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
                            _P(mg_raster_cfg), vp, vp, vp, vp, vp]),
+        "mg_render_l1": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
+                              _P(mg_raster_cfg), vp, vp, vp, vp, vp, vp, vp]),
         "mg_tile_order": (st, [vp, C.c_int64, vp, vp]),
         "mg_l1_loss_grad": (st, [vp, vp, _P(mg_view), C.c_int32, vp, vp, vp]),
         "mg_render_backward": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
@@ -242,6 +244,14 @@ def mg_render(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, imag
                                          ptr(tile_order), views, n_views, C.byref(cfg),
                                          ptr(image), ptr(final_T), ptr(n_contrib),
                                          ptr(frag_count), stream))
+
+
+def mg_render_l1(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, image, final_T,
+                 n_contrib, target, dL_dimage, loss, stream):
+    _check("mg_render_l1", load().mg_render_l1(
+        C.byref(splats), ptr(sorted_vals), ptr(ranges), ptr(tile_order), views, n_views,
+        C.byref(cfg), ptr(image), ptr(final_T), ptr(n_contrib), ptr(target), ptr(dL_dimage),
+        ptr(loss), stream))
 
 
 def mg_l1_loss_grad(image, target, views, n_views, dL_dimage, loss, stream):

@@ -62,9 +62,8 @@ class GraphStep:
             self.loss = self._step()
 
     def _step(self):
-        img = self.rast.forward(self.params, self.cams, self.cfg, view_ranges=self.view_ranges,
-                                check=False)
-        loss, dimg = self.rast.l1_loss_grad(img, self.target)
+        img, loss, dimg = self.rast.forward_l1(self.params, self.cams, self.cfg, self.target,
+                                               view_ranges=self.view_ranges, check=False)
         self.rast.backward(dimg, self.grads)
         self.image = img
         return loss

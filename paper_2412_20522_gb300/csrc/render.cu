@@ -159,18 +159,33 @@ __device__ __forceinline__ bool all_done(const bool *done) {
     return a;
 }
 
+__device__ __forceinline__ float l1_sign(float d, float inv) {
+    return d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // COUNT = true adds per-fragment counters (an untimed diagnostic variant):
 // [0] positions walked (sum of n_contrib), [1] unmasked positions walked,
 // [2] unmasked splats blended, [3] masked splats above the alpha floor.
 // They count every walked position, culled or not.  AUX = false is the
 // inference form: the image only, no final_T / n_contrib for a backward.
-template <bool COUNT, bool AUX = true>
+// L1 = true also takes the L1 render loss in the epilogue, from the colours
+// in registers: dL/dimage = sign(C - target) / (3 W H) and one atomic per CTA
+// adding the CTA's sum of |C - target| / (3 W H) to *loss.
+template <bool COUNT, bool AUX = true, bool L1 = false>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ tile_order,
                       float bg0, float bg1, float bg2,
                       float *__restrict__ image, float *__restrict__ final_T,
-                      uint32_t *__restrict__ n_contrib, unsigned long long *frag_count) {
+                      uint32_t *__restrict__ n_contrib, unsigned long long *frag_count,
+                      const float *__restrict__ target = nullptr,
+                      float *__restrict__ dL_dimage = nullptr, float *loss = nullptr) {
     __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
     __shared__ uint8_t sM[kBatch];
     __shared__ unsigned long long s_frags[4];
@@ -291,23 +306,39 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
     const mg_camera &Cm = vt.cam[ti.v];
     const int64_t HW = (int64_t)Cm.width * Cm.height;
     float *img = image + 3 * vt.pix_off[ti.v];
+    const float inv = 1.0f / (float)(3 * HW);
+    float lsum = 0.0f;
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
         if (!ti.inside[k]) continue;
-        img[ti.pix[k]] = C0[k] + T[k] * bg0;
-        img[HW + ti.pix[k]] = C1[k] + T[k] * bg1;
-        img[2 * HW + ti.pix[k]] = C2[k] + T[k] * bg2;
+        const float c[3] = {C0[k] + T[k] * bg0, C1[k] + T[k] * bg1, C2[k] + T[k] * bg2};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            img[ch * HW + ti.pix[k]] = c[ch];
+            if (L1) {
+                const int64_t e = 3 * vt.pix_off[ti.v] + ch * HW + ti.pix[k];
+                const float d = c[ch] - target[e];
+                dL_dimage[e] = l1_sign(d, inv);
+                lsum += fabsf(d);
+            }
+        }
         if (AUX) {
             final_T[vt.pix_off[ti.v] + ti.pix[k]] = T[k];
             n_contrib[vt.pix_off[ti.v] + ti.pix[k]] = stop[k];
         }
     }
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
+    if (L1) {
+        __shared__ float s_loss[kRenderThreads / 32];
+        lsum = warp_sum(lsum);
+        if (lane == 0) s_loss[warp] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+            for (int w = 0; w < kRenderThreads / 32; ++w) t += s_loss[w];
+            atomicAdd(loss, t * inv);
+        }
+    }
 }
 
 // Warp sums of a splat's ten gradient terms by halving exchanges that split
@@ -614,10 +645,6 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     }
 }
 
-__device__ __forceinline__ float l1_sign(float d, float inv) {
-    return d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
-}
-
 // One view per blockIdx.y; 128-bit loads and stores over the view's aligned
 // body, scalar over its (at most 3 + 3) unaligned ends.
 __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ image,
@@ -669,6 +696,29 @@ __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ imag
 }  // namespace mg
 
 using namespace mg;
+
+extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
+                                  const uint32_t *ranges, const uint32_t *tile_order,
+                                  const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                                  float *image, float *final_T, uint32_t *n_contrib,
+                                  const float *target, float *dL_dimage, float *loss,
+                                  mg_stream_t stream) {
+    if (!splats || !splats->record || !sorted_vals || !ranges || !image || !final_T ||
+        !n_contrib || !target || !dL_dimage || !loss)
+        return MG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats->record) & 15u) != 0) return MG_ERR_INVALID_ARG;
+    ViewTable vt;
+    mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
+    if (st != MG_OK) return st;
+    const int64_t tiles = vt.tile_off[n_views];
+    if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
+    const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
+    render_forward_kernel<false, true, true>
+        <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
+            final_T, n_contrib, nullptr, target, dL_dimage, loss);
+    return mg_host::launch_status();
+}
 
 extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
                                const uint32_t *ranges, const uint32_t *tile_order,

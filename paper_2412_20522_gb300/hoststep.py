@@ -79,9 +79,9 @@ class HostPipeline:
             self.compute.wait_event(self.ev_in[b])
             if self.ev_out[b] is not None:
                 self.compute.wait_event(self.ev_out[b])
-            img = self.rast.forward(self.params[b], self.cams, self.cfg,
-                                    view_ranges=self.view_ranges, check=False)
-            loss, dimg = self.rast.l1_loss_grad(img, self.target[b])
+            img, loss, dimg = self.rast.forward_l1(self.params[b], self.cams, self.cfg,
+                                                   self.target[b], view_ranges=self.view_ranges,
+                                                   check=False)
             self.rast.backward(dimg, self.grads[b])
             self.image[b].copy_(img)
             self.loss[b].copy_(loss)

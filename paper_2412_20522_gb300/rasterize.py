@@ -136,6 +136,7 @@ class Rasterizer:
         self.bwd_count = torch.zeros(6, dtype=torch.int64, device=self.device)
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.num_sorted = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self._l1_fused = False
 
     # -- buffers -------------------------------------------------------------
     def _get(self, name, numel, dtype):
@@ -170,10 +171,12 @@ class Rasterizer:
 
     # -- forward --------------------------------------------------------------
     def forward(self, params: dict, cams, cfg: RasterConfig, view_ranges=None, check=True,
-                count_fragments=False, stage_events=None, inference=False):
+                count_fragments=False, stage_events=None, inference=False, l1_target=None):
         """Masked forward.  Returns the concatenated images (flat float32,
         per view [3][H][W]).  ``inference``: the forward-only renderer of a
-        (pruned) model -- every Gaussian present, no state for a backward."""
+        (pruned) model -- every Gaussian present, no state for a backward.
+        ``l1_target`` (flat float32 like the images): the render kernel also
+        takes the L1 loss against it (see ``forward_l1``)."""
         if inference:
             cfg = RasterConfig(**{**cfg.__dict__, "mask_mode": abi.MG_MASK_ALL_ONES,
                                   "given_mask": None, "lambda_m": 0.0})
@@ -257,10 +260,20 @@ class Rasterizer:
         n_contrib = self._get("n_contrib", pix, torch.int32)
         if count_fragments:
             self.frag_count.zero_()
+        fused = l1_target is not None and not count_fragments
+        if fused:
+            dimg = self._get("dL_dimage", 3 * pix, torch.float32)
+            loss = self._get("loss", 1, torch.float32)
+            loss.zero_()
         ev.begin("render")
-        abi.mg_render(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image, final_T,
-                      n_contrib, self.frag_count if count_fragments else None, stream)
+        if fused:
+            abi.mg_render_l1(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image,
+                             final_T, n_contrib, l1_target, dimg, loss, stream)
+        else:
+            abi.mg_render(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image,
+                          final_T, n_contrib, self.frag_count if count_fragments else None, stream)
         ev.end("render")
+        self._l1_fused = fused
         # kernels of ours per forward: preprocess (with the depth keys);
         # histogram, offsets, 4 digit passes; scan, duplicate; histogram,
         # offsets, one per tile digit pass, ranges; tile order; render
@@ -281,6 +294,27 @@ class Rasterizer:
 
     def backward_launches(self):
         return 2
+
+    def forward_l1(self, params: dict, cams, cfg: RasterConfig, target, view_ranges=None,
+                   check=True, count_fragments=False, stage_events=None):
+        """The masked forward with the L1 render loss taken by the render
+        kernel itself: returns (image, L, dL/dimage), L = L_render (L1) +
+        lambda_m L_m (Eq. 8; the mask loss only when lambda_m != 0, its
+        gradient added by the backward)."""
+        image = self.forward(params, cams, cfg, view_ranges=view_ranges, check=check,
+                             count_fragments=count_fragments, stage_events=stage_events,
+                             l1_target=target)
+        if not self._l1_fused:                   # the counting variant: a separate pass
+            loss, dimg = self.l1_loss_grad(image, target)
+            return image, loss, dimg
+        s = self._state
+        ev = _Events(stage_events)
+        ev.begin("loss")
+        loss = self._buf["loss"][:1]
+        if s["cfg"].lambda_m != 0.0:
+            abi.mg_mask_loss(s["splats"], s["views"], s["V"], s["cfg"], loss, self._stream())
+        ev.end("loss")
+        return image, loss, self._buf["dL_dimage"][:3 * s["pix"]]
 
     def l1_loss_grad(self, image, target):
         """L = L_render (L1) + lambda_m L_m (Eq. 8; the mask loss only when

@@ -82,6 +82,9 @@ def test_bad_arguments_rejected_on_host(lib):
     st = lib.mg_render(C.byref(out), None, None, None, views, 1, C.byref(cfg), None, None, None,
                        None, None)
     assert st == abi.MG_ERR_INVALID_ARG
+    st = lib.mg_render_l1(C.byref(out), None, None, None, views, 1, C.byref(cfg), None, None, None,
+                          None, None, None, None)
+    assert st == abi.MG_ERR_INVALID_ARG
     alt = C.c_int32(0)
     st = lib.mg_sort(None, None, None, None, None, 0, 20, None, 1, None, 0, C.byref(alt), None,
                      None, None)
