@@ -290,6 +290,19 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     const bool active = i < g.n;
 
+    // the Gaussian's attributes first: their loads travel during the mask
+    // sample's arithmetic (lanes past the end read Gaussian 0, unused)
+    const int64_t ia = active ? i : 0;
+    const float *means = reinterpret_cast<const float *>(g.means);
+    const float x = __ldg(means + 3 * ia), y = __ldg(means + 3 * ia + 1),
+                z = __ldg(means + 3 * ia + 2);
+    const float ls[3] = {ld_attr<ST>(g.log_scales, 3 * ia),
+                         ld_attr<ST>(g.log_scales, 3 * ia + 1),
+                         ld_attr<ST>(g.log_scales, 3 * ia + 2)};
+    float q[4];
+    ld_quat<ST>(g.quats, ia, q);
+    const float ol = ld_attr<ST>(g.opacity_logit, ia);
+
     // --- mask (Sec. 3.3): Gumbel-max over the two existence scores, or the
     // threshold of the straight-through ablation (Sec. 4.3)
     float Mf = active ? 1.0f : 0.0f;
@@ -321,14 +334,7 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
     }
     if (!active) return;
 
-    const float *means = reinterpret_cast<const float *>(g.means);
-    const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
-                z = __ldg(means + 3 * i + 2);
-    const float ls[3] = {ld_attr<ST>(g.log_scales, 3 * i), ld_attr<ST>(g.log_scales, 3 * i + 1),
-                         ld_attr<ST>(g.log_scales, 3 * i + 2)};
-    float q[4];
-    ld_quat<ST>(g.quats, i, q);
-    const float op = 1.0f / (1.0f + __expf(-ld_attr<ST>(g.opacity_logit, i)));
+    const float op = 1.0f / (1.0f + __expf(-ol));
 
     for (int v = 0; v < vt.n_views; ++v) {
         if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
