@@ -106,7 +106,7 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 // --------------------------------------------------------------------------
 // key duplication
 // --------------------------------------------------------------------------
-// Slot-parallel: warp w writes instance slots [w C, (w + 1) C), C = 1024,
+// Slot-parallel: warp w writes instance slots [w C, (w + 1) C), C = 512,
 // whatever splats they belong to.  (A warp per 32 splats would leave the
 // nearest splats -- first in depth order, and the largest, thousands of
 // tiles each -- to a few warps: the kernel's time was their tail.)  The warp
@@ -120,7 +120,7 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 // exact integer.  A slot whose tile the Gaussian cannot reach above the
 // alpha floor (bin_tile_hit) gets the key kDroppedKey, which the tile sort
 // drops.
-constexpr int kDupChunk = 1024;
+constexpr int kDupChunk = 512;
 constexpr uint32_t kDroppedKey = 0xFFFFFFFFu;
 
 __global__ void __launch_bounds__(256)
