@@ -605,12 +605,21 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
     if (gw0 >= g.n) return;
     const int nrows = (int)(g.n - gw0 < 32 ? g.n - gw0 : 32);
     float *dsh = sm_dsh[warp];
-    for (int f = lane; f < 32 * S_; f += 32) dsh[f] = 0.0f;
-    __syncwarp();
     const int64_t i = gw0 + lane;
+    float *drow = dsh + lane * S_;
     if (lane < nrows) {
-        // a Gaussian visible in some view: start its 2D gradients and its SH
-        // row towards L2 before the dependent work that reads them
+        // the Gaussian's attributes first: their loads travel while the
+        // visibility is read and the prefetches go out
+        const float *means = reinterpret_cast<const float *>(g.means);
+        const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
+                    z = __ldg(means + 3 * i + 2);
+        const float ls[3] = {ld_attr<ST>(g.log_scales, 3 * i), ld_attr<ST>(g.log_scales, 3 * i + 1),
+                             ld_attr<ST>(g.log_scales, 3 * i + 2)};
+        float q[4];
+        ld_quat<ST>(g.quats, i, q);
+        const float op_logit = ld_attr<ST>(g.opacity_logit, i);
+        // a Gaussian visible in some view: start its 2D gradients, clamp bits
+        // and SH row towards L2 before the dependent work that reads them
         bool vis = false;
         for (int v = 0; v < vt.n_views; ++v) {
             if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
@@ -620,6 +629,7 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
             const char *gp = reinterpret_cast<const char *>(grad2d + 12 * r);
             prefetch_l2(gp);
             prefetch_l2(gp + 47);
+            prefetch_l2(sp.clamp + r);
         }
         if (vis) {
             constexpr int RB = ROW * (int)sizeof(ST);
@@ -628,15 +638,10 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
             for (int o = 0; o < RB; o += 128) prefetch_l2(sp0 + o);
             prefetch_l2(sp0 + RB - 1);
         }
-        float *drow = dsh + lane * S_;
-        const float *means = reinterpret_cast<const float *>(g.means);
-        const float x = __ldg(means + 3 * i), y = __ldg(means + 3 * i + 1),
-                    z = __ldg(means + 3 * i + 2);
-        const float ls[3] = {ld_attr<ST>(g.log_scales, 3 * i), ld_attr<ST>(g.log_scales, 3 * i + 1),
-                             ld_attr<ST>(g.log_scales, 3 * i + 2)};
-        float q[4];
-        ld_quat<ST>(g.quats, i, q);
-        const float op = 1.0f / (1.0f + __expf(-ld_attr<ST>(g.opacity_logit, i)));
+        // the lane's own staging row (bank 17 l + c mod 32: no conflicts)
+#pragma unroll
+        for (int f = 0; f < ROW; ++f) drow[f] = 0.0f;
+        const float op = 1.0f / (1.0f + __expf(-op_logit));
 
         float d_mean[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0}, d_op = 0.0f,
               d_M = 0.0f;
