@@ -478,6 +478,12 @@ const char *mg_version(void);
 mg_status mg_selftest_wait_timeout(int32_t max_polls, mg_status_word *d_status,
                                    mg_stream_t stream);
 
+/* The same for the warp-wide look-back of the single-pass scans (the tile
+ * count scan of mg_bin, the compaction of mg_compact): one warp waits for 32
+ * predecessors that never publish; MG_ERR_TIMEOUT with detail 5. */
+mg_status mg_selftest_warp_wait_timeout(int32_t max_polls, mg_status_word *d_status,
+                                        mg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
             "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
-            "mg_version", "mg_selftest_wait_timeout")
+            "mg_version", "mg_selftest_wait_timeout", "mg_selftest_warp_wait_timeout")
 
 
 class MaskgsError(RuntimeError):
@@ -142,6 +142,7 @@ def load(build_if_missing: bool = True):
         "mg_status_string": (C.c_char_p, [C.c_int32]),
         "mg_version": (C.c_char_p, []),
         "mg_selftest_wait_timeout": (st, [C.c_int32, vp, vp]),
+        "mg_selftest_warp_wait_timeout": (st, [C.c_int32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -303,6 +304,11 @@ def mg_render_inference(splats, sorted_vals, ranges, tile_order, views, n_views,
 def mg_selftest_wait_timeout(max_polls, d_status, stream):
     _check("mg_selftest_wait_timeout", load().mg_selftest_wait_timeout(max_polls, ptr(d_status),
                                                                        stream))
+
+
+def mg_selftest_warp_wait_timeout(max_polls, d_status, stream):
+    _check("mg_selftest_warp_wait_timeout",
+           load().mg_selftest_warp_wait_timeout(max_polls, ptr(d_status), stream))
 
 
 def mg_read_status(d_status, stream) -> mg_status_word:

@@ -99,6 +99,15 @@ __global__ void selftest_wait_kernel(int max_polls, mg_status_word *st) {
     status[1] = 0;
     lookback<uint64_t, 62>(status, 1, 1, st, 4, max_polls);
 }
+
+// The same for the warp-wide look-back of the single-pass scans (one warp,
+// partition 40 of an array where nothing is published; detail 5).
+__global__ void selftest_warp_wait_kernel(int max_polls, mg_status_word *st) {
+    __shared__ uint64_t status[41];
+    for (int i = threadIdx.x; i < 41; i += 32) status[i] = 0;
+    __syncwarp();
+    warp_lookback64(status, 40, st, 5, max_polls);
+}
 }  // namespace mg
 
 extern "C" {
@@ -107,6 +116,13 @@ mg_status mg_selftest_wait_timeout(int32_t max_polls, mg_status_word *d_status,
                                    mg_stream_t stream) {
     if (d_status == nullptr || max_polls < 0 || max_polls > (1 << 24)) return MG_ERR_INVALID_ARG;
     mg::selftest_wait_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(max_polls, d_status);
+    return mg_host::launch_status();
+}
+
+mg_status mg_selftest_warp_wait_timeout(int32_t max_polls, mg_status_word *d_status,
+                                        mg_stream_t stream) {
+    if (d_status == nullptr || max_polls < 0 || max_polls > (1 << 24)) return MG_ERR_INVALID_ARG;
+    mg::selftest_warp_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(max_polls, d_status);
     return mg_host::launch_status();
 }
 

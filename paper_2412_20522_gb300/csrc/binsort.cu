@@ -78,18 +78,23 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
     for (int k = 0; k < kScanItems; ++k) sum += v[k];
     uint64_t agg;
     const uint64_t excl = block_exclusive_scan_u64(sum, sm_warp, agg);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {   // warp 0 publishes and looks back
         uint64_t prefix = 0;
         if (part == 0) {
-            atomicExch((unsigned long long *)&ws->status[0], (unsigned long long)(kFlagPrefix64 | agg));
+            if (threadIdx.x == 0)
+                atomicExch((unsigned long long *)&ws->status[0],
+                           (unsigned long long)(kFlagPrefix64 | agg));
         } else {
-            atomicExch((unsigned long long *)&ws->status[part], (unsigned long long)(kFlagAgg64 | agg));
-            prefix = lookback<uint64_t, 62>(ws->status, 1, part, st, 1);
-            atomicExch((unsigned long long *)&ws->status[part],
-                       (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
+            if (threadIdx.x == 0)
+                atomicExch((unsigned long long *)&ws->status[part],
+                           (unsigned long long)(kFlagAgg64 | agg));
+            prefix = warp_lookback64(ws->status, part, st, 1);
+            if (threadIdx.x == 0)
+                atomicExch((unsigned long long *)&ws->status[part],
+                           (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
         }
-        sm_prefix = prefix;
-        if (part == n_parts - 1) {
+        if (threadIdx.x == 0) sm_prefix = prefix;
+        if (threadIdx.x == 0 && part == n_parts - 1) {
             *d_total = prefix + agg;
             if (prefix + agg > capacity) raise_status(st, MG_ERR_CAPACITY, 1, prefix + agg);
         }

@@ -119,6 +119,48 @@ __device__ __forceinline__ W lookback(const W *status, int64_t stride, int64_t p
     return excl;
 }
 
+// Warp-wide decoupled look-back over 64-bit status words (flag in bits
+// 62-63, value below): the calling warp reads its 32 nearest predecessors at
+// once, waits only for those up to the nearest inclusive prefix, and sums
+// them; it moves to the next 32 only while none of them holds an inclusive
+// prefix -- a walk over published aggregates costs one round trip per 32
+// partitions.  Called by all 32 lanes of one warp; every lane returns the
+// exclusive prefix.  Waits are bounded as in lookback().
+__device__ __forceinline__ uint64_t warp_lookback64(const uint64_t *status, int64_t part,
+                                                    mg_status_word *st, int32_t detail,
+                                                    int max_spins = kMaxTimeoutSpins) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    constexpr uint64_t kMask = (1ull << 62) - 1ull;
+    uint64_t excl = 0;
+    for (int64_t q = part - 1; q >= 0; q -= 32) {
+        const int64_t idx = q - lane;
+        // before partition 0: an empty inclusive prefix
+        uint64_t s = idx >= 0 ? ld_volatile(status + idx) : kFlagPrefix64;
+        for (int spins = 0;; ++spins) {
+            const unsigned inc = __ballot_sync(FULL, (s >> 62) == 2u);
+            // lanes up to the nearest inclusive prefix (lane 0 is the nearest)
+            const unsigned need = inc ? (2u << (__ffs(inc) - 1)) - 1u : FULL;
+            const unsigned missing = __ballot_sync(FULL, (s >> 62) == 0u) & need;
+            if (missing == 0u) {
+                uint64_t v = ((need >> lane) & 1u) ? (s & kMask) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                excl += v;
+                if (inc) return excl;
+                break;
+            }
+            if (spins >= max_spins) {
+                if (lane == 0) raise_status(st, MG_ERR_TIMEOUT, detail, 0);
+                return excl;
+            }
+            __nanosleep(20);
+            if ((missing >> lane) & 1u) s = ld_volatile(status + idx);
+        }
+    }
+    return excl;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
 // (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),

@@ -67,18 +67,23 @@ compact_scan_kernel(const uint8_t *__restrict__ keep, int64_t n, int32_t *__rest
     for (int k = 0; k < kCompactItems; ++k) cnt += f[k] != 0;
     uint64_t agg;
     const uint64_t excl = block_exclusive_scan_u64(cnt, sm_warp, agg);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {   // warp 0 publishes and looks back
         uint64_t prefix = 0;
         if (part == 0) {
-            atomicExch((unsigned long long *)&ws->status[0], (unsigned long long)(kFlagPrefix64 | agg));
+            if (threadIdx.x == 0)
+                atomicExch((unsigned long long *)&ws->status[0],
+                           (unsigned long long)(kFlagPrefix64 | agg));
         } else {
-            atomicExch((unsigned long long *)&ws->status[part], (unsigned long long)(kFlagAgg64 | agg));
-            prefix = lookback<uint64_t, 62>(ws->status, 1, part, st, 3);
-            atomicExch((unsigned long long *)&ws->status[part],
-                       (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
+            if (threadIdx.x == 0)
+                atomicExch((unsigned long long *)&ws->status[part],
+                           (unsigned long long)(kFlagAgg64 | agg));
+            prefix = warp_lookback64(ws->status, part, st, 3);
+            if (threadIdx.x == 0)
+                atomicExch((unsigned long long *)&ws->status[part],
+                           (unsigned long long)(kFlagPrefix64 | (prefix + agg)));
         }
-        sm_prefix = prefix;
-        if (part == n_parts - 1) *d_n_kept = (int64_t)(prefix + agg);
+        if (threadIdx.x == 0) sm_prefix = prefix;
+        if (threadIdx.x == 0 && part == n_parts - 1) *d_n_kept = (int64_t)(prefix + agg);
     }
     __syncthreads();
     int32_t run = (int32_t)(sm_prefix + excl);

@@ -121,3 +121,5 @@ def test_mask_pruning_and_inference_arguments_rejected_on_host(lib):
     assert lib.mg_render_inference(C.byref(out), None, None, None, views, 1, C.byref(cfg), None,
                                    None) == abi.MG_ERR_INVALID_ARG
     assert lib.mg_tile_order(None, 10, None, None) == abi.MG_ERR_INVALID_ARG
+    assert lib.mg_selftest_wait_timeout(10, None, None) == abi.MG_ERR_INVALID_ARG
+    assert lib.mg_selftest_warp_wait_timeout(10, None, None) == abi.MG_ERR_INVALID_ARG

@@ -45,6 +45,11 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     st = abi.mg_read_status(status, stream)
     assert st.status == abi.MG_ERR_TIMEOUT and st.detail == 4
     assert abi.status_string(st.status) == "device-side wait timed out"
+    # the warp-wide look-back of the single-pass scans
+    status.zero_()
+    abi.mg_selftest_warp_wait_timeout(1000, status, stream)
+    st = abi.mg_read_status(status, stream)
+    assert st.status == abi.MG_ERR_TIMEOUT and st.detail == 5
     # the same context renders normally afterwards
     g, cams, _ = scenes.tiny_workload(2000)
     r = Rasterizer()
