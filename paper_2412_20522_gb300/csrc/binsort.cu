@@ -32,6 +32,8 @@
 namespace mg {
 
 constexpr int kScanThreads = 256, kScanItems = 8, kScanPart = kScanThreads * kScanItems;
+// instance slots per duplication warp (the scan marks each chunk's owner)
+constexpr int kDupChunk = 512;
 // 512 threads x 12 keys: with every partition of a small sort running at
 // once, a partition's look-back ends at the nearest inclusive prefix, which
 // spreads about a window per round trip -- fewer, larger partitions shorten
@@ -53,7 +55,7 @@ struct ScanWS {
 __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order, int64_t n,
             uint32_t *__restrict__ out, uint64_t *d_total, uint64_t capacity, ScanWS *ws,
-            int64_t n_parts, mg_status_word *st) {
+            int64_t n_parts, mg_status_word *st, uint32_t *__restrict__ owner_hint) {
     __shared__ uint64_t sm_warp[33];
     __shared__ uint64_t sm_prefix;
     __shared__ int64_t sm_part;
@@ -104,6 +106,14 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < n) out[base + k] = run > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)run;
+        // the position owns slots [run, run + v): it marks the duplication
+        // chunks that start among them (owner_hint[c C] = position, C =
+        // kDupChunk), below the capacity
+        if (owner_hint != nullptr) {
+            const uint64_t e = run + v[k] < capacity ? run + v[k] : capacity;
+            for (uint64_t c = (run + kDupChunk - 1) / kDupChunk; c * kDupChunk < e; ++c)
+                owner_hint[c * kDupChunk] = (uint32_t)(base + k);
+        }
         run += v[k];
     }
 }
@@ -115,23 +125,21 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
 // whatever splats they belong to.  (A warp per 32 splats would leave the
 // nearest splats -- first in depth order, and the largest, thousands of
 // tiles each -- to a few warps: the kernel's time was their tail.)  The warp
-// finds the position owning its first slot by a 32-ary search of the offsets
-// (non-decreasing; the owner is the last position whose offset is <= the
-// slot), then walks positions 32 at a time: each lane holds one position's
-// offset, record and binning record, and every 32 consecutive slots find
-// their owner lane by a binary search over the lanes (shuffles) and are
-// written fully coalesced.  Slot m of a rectangle is tile (x0 + m % w,
+// reads the position owning its first slot (the last position whose offset
+// is <= the slot) from the mark the scan left in that slot's value, then
+// walks positions 32 at a time: each lane holds one position's offset, slot
+// count (the step to the next offset), record and binning record, and every
+// 32 consecutive slots find their owner lane by a binary search over the
+// lanes (shuffles) and are written fully coalesced.  Slot m of a rectangle is tile (x0 + m % w,
 // y0 + m / w), the quotient through an FP32 reciprocal corrected to the
 // exact integer.  A slot whose tile the Gaussian cannot reach above the
 // alpha floor (bin_tile_hit) gets the key kDroppedKey, which the tile sort
 // drops.
-constexpr int kDupChunk = 512;
 constexpr uint32_t kDroppedKey = 0xFFFFFFFFu;
 
 __global__ void __launch_bounds__(256)
-duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restrict__ tiles,
-                 const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
-                 int64_t n_records, const uint64_t *__restrict__ d_num_instances,
+duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restrict__ order,
+                 const uint32_t *__restrict__ offsets, int64_t n_records, const uint64_t *__restrict__ d_num_instances,
                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t capacity,
                  int tile_w, int tile_h, bool filter) {
     const unsigned FULL = 0xffffffffu;
@@ -143,41 +151,35 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
     if (s0 >= K) return;                                  // warp-uniform
     const uint64_t s1 = s0 + kDupChunk < K ? s0 + kDupChunk : K;
 
-    // owner of slot s0: the last position i with offsets[i] <= s0 (offsets[0] = 0)
-    int64_t lo = 0, hi = n_records;
-    while (hi - lo > 32) {
-        const int64_t step = (hi - lo + 31) >> 5;
-        const int64_t idx = lo + (int64_t)lane * step;
-        const bool le = idx < hi && (uint64_t)offsets[idx] <= s0;
-        const unsigned b = __ballot_sync(FULL, le);
-        lo += (int64_t)(31 - __clz(b)) * step;
-        hi = lo + step < hi ? lo + step : hi;
-    }
-    {
-        const int64_t idx = lo + lane;
-        const bool le = idx < hi && (uint64_t)offsets[idx] <= s0;
-        lo += 31 - __clz(__ballot_sync(FULL, le));
-    }
+    // owner of slot s0 (the last position i with offsets[i] <= s0), marked
+    // by the scan in the slot's value
+    const int64_t lo = (int64_t)vals[s0];
+    const uint32_t total32 = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
 
     uint64_t s = s0;
     for (int64_t i = lo; s < s1; i += 32) {
         const int64_t ip = i + lane;
-        uint32_t off = 0xFFFFFFFFu, nt = 0, r = 0, xy0 = 0, w = 1, first = 0, gx = 1;
+        uint32_t off = 0xFFFFFFFFu, nxt = total32, r = 0, xy0 = 0, w = 1, first = 0, gx = 1;
         float4 b0 = make_float4(0.f, 0.f, 1.f, 0.f), b1 = make_float4(1.f, 0.f, 0.f, 0.f);
         if (ip < n_records) {
             off = offsets[ip];
             r = order ? order[ip] : (uint32_t)ip;
-            nt = tiles[r];
-            if (nt != 0) {
-                const float4 *br = bin_record + 3 * (int64_t)r;
-                b0 = br[0];
-                b1 = br[1];
-                const uint4 u = reinterpret_cast<const uint4 *>(br)[2];
-                xy0 = u.x;
-                w = u.y;
-                first = u.z;
-                gx = u.w;
-            }
+            if (lane == 31 && ip + 1 < n_records) nxt = offsets[ip + 1];
+        }
+        // a position's slot count is the step to the next offset (the last
+        // position ends at the total; offsets below the capacity are exact)
+        const uint32_t down = __shfl_down_sync(FULL, off, 1);
+        if (lane < 31 && ip + 1 < n_records) nxt = down;
+        const uint32_t nt = ip < n_records ? nxt - off : 0u;
+        if (nt != 0) {
+            const float4 *br = bin_record + 3 * (int64_t)r;
+            b0 = br[0];
+            b1 = br[1];
+            const uint4 u = reinterpret_cast<const uint4 *>(br)[2];
+            xy0 = u.x;
+            w = u.y;
+            first = u.z;
+            gx = u.w;
         }
         const float rw = 1.0f / (float)w;
         // slots of these 32 positions: up to the end of the last valid one
@@ -633,10 +635,10 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
     }
     scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, order, R, offsets,
                                                          d_num_instances, capacity, ws, parts,
-                                                         d_status);
+                                                         d_status, capacity > 0 ? vals : nullptr);
     if (capacity > 0)
         duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
-            reinterpret_cast<const float4 *>(splats->bin_record), splats->tiles_touched, order,
+            reinterpret_cast<const float4 *>(splats->bin_record), order,
             offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
             cfg->bin_mode == MG_BIN_FILTERED);
     return mg_host::launch_status();
@@ -758,10 +760,10 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
     }
     scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, order, R, offsets,
                                                          d_num_instances, capacity, ws, parts,
-                                                         d_status);
+                                                         d_status, capacity > 0 ? vals : nullptr);
     if (capacity > 0)
         duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
-            reinterpret_cast<const float4 *>(splats->bin_record), splats->tiles_touched, order,
+            reinterpret_cast<const float4 *>(splats->bin_record), order,
             offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
             cfg->bin_mode == MG_BIN_FILTERED);
     return mg_host::launch_status();
