@@ -284,8 +284,11 @@ __device__ __forceinline__ void sh_colour(const void *sh, int64_t i, const float
 
 // The SH rows are read only for Gaussians that are visible in a view, one
 // row per lane with 128-bit loads (no row of an invisible Gaussian is read).
+// Eight CTAs per SM: the 64 registers this leaves hold the kernel without
+// spills for FP32 storage (8 bytes spill with 16-bit storage), and the
+// memory latency it waits on wants the extra warps.
 template <int DEG, typename ST>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 8)
 preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out) {
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     const bool active = i < g.n;
