@@ -594,9 +594,11 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 
 // dL/dsh accumulates over views in a per-warp shared-memory tile (one row
 // per lane, odd row stride) and leaves with coalesced 128-bit stores; SH rows
-// are read only for Gaussians visible in some view.
+// are read only for Gaussians visible in some view.  Five CTAs per SM: the
+// 96 registers this leaves cost a few bytes of spills, and the latency-bound
+// kernel gains more from the fifth CTA's warps.
 template <int DEG, typename ST>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 5)
 preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats sp,
                            const float *__restrict__ grad2d, mg_param_grads out) {
     constexpr int K = (DEG + 1) * (DEG + 1);
