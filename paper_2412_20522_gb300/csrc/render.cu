@@ -416,8 +416,9 @@ constexpr int kAcc = 10;
 // [0] (warp, splat) list iterations, [1] of which masked, [2] unmasked with a
 // contributing pixel, [3] masked with a contributing pixel, [4] contributing
 // pixels over [2], [5] staged batches.
-// Nine CTAs per SM (36 warps): the register cap this asks for (56) holds
-// without spills, and nine copies of the 23.8 KB of shared memory fit.
+// Eight CTAs per SM (32 warps): the register cap this asks for (64) holds
+// without spills, and eight copies of the 27.3 KB of shared memory fit (a
+// ninth does not).
 constexpr int kBatchB = 128;                    // splats staged per backward batch
 template <bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads, 1024 / kRenderThreads)
