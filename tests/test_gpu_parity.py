@@ -156,8 +156,8 @@ def _check_backward(rast, dev, g, cams, ocfg, views, M, minfo, straddles, target
     return flatten
 
 
-def _full_check(rz, g, cams, targets, cfg_kw=None, tile=(16, 16)):
-    rast, dev, img = _run(rz, g, cams, targets, cfg_kw, tile)
+def _full_check(rz, g, cams, targets, cfg_kw=None, tile=(16, 16), capacity=0):
+    rast, dev, img = _run(rz, g, cams, targets, cfg_kw, tile, capacity=capacity)
     ocfg, views, M, minfo = _oracle(g, cams, cfg_kw, tile)
     _check_discrete(rast, views, M, cams)
     rep = []
@@ -308,3 +308,25 @@ def test_every_gaussian_masked(rz):
     im = img.cpu().numpy().reshape(3, -1)
     for c, b in enumerate((0.3, 0.6, 0.9)):
         assert np.all(im[c] == np.float32(b))
+
+
+def test_duplication_chunks_inside_large_splats(rz):
+    """Frame-filling splats whose instance ranges cross several 512-slot
+    duplication chunks (the scan marks each chunk's owning splat), with the
+    instance buffer sized to the exact count (the last chunk ends at the
+    capacity), against the oracle."""
+    g = scenes.uniform_gaussians(3000, seed=61)
+    cam = scenes.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 1000, 760, 600.0)
+    for k in range(4):                          # low-opacity splats over the whole frame
+        g.means[k] = (0.05 * k, -0.04 * k, 0.1 * k)
+        g.log_scales[k] = np.log(2.5)
+        g.opacity_logit[k] = -2.0 - 0.5 * k
+    tgt = scenes.target_image(760, 1000, seed=62)
+    first = rz.Rasterizer()
+    first.forward(to_device(g), [cam], rz.RasterConfig(), check=True)
+    torch.cuda.synchronize()
+    K = int(first.num_instances.item())
+    assert K > 4 * 3000                         # each large splat spans several chunks
+    rast, views = _full_check(rz, g, [cam], [tgt], capacity=K)
+    assert rast.capacity == K                   # no regrowth: the exact size sufficed
+    assert int(rast.num_instances.item()) == K
