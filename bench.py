@@ -75,13 +75,14 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.dir = tempfile.mkdtemp(prefix="maskgs_clocks_")
+        self.path = os.path.join(self.dir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
@@ -113,6 +114,11 @@ class ClockSampler:
             for nm, val in zip(names, f[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+            os.rmdir(self.dir)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
@@ -263,20 +269,35 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3)):
         gs.replay()
     torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     g0 = torch.cuda.Event(enable_timing=True)
     g1 = torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    for _ in range(args.steps):
-        gs.replay()
-    g1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
+
+    def timed_block():
+        # exactly K steps, a barrier and a synchronisation on both sides
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        g0.record(stream)
+        for _ in range(args.steps):
+            gs.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        return g0.elapsed_time(g1)
+
+    # blocks of K steps until at least 0.5 s is timed (the same number of
+    # blocks on every rank); the headline is the median block
+    blocks = [timed_block()]
+    n_blocks = int(_max_over_ranks(max(3.0, math.ceil(500.0 / max(blocks[0], 1e-3))), ws, dev))
+    n_blocks = min(n_blocks, 400)
+    while len(blocks) < n_blocks:
+        blocks.append(timed_block())
     clk = clocks.stop()
-    ms = _max_over_ranks(g0.elapsed_time(g1) / args.steps, ws, dev)
+    ms = _max_over_ranks(statistics.median(blocks) / args.steps, ws, dev)
+    timed_blocks = {"blocks": len(blocks), "steps_per_block": args.steps,
+                    "block_ms_min": min(blocks), "block_ms_median": statistics.median(blocks),
+                    "block_ms_max": max(blocks), "timed_s": sum(blocks) / 1e3}
     if gs.status() != abi.MG_OK:
         raise RuntimeError(f"device status {gs.status()} after the graph steps")
     del gs
@@ -301,10 +322,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     counts = rect.frag_count.cpu().tolist()
     del rect
-    flops_fwd, flops_bwd = render_flops(counts)
+    # algorithmic flops on the lists the timed kernels walk (filtered tile
+    # lists, every pair up to each pixel's stop); the same on the whole
+    # 3-sigma rectangles of the 3DGS binning (method-equivalent, secondary)
+    flops_fwd, flops_bwd = render_flops(counts_exec)
+    flops_fwd_rect, flops_bwd_rect = render_flops(counts)
     # executed by the backward: every (warp, splat) iteration evaluates 64 alphas
-    flops_bwd_exec = (bwd_counts[0] * 64 * FLOPS_ALPHA + counts[3] * FLOPS_BWD_MASKED +
-                      counts[2] * FLOPS_BWD_UNMASKED)
+    flops_bwd_exec = (bwd_counts[0] * 64 * FLOPS_ALPHA + counts_exec[3] * FLOPS_BWD_MASKED +
+                      counts_exec[2] * FLOPS_BWD_UNMASKED)
     K = int(rast.num_instances.item())
     so = rast.splat_outputs()
     visible = int((so["radius"] > 0).sum().item())
@@ -318,14 +343,16 @@ def run_ours(args):
     from paper_2412_20522_gb300.hoststep import HostPipeline
     host_params = {k: v.cpu().pin_memory() for k, v in params.items()}
     host_tgt = tgt.cpu().pin_memory()
-    hp = HostPipeline(host_params, host_tgt, cams, cfg, device=dev)
+    hp = HostPipeline(host_params, host_tgt, cams, cfg, device=dev)      # graph replays
     h2d, d2h = hp.h2d_bytes(), hp.d2h_bytes()
-    e2e_n = max(4, args.steps // 2)
+    e2e_n = max(50, args.steps)
     for _ in range(3):
         hp.step()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
     e0.record(hp.h2d)
     for _ in range(e2e_n):
         b = hp.step()
@@ -334,6 +361,7 @@ def run_ours(args):
     e2e_ms = _max_over_ranks(e0.elapsed_time(e1) / e2e_n, ws, dev)
     _, host_loss, _ = hp.results(b)
     e2e_loss = float(host_loss[0])
+    link = host_link_times(hp)
     del hp
 
     host_img = torch.empty(3 * W * H, dtype=torch.float32).pin_memory()
@@ -375,8 +403,18 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                 "traffic": _profiled_traffic(dom),
                 "peak_source": f"FP32 FMA lanes x 2 x max SM clock ({sms} SMs, {smmax:.0f} MHz)",
-                "flops_basis": "fragments of the 3-sigma rectangle tile lists up to each "
-                               "pixel's stop (the method's walk)"}
+                "flops_basis": "the filtered tile lists the kernels walk: every (pixel, splat) "
+                               "pair up to each pixel's stop, 15 flops of alpha; masked splats "
+                               "above the floor 12, blended splats 48 (backward)",
+                "flops_per_launch": flops_fwd if dom == "render" else flops_bwd,
+                "pairs": {"walked": counts_exec[0], "walked_unmasked": counts_exec[1],
+                          "blended": counts_exec[2], "masked_above_floor": counts_exec[3]}}
+        rect_f = (flops_fwd_rect if dom == "render" else flops_bwd_rect)
+        roof["method_equivalent"] = {
+            "achieved": rect_f / (stage_ms[dom] * 1e-3) / 1e12,
+            "frac": rect_f / (stage_ms[dom] * 1e-3) / 1e12 / fp32_peak_tflops,
+            "basis": "the same flops counted on the whole 3-sigma rectangle lists of the 3DGS "
+                     "binning (work the tile filter removes is counted as done)"}
         # the kernels are bound by instruction issue: its utilisation
         issue = _profiled_issue(dom, sms)
         if issue is not None:
@@ -440,19 +478,27 @@ def run_ours(args):
                    "fragments": {"walked": counts[0], "walked_unmasked": counts[1],
                                  "blended": counts[2], "masked_above_floor": counts[3],
                                  "walked_filtered_lists": counts_exec[0]},
-                   "render_gflop": {"fwd": flops_fwd / 1e9, "bwd": flops_bwd / 1e9},
+                   "render_gflop": {"fwd": flops_fwd / 1e9, "bwd": flops_bwd / 1e9,
+                                    "fwd_rect_lists": flops_fwd_rect / 1e9,
+                                    "bwd_rect_lists": flops_bwd_rect / 1e9},
                    "bwd_iterations": dict(zip(("list", "masked", "contrib_unmasked",
                                                "contrib_masked", "contrib_lanes", "batches"),
                                               bwd_counts)),
                    "visible": visible, "mask_on_fraction": mask_on},
         "stage_ms": stage_ms,
+        "timed_blocks": timed_blocks,
         "step_ms_distribution": step_dist,
         "roofline": roof,
         "stage_roofline_hbm": stage_roof,
         "e2e": {"value": _whole_job_value(mpix, ws, e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "copies": "pinned host <-> device every step, overlapped with the neighbouring "
-                          "steps' compute (two copy streams, double-buffered)",
+                          "steps' compute (two copy streams, double-buffered; each slot "
+                          "replays its captured graph of the step)",
+                "steps_timed": e2e_n,
+                "achieved_h2d_gbs": h2d / (e2e_ms * 1e-3) / 1e9,
+                "achieved_d2h_gbs": d2h / (e2e_ms * 1e-3) / 1e9,
+                "host_link": link,
                 "serial_ms_per_step": serial_ms, "loss": e2e_loss},
         "gpu_launches": gpu_launches_per_step * args.steps,
         "clocks": clk,
@@ -464,14 +510,54 @@ def run_ours(args):
         line["forms"]["next_rows"] = run_next_rows(dev, g, cams, target, ms, peaks)
         line["forms"]["tiny_c1"] = tiny_workload_times(dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(steps=1)
+        # the oracle runs only here: timed as the CPU baseline, and compared
+        # with the GPU output by output (parity, and the precision forms'
+        # error per output)
+        cb, parity = oracle_step_and_parity(dev, params, g, cams[0], target)
+        line["cpu_baseline"] = cb
         line["cpu_baseline"]["tiny_workload"] = tiny_workload_oracle_seconds()
+        line["parity"] = parity
+        line["precision_c4_error"] = precision_c4_error(dev)
     if clk is not None and clk["samples"] < 3:
         line["clocks"]["note"] = "timed region shorter than three 100 ms samples"
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def host_link_times(hp, n=20):
+    """The host link alone, with the step's own buffers: every input copied
+    host -> device, every output device -> host, each direction by itself and
+    both at once on their two streams (no compute), ms per step and GB/s."""
+    import torch
+    from paper_2412_20522_gb300.rasterize import PARAM_NAMES
+
+    def h2d():
+        with torch.cuda.stream(hp.h2d):
+            for k in PARAM_NAMES:
+                hp.params[0][k].copy_(hp.host_params[k], non_blocking=True)
+            hp.target[0].copy_(hp.host_target, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(hp.d2h):
+            hp.host_image[0].copy_(hp.image[0], non_blocking=True)
+            hp.host_loss[0].copy_(hp.loss[0], non_blocking=True)
+            for k in PARAM_NAMES:
+                hp.host_grads[0][k].copy_(hp.grads[0][k], non_blocking=True)
+
+    out = {}
+    for name, fns in (("h2d_alone", (h2d,)), ("d2h_alone", (d2h,)), ("both", (h2d, d2h))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n):
+            for f in fns:
+                f()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = (time.perf_counter() - t) * 1e3 / n
+    out["h2d_alone_gbs"] = hp.h2d_bytes() / (out["h2d_alone_ms"] * 1e-3) / 1e9
+    out["d2h_alone_gbs"] = hp.d2h_bytes() / (out["d2h_alone_ms"] * 1e-3) / 1e9
+    return out
 
 
 def _device_params(g, dev, storage=None):
@@ -699,6 +785,154 @@ def cpu_baseline_sample(steps=1, crop=None):
             "cpu": _cpu_model(), "kind": "oracle", "seconds_per_step": t,
             "sample": f"{what}: masked fwd+bwd of the 1.2M-Gaussian scene, all Gaussians "
                       f"preprocessed, FP64, OpenMP over tiles; median of {steps} step(s)"}
+
+
+PARITY_EPS = 1e-4          # straddle band of the oracle's fragment decisions (relative)
+IMG_TOL, GRAD_TOL = 2e-4, 1e-3
+PARAMS = ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")
+
+
+def error_stats(a, b):
+    """a (GPU) against b (oracle), flattened: relative L2; the largest
+    absolute error over the largest |b|; and, over the elements with
+    |b| >= 1e-3 max|b|, the worst relative error and how many exceed 1e-2 --
+    a per-tensor norm alone could hide a few badly wrong elements."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    d = a - b
+    nb = float(np.linalg.norm(b))
+    out = {"rel_l2": float(np.linalg.norm(d)) / nb if nb > 0 else float(np.linalg.norm(d))}
+    mb = float(np.abs(b).max()) if b.size else 0.0
+    out["max_abs_err_over_max_ref"] = float(np.abs(d).max()) / mb if mb > 0 else 0.0
+    sel = np.abs(b) >= 1e-3 * mb if mb > 0 else np.zeros(b.shape, bool)
+    if sel.any():
+        r = np.abs(d[sel]) / np.abs(b[sel])
+        out["worst_rel_elem"] = float(r.max())
+        out["elems_rel_over_1e-2"] = int((r > 1e-2).sum())
+        out["elems_compared"] = int(sel.sum())
+    return out
+
+
+def _oracle_step(g, cam, target):
+    """The oracle's masked forward, L1 loss gradient (zero on straddle
+    pixels) and backward of one view; returns (seconds, views, M, grads,
+    per_view, dimg, straddle)."""
+    from oracle import pipeline
+    ocfg = pipeline.OracleConfig(eps=PARITY_EPS)
+    t0 = time.perf_counter()
+    views, M, minfo = pipeline.forward(g, [cam], ocfg)
+    v = views[0]
+    straddle = (v.out["flags"] & 11) != 0
+    _, dimg = pipeline.l1_loss_grad(v.out["image"], target)
+    dimg = dimg * (~straddle)[None]
+    grads, per_view = pipeline.backward(g, [cam], ocfg, views, M, minfo, [dimg])
+    return time.perf_counter() - t0, views, M, grads, per_view, dimg, straddle
+
+
+def _gpu_vs_oracle(rast, img, out, cam, views, M, grads, per_view, straddle, lists=True):
+    """Every output of a GPU step against the oracle's (one view)."""
+    H, W = cam.height, cam.width
+    v = views[0]
+    so = rast.splat_outputs()
+    d = np.abs(img.cpu().numpy().reshape(3, H, W) - v.out["image"]).max(0)
+    dT = np.abs(so["final_T"].cpu().numpy().reshape(H, W) - v.out["final_T"])
+    gN = so["n_contrib"].cpu().numpy().reshape(H, W)
+    clean = ~straddle
+    rep = {
+        "image": {"pixels": H * W, "straddle_pixels": int(straddle.sum()),
+                  "pixels_over_tol": int((d > IMG_TOL).sum()),
+                  "pixels_over_tol_not_straddle": int(((d > IMG_TOL) & clean).sum()),
+                  "max_abs_err_not_straddle": float(d[clean].max()) if clean.any() else 0.0,
+                  "max_abs_err_all": float(d.max()), "tolerance": IMG_TOL},
+        "final_T": {"max_abs_err_not_straddle": float(dT[clean].max()) if clean.any() else 0.0,
+                    "max_abs_err_all": float(dT.max())},
+        "stop_index_mismatch_not_straddle": int((gN != v.out["n_contrib"])[clean].sum()),
+        "mask_mismatch": int((so["mask"].cpu().numpy() != M).sum()),
+    }
+    if lists:
+        Ks = int(so["num_sorted"].item())
+        keys = rast.sorted_keys().cpu().numpy().view(np.uint32)[:Ks]
+        vals = so["sorted_vals"].cpu().numpy().view(np.uint32)[:Ks]
+        rng = so["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
+        ne = v.ranges[:, 1] > v.ranges[:, 0]
+        rep["tile_lists"] = {
+            "candidates_equal": int(so["num_instances"].item()) == v.K,
+            "kept": Ks, "kept_equal": Ks == v.K_kept,
+            "sorted_keys_equal": bool(Ks == v.K_kept and np.array_equal(
+                keys.astype(np.uint64), v.sorted_keys >> np.uint64(32))),
+            "sorted_values_equal": bool(Ks == v.K_kept and np.array_equal(vals, v.sorted_vals)),
+            "ranges_equal": bool(np.array_equal(rng[ne], v.ranges[ne]))}
+    gr = {k: error_stats(out[k].cpu().numpy(), grads[k]) for k in PARAMS}
+    g2 = so["grad2d"].cpu().numpy().reshape(-1, 12)
+    pv = per_view[0]
+    for name, sl in (("dmean2d", slice(0, 2)), ("dconic", slice(2, 5)), ("dopacity", 5),
+                     ("drgb", slice(6, 9)), ("dmask", 9)):
+        gr["2d_" + name] = error_stats(g2[:, sl], pv[name])
+    rep["gradients"] = gr
+    rep["gradients_within_tol"] = all(e["rel_l2"] <= GRAD_TOL for e in gr.values())
+    rep["grad_tolerance_rel_l2"] = GRAD_TOL
+    return rep
+
+
+def oracle_step_and_parity(dev, params, g, cam, target):
+    """CPU-baseline leg: the oracle's step on the full benchmark view, timed,
+    and the GPU step on the same inputs and upstream gradient compared with
+    it output by output (the parity record of the bench line)."""
+    import torch
+    from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
+    secs, views, M, grads, per_view, dimg, straddle = _oracle_step(g, cam, target)
+    cb = {"value": cam.width * cam.height / 1e6 / secs, "unit": "Mpix/s", "cores": os.cpu_count(),
+          "cpu": _cpu_model(), "kind": "oracle", "seconds_per_step": secs,
+          "sample": f"the full {cam.width}x{cam.height} view: masked fwd + L1 loss + bwd of the "
+                    "1.2M-Gaussian scene, all Gaussians preprocessed, FP64, OpenMP over tiles "
+                    "(straddle pixels' upstream gradient zeroed for the parity comparison); one step"}
+    rast = Rasterizer(dev)
+    img = rast.forward(params, [cam], RasterConfig())
+    out = rast.backward(torch.as_tensor(dimg.astype(np.float32).reshape(-1)).to(dev))
+    torch.cuda.synchronize()
+    rep = _gpu_vs_oracle(rast, img, out, cam, views, M, grads, per_view, straddle)
+    rep["upstream"] = "the oracle's L1 gradient with straddle pixels zeroed, on both sides"
+    rep["straddle_band"] = PARITY_EPS
+    return cb, rep
+
+
+def c4_crop_workload():
+    """The precision configuration: 3M clustered Gaussians (seed 2024125),
+    view 0 of four ring views at 1957x1297 (f = 1150 * 1957 / 1557), its
+    centre 64x64 crop as a camera, and the crop of view 0's target."""
+    from paper_2412_20522_gb300 import scenes
+    g3 = scenes.cluster_gaussians(3_000_000, seed=2024125)
+    f4 = 1150.0 * 1957 / 1557
+    full = scenes.ring_camera(0.0, 4.0, 1957, 1297, f4)
+    cam = _crop_camera(full, 64, 64)
+    x0, y0 = (full.width - 64) // 2, (full.height - 64) // 2
+    tgt = scenes.target_image(1297, 1957, seed=2024126)[:, y0:y0 + 64, x0:x0 + 64].copy()
+    return g3, cam, tgt
+
+
+def precision_c4_error(dev):
+    """Error of each output (image, final T, stop index, the six parameter
+    gradients and the five 2D gradients) against the FP64 oracle on the FP32
+    parameters, for BF16, FP16 and FP32 storage of log-scales, quaternions,
+    opacity logits and SH, at the precision configuration's crop."""
+    import torch
+    from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
+    g3, cam, tgt = c4_crop_workload()
+    _, views, M, grads, per_view, dimg, straddle = _oracle_step(g3, cam, tgt)
+    d = torch.as_tensor(dimg.astype(np.float32).reshape(-1)).to(dev)
+    res = {"gaussians": g3.n, "view": "centre 64x64 crop of view 0 of 4 at 1957x1297",
+           "upstream": "the oracle's L1 gradient with straddle pixels zeroed"}
+    for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16), ("fp32", None)):
+        p = _device_params(g3, dev, dt)
+        rast = Rasterizer(dev)
+        img = rast.forward(p, [cam], RasterConfig())
+        out = rast.backward(d)
+        torch.cuda.synchronize()
+        res[name] = _gpu_vs_oracle(rast, img, out, cam, views, M, grads, per_view, straddle,
+                                   lists=(dt is None))
+        del p, rast
+    torch.cuda.empty_cache()
+    return res
 
 
 def _cpu_model() -> str:

@@ -183,8 +183,9 @@ typedef struct {
  *   tiles_touched[R] u32, the record's candidate tiles for the binning: its
  *     whole 3-sigma rectangle (MG_BIN_RECT), or (MG_BIN_FILTERED) the tiles of
  *     that rectangle that meet the bounding box of the region where the tile
- *     filter can keep a tile -- a box computed in correctly rounded FP64 that
- *     provably holds every tile the filter keeps, so no list changes; 0 = no
+ *     filter can keep a tile -- a box computed by a fixed sequence of
+ *     correctly rounded FP32 operations, with margins that make it hold every
+ *     tile the filter keeps, so no list changes; 0 = no
  *     candidate (culled, or nothing of it can reach the floor in a tile);
  *   radius[R] i32 (pixels, 0 = culled),
  *   clamp[R] u8 (bit c: colour channel c was clamped at 0),
@@ -286,10 +287,11 @@ size_t mg_bin_workspace_bytes(int64_t n_records);
  * return MG_ERR_INVALID_ARG.  The array (about 64 KB) is held on every GPU
  * that loads the library until the process exits.  The first call on each
  * device looks up the array's device address (with that device current) and
- * caches it; make that first call before any stream capture.  Every call
- * shares the one array, so calls that overlap on the GPU (other streams, other
- * threads) race: serialise them.  Nothing is allocated: no cudaMalloc, no
- * cudaFree. */
+ * caches it; make that first call before any stream capture.  The cached
+ * address does not survive cudaDeviceReset: do not call this function on a
+ * device after resetting it in the same process.  Every call shares the one
+ * array, so calls that overlap on the GPU (other streams, other threads) race:
+ * serialise them.  Nothing is allocated: no cudaMalloc, no cudaFree. */
 mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *views, int32_t n_views,
                          const mg_raster_cfg *cfg, const uint32_t *order, uint32_t *offsets,
                          uint32_t *keys, uint32_t *vals, uint64_t capacity,

@@ -714,8 +714,12 @@ mg_status bin_scratch_address(void **out) {
     std::lock_guard<std::mutex> lock(g_bin_scratch_mutex);
     if (g_bin_scratch_addr[dev] == nullptr) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess || p == nullptr)
+        if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess || p == nullptr) {
+            // take the (non-sticky) error off the runtime's last-error slot so
+            // that a later, unrelated launch check does not report it
+            cudaGetLastError();
             return MG_ERR_CUDA;
+        }
         g_bin_scratch_addr[dev] = p;
     }
     *out = g_bin_scratch_addr[dev];

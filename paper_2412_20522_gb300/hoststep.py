@@ -6,7 +6,9 @@ parameter gradient) back to pinned host memory.  The steps are pipelined
 over three CUDA streams: the inputs of step i+1 travel while step i computes,
 and the gradients of step i travel back while step i+1 computes.  Device
 input and output buffers are double-buffered; events order every reuse.
-All compute is the libmaskgs step (``Rasterizer``).
+All compute is the libmaskgs step: by default each slot replays its own
+captured CUDA graph of the whole step (``autotune.GraphStep``, no launch
+gaps); ``graph=False`` issues the same kernels one by one (``Rasterizer``).
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ from .rasterize import PARAM_NAMES, RasterConfig, Rasterizer
 
 class HostPipeline:
     def __init__(self, host_params: dict, host_target: torch.Tensor, cams, cfg: RasterConfig,
-                 device="cuda", view_ranges=None):
+                 device="cuda", view_ranges=None, graph: bool = True):
         self.dev = torch.device(device)
         self.cams, self.cfg, self.view_ranges = cams, cfg, view_ranges
         for k, t in host_params.items():
@@ -46,12 +48,28 @@ class HostPipeline:
         self.ev_in = [None, None]       # inputs of slot b on the device
         self.ev_comp = [None, None]     # step of slot b computed (inputs free, outputs ready)
         self.ev_out = [None, None]      # outputs of slot b on the host (device outputs free)
-        # size the instance buffers once (a synchronising forward)
+        # both slots' inputs, then (eager form) size the instance buffers once
+        # with a synchronising forward; each GraphStep sizes its own
         with torch.cuda.stream(self.compute):
-            for k in PARAM_NAMES:
-                self.params[0][k].copy_(host_params[k])
-            self.rast.forward(self.params[0], cams, cfg, view_ranges=view_ranges, check=True)
+            for b in range(2):
+                for k in PARAM_NAMES:
+                    self.params[b][k].copy_(host_params[k])
+                self.target[b].copy_(host_target)
+            if not graph:
+                self.rast.forward(self.params[0], cams, cfg, view_ranges=view_ranges, check=True)
         torch.cuda.synchronize(self.dev)
+        self.graphs = None
+        if graph:
+            # one captured step per slot, reading that slot's inputs and
+            # writing its own gradients, image and loss
+            from .autotune import GraphStep
+            self.graphs = [GraphStep(self.params[b], cams, cfg, self.target[b],
+                                     view_ranges=view_ranges) for b in range(2)]
+            for b in range(2):
+                self.grads[b] = self.graphs[b].grads
+                self.image[b] = self.graphs[b].image
+                self.loss[b] = self.graphs[b].loss
+            torch.cuda.synchronize(self.dev)
         self.i = 0
 
     def h2d_bytes(self) -> int:
@@ -79,12 +97,15 @@ class HostPipeline:
             self.compute.wait_event(self.ev_in[b])
             if self.ev_out[b] is not None:
                 self.compute.wait_event(self.ev_out[b])
-            img, loss, dimg = self.rast.forward_l1(self.params[b], self.cams, self.cfg,
-                                                   self.target[b], view_ranges=self.view_ranges,
-                                                   check=False)
-            self.rast.backward(dimg, self.grads[b])
-            self.image[b].copy_(img)
-            self.loss[b].copy_(loss)
+            if self.graphs is not None:
+                self.graphs[b].replay()
+            else:
+                img, loss, dimg = self.rast.forward_l1(self.params[b], self.cams, self.cfg,
+                                                       self.target[b],
+                                                       view_ranges=self.view_ranges, check=False)
+                self.rast.backward(dimg, self.grads[b])
+                self.image[b].copy_(img)
+                self.loss[b].copy_(loss)
             self.ev_comp[b] = torch.cuda.Event()
             self.ev_comp[b].record(self.compute)
         # outputs back to the host

@@ -336,21 +336,53 @@ class Rasterizer:
         abi.mg_mask_loss(s["splats"], s["views"], s["V"], s["cfg"], loss, self._stream())
         return loss
 
+    # -- state handed to a pending backward -------------------------------------
+    # Buffers a backward reads: the splat records and per-Gaussian mask state,
+    # the sorted instance lists, tile ranges and launch order, and the
+    # per-pixel final transmittance and stop index.
+    _STATE_BUFFERS = ("record", "tiles", "radius", "clamp", "bin_record", "mask", "mask_soft",
+                      "mask_count", "depth_key", "keys", "vals", "keys_alt", "vals_alt",
+                      "ranges", "tile_order", "final_T", "n_contrib")
+
+    def take_state(self) -> dict:
+        """Detach the last forward's state from this Rasterizer: the buffers
+        it points into move to the returned state (the next forward allocates
+        new ones), so a later forward cannot overwrite what a pending backward
+        of this one reads.  Pass it to ``backward(state=...)``."""
+        s = self._state
+        if s is None:
+            raise RuntimeError("take_state: no forward state (inference forwards keep none)")
+        s = dict(s)
+        s["buffers"] = {k: self._buf.pop(k) for k in self._STATE_BUFFERS if k in self._buf}
+        self._state = None
+        return s
+
     # -- backward -------------------------------------------------------------
     def backward(self, dL_dimage, out: dict | None = None, stage_events=None,
-                 count_iterations=False):
-        """Gradients of <dL_dimage, image> w.r.t. every parameter (overwritten
-        into ``out`` when given)."""
-        s = self._state
+                 count_iterations=False, state: dict | None = None, lambda_m=None):
+        """Gradients of <dL_dimage, image> (+ lambda_m L_m when the
+        configuration's lambda_m is set) w.r.t. every parameter, overwritten
+        into ``out`` when given.  ``state``: a forward's state from
+        ``take_state`` (default: this Rasterizer's last forward).
+        ``lambda_m``: overrides the weight of the mask-loss gradient."""
+        s = state if state is not None else self._state
+        if s is None:
+            raise RuntimeError("backward: no forward state (its state was taken, or the "
+                               "forward was an inference forward)")
+        buf = s["buffers"] if "buffers" in s else self._buf
         stream = self._stream()
         ev = _Events(stage_events)
+        cfg = s["cfg"]
+        if lambda_m is not None and float(lambda_m) != cfg.lambda_m:
+            cfg = abi.mg_raster_cfg.from_buffer_copy(cfg)
+            cfg.lambda_m = float(lambda_m)
         grad2d = self._get("grad2d", s["R"] * abi.MG_GRAD2D_FLOATS, torch.float32)
         ev.begin("render_bwd")
         if count_iterations:
             self.bwd_count.zero_()
         abi.mg_render_backward(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"],
-                               s["views"], s["V"], s["cfg"], self._buf["final_T"],
-                               self._buf["n_contrib"], dL_dimage, grad2d,
+                               s["views"], s["V"], cfg, buf["final_T"],
+                               buf["n_contrib"], dL_dimage, grad2d,
                                self.bwd_count if count_iterations else None, stream)
         if out is None:
             out = {k: torch.empty(s["params"][k].shape, dtype=torch.float32, device=self.device)
@@ -360,7 +392,7 @@ class Rasterizer:
         for k in PARAM_NAMES:
             setattr(pg, k, out[k].data_ptr())
         ev.begin("preprocess_bwd")
-        abi.mg_preprocess_backward(s["g"], s["views"], s["V"], s["cfg"], s["splats"], grad2d, pg,
+        abi.mg_preprocess_backward(s["g"], s["views"], s["V"], cfg, s["splats"], grad2d, pg,
                                    stream)
         ev.end("preprocess_bwd")
         return out
@@ -386,36 +418,63 @@ class Rasterizer:
 
 
 class MaskedRasterize(torch.autograd.Function):
-    """images = MaskedRasterize.apply(means, log_scales, quats, opacity_logit,
-    sh, mask_logits, rasterizer, cams, cfg) -- the concatenated per-view
-    images; the backward is the hand-written one of libmaskgs."""
+    """(images, mask_loss) = MaskedRasterize.apply(means, log_scales, quats,
+    opacity_logit, sh, mask_logits, rasterizer, cams, cfg, view_ranges).
+
+    images: the concatenated per-view images (Eq. 3-4); mask_loss:
+    lambda_m L_m of Eq. 7-8 (a 0-d tensor, zero when cfg.lambda_m is 0).  The
+    backward is the hand-written one of libmaskgs: Eq. 6 and Appendix A for
+    the mask, the chain rule to every parameter, and the straight-through
+    Gumbel-softmax (Sec. 3.3) to the existence scores, the mask loss's
+    gradient scaled by the gradient that reaches the mask-loss output.
+
+    Each forward detaches its state from the Rasterizer (``take_state``), so
+    several forwards may be pending on one Rasterizer before their backwards
+    run, in any order."""
 
     @staticmethod
-    def forward(ctx, means, log_scales, quats, opacity_logit, sh, mask_logits, rast, cams, cfg):
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, mask_logits, rast, cams, cfg,
+                view_ranges):
         params = dict(means=means.detach(), log_scales=log_scales.detach(),
                       quats=quats.detach(), opacity_logit=opacity_logit.detach(),
                       sh=sh.detach(), mask_logits=mask_logits.detach())
-        img = rast.forward(params, cams, cfg)
+        img = rast.forward(params, cams, cfg, view_ranges=view_ranges)
+        ml = torch.zeros((), dtype=torch.float32, device=rast.device)
+        if cfg.lambda_m != 0.0:
+            ml = rast.mask_loss().reshape(()).clone()
         ctx.rast = rast
-        return img.clone()
+        ctx.state = rast.take_state()
+        ctx.lambda_m = float(cfg.lambda_m)
+        return img.clone(), ml
 
     @staticmethod
-    def backward(ctx, dimg):
-        out = ctx.rast.backward(dimg.contiguous())
-        p = ctx.rast._state["params"]
+    def backward(ctx, dimg, dml):
+        state = ctx.state
+        lam = 0.0
+        if ctx.lambda_m != 0.0 and dml is not None:
+            lam = ctx.lambda_m * float(dml.item())
+        if dimg is None:
+            dimg = torch.zeros(3 * state["pix"], dtype=torch.float32, device=ctx.rast.device)
+        out = ctx.rast.backward(dimg.contiguous().float(), state=state, lambda_m=lam)
+        p = state["params"]
         # gradients are computed in FP32; autograd wants the parameters' dtype
         g = [out[k].to(p[k].dtype) for k in PARAM_NAMES]
-        return (*g, None, None, None)
+        return (*g, None, None, None, None)
 
 
-def rasterize(params: dict, cams, cfg: RasterConfig, rast: Rasterizer | None = None):
-    """Differentiable masked rasterisation of ``params`` (float32 CUDA tensors)
-    for ``cams``; returns a list of [3, H, W] images."""
+def rasterize(params: dict, cams, cfg: RasterConfig, rast: Rasterizer | None = None,
+              view_ranges=None, return_mask_loss: bool = False):
+    """Differentiable masked rasterisation of ``params`` (CUDA tensors: means
+    and mask logits FP32, the other attributes FP32, BF16 or FP16) for
+    ``cams``; returns a list of [3, H, W] images, and with
+    ``return_mask_loss`` also lambda_m L_m (Eq. 7-8), a differentiable 0-d
+    tensor to add to the render loss (Eq. 8)."""
     rast = rast or Rasterizer(params["means"].device)
-    flat = MaskedRasterize.apply(*(params[k] for k in PARAM_NAMES), rast, cams, cfg)
+    flat, ml = MaskedRasterize.apply(*(params[k] for k in PARAM_NAMES), rast, cams, cfg,
+                                     view_ranges)
     out, o = [], 0
     for c in cams:
         n = 3 * c.width * c.height
         out.append(flat[o:o + n].view(3, c.height, c.width))
         o += n
-    return out
+    return (out, ml) if return_mask_loss else out

@@ -1,7 +1,8 @@
 """The pipelined host-data stepper gives every step's image, loss and
 gradients on the host equal to those of a plain device step (images bit for
 bit; gradients and loss to atomic-summation rounding), with several steps in
-flight."""
+flight -- each slot replaying its captured graph, or issuing the kernels
+eagerly."""
 import numpy as np
 import pytest
 import torch
@@ -12,7 +13,8 @@ from paper_2412_20522_gb300 import scenes
 pytestmark = pytest.mark.gpu
 
 
-def test_pipelined_steps_match_device_step():
+@pytest.mark.parametrize("graph", [True, False])
+def test_pipelined_steps_match_device_step(graph):
     from paper_2412_20522_gb300.hoststep import HostPipeline
     from paper_2412_20522_gb300.rasterize import PARAM_NAMES, RasterConfig, Rasterizer
     g = scenes.cluster_gaussians(40_000, seed=5, centre_radius=1.5, reject_radius=2.0,
@@ -31,7 +33,7 @@ def test_pipelined_steps_match_device_step():
     ref_grads = {k: v.cpu().numpy() for k, v in ref.items()}
 
     host = {k: v.cpu().pin_memory() for k, v in p.items()}
-    hp = HostPipeline(host, tgt.pin_memory(), cams, cfg)
+    hp = HostPipeline(host, tgt.pin_memory(), cams, cfg, graph=graph)
     slots = [hp.step() for _ in range(5)]
     for b in slots[-2:]:
         h_img, h_loss, h_grads = hp.results(b)

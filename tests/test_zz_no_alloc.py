@@ -84,3 +84,47 @@ def test_noalloc_rejects_more_records_than_its_array_holds():
     assert e.value.status == abi.MG_ERR_INVALID_ARG
     assert abi.load().mg_bin_noalloc(None, ok, 1, RasterConfig().c(), None, None, None, None, 0,
                                      None, None, None) == abi.MG_ERR_INVALID_ARG
+
+
+def test_noalloc_at_its_largest_size():
+    """Exactly 2^24 records, the most the fixed array holds: the request passes
+    the size check and its scan uses the array up to its last word.  Counting
+    mode (capacity 0: offsets and the total only, no instance is written), so
+    only the tile counts are needed; the result equals mg_bin's, twice."""
+    from paper_2412_20522_gb300 import abi
+    from paper_2412_20522_gb300.rasterize import RasterConfig, make_views
+    _, cams, _ = scenes.tiny_workload(100)
+    dev = torch.device("cuda")
+    R = 1 << 24
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    tiles = torch.randint(0, 4, (R,), generator=gen, dtype=torch.int32).to(dev)
+    dummy = torch.zeros(16, dtype=torch.float32, device=dev)     # not read in counting mode
+    s = abi.mg_splats()
+    s.tiles_touched = tiles.data_ptr()
+    s.bin_record = dummy.data_ptr()
+    views = make_views(cams, [(0, R)])
+    cfg = RasterConfig().c()
+    stream = C_stream()
+    ws = torch.empty(abi.mg_bin_workspace_bytes(R), dtype=torch.uint8, device=dev)
+    results = []
+    for noalloc in (False, True, True):
+        offsets = torch.full((R,), -1, dtype=torch.int32, device=dev)
+        n = torch.zeros(1, dtype=torch.int64, device=dev)
+        status = torch.zeros(2, dtype=torch.int64, device=dev)
+        if noalloc:
+            abi.mg_bin_noalloc(s, views, 1, cfg, None, offsets, None, None, 0, n, status, stream)
+        else:
+            abi.mg_bin(s, views, 1, cfg, None, offsets, None, None, 0, n, ws, ws.numel(), status,
+                       stream)
+        torch.cuda.synchronize()
+        assert int(status[0].item()) == 0
+        results.append((int(n.item()), offsets.cpu().numpy()))
+    assert results[0][0] == int(tiles.sum().item())
+    for k, off in results[1:]:
+        assert k == results[0][0]
+        assert np.array_equal(off, results[0][1])
+
+
+def C_stream():
+    import ctypes
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
