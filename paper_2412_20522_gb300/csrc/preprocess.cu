@@ -412,21 +412,24 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
 // ---------------------------------------------------------------------------
 // Backward of the covariance chain: conic Q = Sigma_bar^-1 -> Sigma_bar =
 // P P^T + 0.3 I -> P = T M (T = J W, M = R diag(s)) -> s = exp(log s),
-// R(q / |q|), J(t).  Templated on the arithmetic type: FP32 in general, FP64
-// for needle splats (lambda_1 / lambda_2 above kFp64Condition) whose FP32
-// factor P cannot resolve the thin direction (the oracle shows relative
-// gradient errors near 2e-3 there in FP32, 4e-5 with this split).
+// R(q / |q|), J(t).  FP32 throughout except the 2x2 inversion's backward
+// dSigma = -Q Ghat Q (Ghat = dL/dQ) for ill-conditioned splats
+// (lambda_1 / lambda_2 above kFp64Condition): there Q's two eigenvalues are
+// far apart and the FP32 products leave dSigma's major-axis component as
+// rounding noise (about eps lambda_1^2 / lambda_2^2 relative), which P then
+// carries into the long axis's scale and rotation gradients.  Q and dSigma
+// are then formed in FP64 from the FP32 a, b, c and Cauchy-Binet determinant
+// (an emulation of this chain on the benchmark view against the FP64 oracle:
+// relative L2 1.0e-3 / 2.0e-3 on dL/dlog_scales / dL/dquats in FP32 alone,
+// 3.5e-6 / 6.7e-5 with this step in FP64 above the condition 100).
 // ---------------------------------------------------------------------------
-constexpr float kFp64Condition = 1000.0f;
+constexpr float kFp64Condition = 100.0f;
 
-template <typename F>
 struct CovState {
-    F P[2][3], M[3][3], R[3][3], T[2][3], s[3], qn[4], nrm, tzs, txc, tyc;
-    F Q00, Q01, Q11;
+    float P[2][3], M[3][3], R[3][3], T[2][3], s[3], qn[4], nrm, tzs, txc, tyc;
 };
 
-__device__ __forceinline__ void cov_state_fp32(const Splat32 &S, float ux, float uy, float l1,
-                                               float l2, CovState<float> &F) {
+__device__ __forceinline__ void cov_state(const Splat32 &S, CovState &F) {
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -449,88 +452,51 @@ __device__ __forceinline__ void cov_state_fp32(const Splat32 &S, float ux, float
     F.tzs = S.tzs;
     F.txc = S.txc;
     F.tyc = S.tyc;
-    // Sigma^-1 from the eigen form (accurate for thin splats)
-    const float w1 = 1.0f / l1, w2 = 1.0f / l2;
-    F.Q00 = w1 * ux * ux + w2 * uy * uy;
-    F.Q01 = (w1 - w2) * ux * uy;
-    F.Q11 = w1 * uy * uy + w2 * ux * ux;
 }
 
-// FP64 recomputation of the same quantities from the FP32 inputs (the clamp
-// decisions are the FP32 path's).
-__device__ __noinline__ void cov_state_fp64(const mg_camera &C, float x, float y, float z,
-                                            const float ls[3], const float q[4], bool clampx,
-                                            bool clampy, CovState<double> &D) {
-    const float *V = C.viewmat;
-    const double tx = (double)V[0] * x + (double)V[1] * y + (double)V[2] * z + V[3];
-    const double ty = (double)V[4] * x + (double)V[5] * y + (double)V[6] * z + V[7];
-    const double tz = (double)V[8] * x + (double)V[9] * y + (double)V[10] * z + V[11];
-    D.tzs = tz;
-    const double limx = 1.3 * (0.5 * C.width / (double)C.fx);
-    const double limy = 1.3 * (0.5 * C.height / (double)C.fy);
-    D.txc = clampx ? (tx > 0 ? limx : -limx) * tz : tx;
-    D.tyc = clampy ? (ty > 0 ? limy : -limy) * tz : ty;
-    const double j00 = C.fx / tz, j02 = -(double)C.fx * D.txc / (tz * tz);
-    const double j11 = C.fy / tz, j12 = -(double)C.fy * D.tyc / (tz * tz);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        D.T[0][k] = j00 * V[k] + j02 * V[8 + k];
-        D.T[1][k] = j11 * V[4 + k] + j12 * V[8 + k];
-    }
-    double w = q[0], qx = q[1], qy = q[2], qz = q[3];
-    D.nrm = sqrt(w * w + qx * qx + qy * qy + qz * qz);
-    w /= D.nrm; qx /= D.nrm; qy /= D.nrm; qz /= D.nrm;
-    D.qn[0] = w; D.qn[1] = qx; D.qn[2] = qy; D.qn[3] = qz;
-    D.R[0][0] = 1 - 2 * (qy * qy + qz * qz); D.R[0][1] = 2 * (qx * qy - w * qz);
-    D.R[0][2] = 2 * (qx * qz + w * qy);      D.R[1][0] = 2 * (qx * qy + w * qz);
-    D.R[1][1] = 1 - 2 * (qx * qx + qz * qz); D.R[1][2] = 2 * (qy * qz - w * qx);
-    D.R[2][0] = 2 * (qx * qz - w * qy);      D.R[2][1] = 2 * (qy * qz + w * qx);
-    D.R[2][2] = 1 - 2 * (qx * qx + qy * qy);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) D.s[k] = exp((double)ls[k]);
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) D.M[j][k] = D.R[j][k] * D.s[k];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            D.P[i][k] = D.T[i][0] * D.M[0][k] + D.T[i][1] * D.M[1][k] + D.T[i][2] * D.M[2][k];
-    const double n0 = D.P[0][0] * D.P[0][0] + D.P[0][1] * D.P[0][1] + D.P[0][2] * D.P[0][2];
-    const double n1 = D.P[1][0] * D.P[1][0] + D.P[1][1] * D.P[1][1] + D.P[1][2] * D.P[1][2];
-    const double a = n0 + 0.3, c = n1 + 0.3;
-    const double b = D.P[0][0] * D.P[1][0] + D.P[0][1] * D.P[1][1] + D.P[0][2] * D.P[1][2];
-    const double m01 = D.P[0][0] * D.P[1][1] - D.P[0][1] * D.P[1][0];
-    const double m02 = D.P[0][0] * D.P[1][2] - D.P[0][2] * D.P[1][0];
-    const double m12 = D.P[0][1] * D.P[1][2] - D.P[0][2] * D.P[1][1];
-    const double det = m01 * m01 + m02 * m02 + m12 * m12 + 0.3 * (n0 + n1) + 0.09;
-    D.Q00 = c / det;
-    D.Q01 = -b / det;
-    D.Q11 = a / det;
-}
-
+// dSigma = -Q Ghat Q, Ghat = [[G_a, G_b / 2], [G_b / 2, G_c]] (the conic's
+// off-diagonal entry appears once in the quadratic form), in the type F.
 template <typename F>
-__device__ __forceinline__ void cov_backward(const CovState<F> &S, const mg_camera &C, bool clampx,
-                                             bool clampy, float dca, float dcb, float dcc,
+__device__ __forceinline__ void inverse_backward(F Q00, F Q01, F Q11, float dca, float dcb,
+                                                 float dcc, float &dS00, float &dS01,
+                                                 float &dS11) {
+    const F G00 = dca, G01 = F(0.5) * (F)dcb, G11 = dcc;
+    const F A00 = Q00 * G00 + Q01 * G01, A01 = Q00 * G01 + Q01 * G11;
+    const F A10 = Q01 * G00 + Q11 * G01, A11 = Q01 * G01 + Q11 * G11;
+    dS00 = (float)(-(A00 * Q00 + A01 * Q01));
+    dS01 = (float)(-(A00 * Q01 + A01 * Q11));
+    dS11 = (float)(-(A10 * Q01 + A11 * Q11));
+}
+
+// The inversion's backward for one splat: FP32 from the eigen form when it is
+// well conditioned, FP64 from (a, b, c, det) when it is not.
+__device__ __forceinline__ void conic_backward(const Splat32 &S, float ux, float uy, float l1,
+                                               float l2, float dca, float dcb, float dcc,
+                                               float &dS00, float &dS01, float &dS11) {
+    if (l1 > kFp64Condition * l2) {
+        const double id = 1.0 / (double)S.det;
+        inverse_backward<double>((double)S.c * id, -(double)S.b * id, (double)S.a * id, dca, dcb,
+                                 dcc, dS00, dS01, dS11);
+    } else {
+        const float w1 = 1.0f / l1, w2 = 1.0f / l2;
+        inverse_backward<float>(w1 * ux * ux + w2 * uy * uy, (w1 - w2) * ux * uy,
+                                w1 * uy * uy + w2 * ux * ux, dca, dcb, dcc, dS00, dS01, dS11);
+    }
+}
+
+__device__ __forceinline__ void cov_backward(const CovState &S, const mg_camera &C, bool clampx,
+                                             bool clampy, float dS00, float dS01, float dS11,
                                              float d_ls[3], float d_q[4], float dL_dt[3]) {
     const float *V = C.viewmat;
-    // dL/dSigma = -Q Ghat Q with Ghat = [[G_a, G_b/2], [G_b/2, G_c]]
-    const F G00 = dca, G01 = F(0.5) * (F)dcb, G11 = dcc;
-    const F A00 = S.Q00 * G00 + S.Q01 * G01, A01 = S.Q00 * G01 + S.Q01 * G11;
-    const F A10 = S.Q01 * G00 + S.Q11 * G01, A11 = S.Q01 * G01 + S.Q11 * G11;
-    const F dS00 = -(A00 * S.Q00 + A01 * S.Q01);
-    const F dS01 = -(A00 * S.Q01 + A01 * S.Q11);
-    const F dS11 = -(A10 * S.Q01 + A11 * S.Q11);
     // Sigma_bar = P P^T + 0.3 I  =>  dP = 2 dSigma P
-    F dP[2][3];
+    float dP[2][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        dP[0][k] = F(2) * (dS00 * S.P[0][k] + dS01 * S.P[1][k]);
-        dP[1][k] = F(2) * (dS01 * S.P[0][k] + dS11 * S.P[1][k]);
+        dP[0][k] = 2.0f * (dS00 * S.P[0][k] + dS01 * S.P[1][k]);
+        dP[1][k] = 2.0f * (dS01 * S.P[0][k] + dS11 * S.P[1][k]);
     }
     // P = T M:  dT = dP M^T, dM = T^T dP
-    F dT[2][3], dM[3][3];
+    float dT[2][3], dM[3][3];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -541,51 +507,51 @@ __device__ __forceinline__ void cov_backward(const CovState<F> &S, const mg_came
 #pragma unroll
         for (int k = 0; k < 3; ++k) dM[j][k] = S.T[0][j] * dP[0][k] + S.T[1][j] * dP[1][k];
     // M = R diag(s), s = exp(log s)
-    F dR[3][3];
+    float dR[3][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int k = 0; k < 3; ++k) dR[j][k] = dM[j][k] * S.s[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const F ds = dM[0][k] * S.R[0][k] + dM[1][k] * S.R[1][k] + dM[2][k] * S.R[2][k];
-        d_ls[k] += (float)(ds * S.s[k]);
+        const float ds = dM[0][k] * S.R[0][k] + dM[1][k] * S.R[1][k] + dM[2][k] * S.R[2][k];
+        d_ls[k] += ds * S.s[k];
     }
     // R(q_hat), then q_hat = q / |q|
     {
-        const F w = S.qn[0], qx = S.qn[1], qy = S.qn[2], qz = S.qn[3];
-        const F gw = F(2) * (qz * (dR[1][0] - dR[0][1]) + qy * (dR[0][2] - dR[2][0]) +
-                             qx * (dR[2][1] - dR[1][2]));
-        const F gx = F(2) * (qy * (dR[1][0] + dR[0][1]) + qz * (dR[2][0] + dR[0][2]) +
-                             w * (dR[2][1] - dR[1][2])) - F(4) * qx * (dR[1][1] + dR[2][2]);
-        const F gy = F(2) * (qx * (dR[1][0] + dR[0][1]) + w * (dR[0][2] - dR[2][0]) +
-                             qz * (dR[1][2] + dR[2][1])) - F(4) * qy * (dR[0][0] + dR[2][2]);
-        const F gz = F(2) * (w * (dR[1][0] - dR[0][1]) + qx * (dR[2][0] + dR[0][2]) +
-                             qy * (dR[1][2] + dR[2][1])) - F(4) * qz * (dR[0][0] + dR[1][1]);
-        const F dot = gw * w + gx * qx + gy * qy + gz * qz;
-        const F in = F(1) / S.nrm;
-        d_q[0] += (float)((gw - dot * w) * in);
-        d_q[1] += (float)((gx - dot * qx) * in);
-        d_q[2] += (float)((gy - dot * qy) * in);
-        d_q[3] += (float)((gz - dot * qz) * in);
+        const float w = S.qn[0], qx = S.qn[1], qy = S.qn[2], qz = S.qn[3];
+        const float gw = 2.0f * (qz * (dR[1][0] - dR[0][1]) + qy * (dR[0][2] - dR[2][0]) +
+                                 qx * (dR[2][1] - dR[1][2]));
+        const float gx = 2.0f * (qy * (dR[1][0] + dR[0][1]) + qz * (dR[2][0] + dR[0][2]) +
+                                 w * (dR[2][1] - dR[1][2])) - 4.0f * qx * (dR[1][1] + dR[2][2]);
+        const float gy = 2.0f * (qx * (dR[1][0] + dR[0][1]) + w * (dR[0][2] - dR[2][0]) +
+                                 qz * (dR[1][2] + dR[2][1])) - 4.0f * qy * (dR[0][0] + dR[2][2]);
+        const float gz = 2.0f * (w * (dR[1][0] - dR[0][1]) + qx * (dR[2][0] + dR[0][2]) +
+                                 qy * (dR[1][2] + dR[2][1])) - 4.0f * qz * (dR[0][0] + dR[1][1]);
+        const float dot = gw * w + gx * qx + gy * qy + gz * qz;
+        const float in = 1.0f / S.nrm;
+        d_q[0] += (gw - dot * w) * in;
+        d_q[1] += (gx - dot * qx) * in;
+        d_q[2] += (gy - dot * qy) * in;
+        d_q[3] += (gz - dot * qz) * in;
     }
     // T = J W:  dJ = dT W^T ; J = [[fx/tz, 0, -fx txc/tz^2], [0, fy/tz, -fy tyc/tz^2]]
-    F dJ00 = 0, dJ02 = 0, dJ11 = 0, dJ12 = 0;
+    float dJ00 = 0.0f, dJ02 = 0.0f, dJ11 = 0.0f, dJ12 = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        dJ00 += dT[0][k] * (F)V[k];
-        dJ02 += dT[0][k] * (F)V[8 + k];
-        dJ11 += dT[1][k] * (F)V[4 + k];
-        dJ12 += dT[1][k] * (F)V[8 + k];
+        dJ00 += dT[0][k] * V[k];
+        dJ02 += dT[0][k] * V[8 + k];
+        dJ11 += dT[1][k] * V[4 + k];
+        dJ12 += dT[1][k] * V[8 + k];
     }
-    const F fx = C.fx, fy = C.fy;
-    const F itz = F(1) / S.tzs, itz2 = itz * itz, itz3 = itz2 * itz;
+    const float fx = C.fx, fy = C.fy;
+    const float itz = 1.0f / S.tzs, itz2 = itz * itz, itz3 = itz2 * itz;
     // d J02 / d tz: 2 fx txc / tz^3 unclamped, fx txc / tz^3 clamped
-    dL_dt[2] += (float)(-dJ00 * fx * itz2 - dJ11 * fy * itz2 +
-                        dJ02 * fx * S.txc * itz3 * (clampx ? F(1) : F(2)) +
-                        dJ12 * fy * S.tyc * itz3 * (clampy ? F(1) : F(2)));
-    if (!clampx) dL_dt[0] += (float)(-dJ02 * fx * itz2);
-    if (!clampy) dL_dt[1] += (float)(-dJ12 * fy * itz2);
+    dL_dt[2] += -dJ00 * fx * itz2 - dJ11 * fy * itz2 +
+                dJ02 * fx * S.txc * itz3 * (clampx ? 1.0f : 2.0f) +
+                dJ12 * fy * S.tyc * itz3 * (clampy ? 1.0f : 2.0f);
+    if (!clampx) dL_dt[0] += -dJ02 * fx * itz2;
+    if (!clampy) dL_dt[1] += -dJ12 * fy * itz2;
 }
 
 __device__ __forceinline__ void prefetch_l2(const void *p) {
@@ -715,16 +681,11 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
             // ---- conic -> Sigma_bar -> P = J W R S -> scales, rotation, J
             float ux, uy, l1, l2;
             eigen2(S, ux, uy, l1, l2);
-            if (l1 > kFp64Condition * l2) {
-                // needle splat: the FP32 factor cannot resolve its thin direction
-                CovState<double> D;
-                cov_state_fp64(C, x, y, z, ls, q, S.clampx, S.clampy, D);
-                cov_backward<double>(D, C, S.clampx, S.clampy, g0.z, g0.w, g1.x, d_ls, d_q, dL_dt);
-            } else {
-                CovState<float> F;
-                cov_state_fp32(S, ux, uy, l1, l2, F);
-                cov_backward<float>(F, C, S.clampx, S.clampy, g0.z, g0.w, g1.x, d_ls, d_q, dL_dt);
-            }
+            float dS00, dS01, dS11;
+            conic_backward(S, ux, uy, l1, l2, g0.z, g0.w, g1.x, dS00, dS01, dS11);
+            CovState F;
+            cov_state(S, F);
+            cov_backward(F, C, S.clampx, S.clampy, dS00, dS01, dS11, d_ls, d_q, dL_dt);
             // t = W p + t_cam  =>  dp += W^T dt
 #pragma unroll
             for (int k = 0; k < 3; ++k)

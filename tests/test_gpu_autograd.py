@@ -21,6 +21,8 @@ pytestmark = pytest.mark.gpu
 
 GRAD_TOL = 1e-3
 EPS = 1e-4
+# two GPU runs of the same gradient: float-atomic summation order differs
+ATOMIC_TOL = 1e-4
 
 
 def _workload(which):
@@ -68,7 +70,9 @@ def test_autograd_step_matches_oracle(which):
     print(which, "autograd grad rel L2", errs)
     assert all(e <= GRAD_TOL for e in errs.values()), errs
 
-    # the same gradients through the plain C-ABI sequence (no autograd)
+    # the same gradients through the plain C-ABI sequence (no autograd), to
+    # the rounding of float atomics (their order differs from run to run, and
+    # the chain to scales and rotations of thin splats magnifies it)
     rast = Rasterizer()
     rast.forward({k: p.detach() for k, p in params.items()}, cams, cfg)
     flat = torch.as_tensor(np.concatenate([d.reshape(-1) for d in dimgs]).astype(np.float32))
@@ -76,7 +80,7 @@ def test_autograd_step_matches_oracle(which):
     torch.cuda.synchronize()
     for k in PARAMS:
         e = rel_l2(params[k].grad.cpu().numpy(), direct[k].cpu().numpy())
-        assert e <= 1e-5, (k, e)
+        assert e <= ATOMIC_TOL, (k, e)
 
 
 def test_two_pending_forwards_on_one_rasterizer():
@@ -115,7 +119,7 @@ def test_two_pending_forwards_on_one_rasterizer():
     torch.cuda.synchronize()
     for k in PARAMS:
         e = rel_l2(params[k].grad.cpu().numpy(), ref[k].numpy())
-        assert e <= 1e-5, (k, e)
+        assert e <= ATOMIC_TOL, (k, e)
 
 
 def test_autograd_reduced_storage_returns_parameter_dtype():
@@ -138,4 +142,4 @@ def test_autograd_reduced_storage_returns_parameter_dtype():
     for k in PARAMS:
         assert params[k].grad.dtype == params[k].dtype
         e = rel_l2(params[k].grad.float().cpu().numpy(), ref[k].cpu().numpy())
-        assert e <= (1e-2 if k in STORED else 1e-5), (k, e)
+        assert e <= (1e-2 if k in STORED else ATOMIC_TOL), (k, e)

