@@ -582,7 +582,7 @@ def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
     single-view form measured above (same GPU, same run)."""
     import torch
     from paper_2412_20522_gb300 import scenes
-    from paper_2412_20522_gb300.autotune import GraphStep, autotune_tile, time_step
+    from paper_2412_20522_gb300.autotune import GraphStep, autotune, time_step
     from paper_2412_20522_gb300.rasterize import RasterConfig
 
     forms = {"plain_fp32_single_view": {"ms_per_step": plain_ms,
@@ -593,12 +593,14 @@ def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
     cams8 = [scenes.ring_camera(2 * math.pi * k / 8, 4.0, 1557, 1038, 1150.0) for k in range(8)]
     p = _device_params(g, dev)
     tgt8 = torch.as_tensor(np.concatenate([target.reshape(-1)] * 8)).to(dev)
-    tile = autotune_tile(p, cams8, tgt8, steps=3)
-    gs = GraphStep(p, cams8, RasterConfig(tile_w=tile[0], tile_h=tile[1]), tgt8)
+    tuned = autotune(p, cams8, tgt8, steps=3)
+    gs = GraphStep(p, cams8, tuned, tgt8)
     ms = time_step(gs.replay, steps=steps)
     pix = 8 * 1557 * 1038
-    forms["multiview_graph"] = {"views": 8, "tile": f"{tile[0]}x{tile[1]}", "ms_per_step": ms,
-                                "mpix_per_s": pix / 1e6 / (ms * 1e-3),
+    forms["multiview_graph"] = {"views": 8, "tile": f"{tuned.tile_w}x{tuned.tile_h}",
+                                "sort": tuned.sort,
+                                "staging": [tuned.render_batch, tuned.render_batch_bwd],
+                                "ms_per_step": ms, "mpix_per_s": pix / 1e6 / (ms * 1e-3),
                                 "status": gs.status()}
     del gs, p
     torch.cuda.empty_cache()

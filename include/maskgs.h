@@ -171,6 +171,12 @@ typedef struct {
     int32_t mask_loss;       /* MG_MASK_LOSS_* */
     float ste_logit;         /* MG_MASK_STE threshold on l_0 - l_1 (FP32 comparison) */
     int32_t bin_mode;        /* MG_BIN_* */
+    /* Splats staged in shared memory per batch by the render kernels (a
+     * tuning choice; no result depends on it): render_batch 128 or 256 for
+     * the forward, render_batch_bwd 64 or 128 for the backward, 0 = the
+     * defaults (256, 128); other values return MG_ERR_INVALID_ARG. */
+    int32_t render_batch;
+    int32_t render_batch_bwd;
 } mg_raster_cfg;
 
 /* Per-view preprocess outputs (R = sum_v gaussian_count_v records):
@@ -323,6 +329,31 @@ mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
                   size_t workspace_bytes, int32_t *result_in_alt, uint64_t *d_num_sorted,
                   mg_status_word *d_status, mg_stream_t stream);
 size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);
+/* The lists of mg_sort by another route, one pass over the whole tile id
+ * (Sec. 3.1: each tile's Gaussians in depth order), that needs no depth order
+ * of the records beforehand: the instances (keys = global tile ids, vals =
+ * record indices, as mg_bin writes them, in any order -- mg_bin with a null
+ * order emits them in record order) are grouped by tile by a counting pass
+ * (per-tile counts, their scan, then a scatter of each tile's instances into
+ * its range), and every tile's list is then ordered by (depth_key[record],
+ * record) -- depth_key as mg_preprocess writes it (device u32[R], required).
+ * Pairs keyed 0xFFFFFFFF are dropped.  Outputs: sorted_vals (u32[capacity]):
+ * the records of tile t at [ranges[2t], ranges[2t+1]); *d_num_sorted
+ * (nullable) = the number kept.  The lists equal mg_sort's on depth-ordered
+ * instances bit for bit.  grouped: u32[capacity] scratch (the tile-grouped,
+ * not yet ordered records).  workspace: mg_sort_by_tile_workspace_bytes(
+ * capacity, n_tiles_total) bytes, 16-byte aligned, any content.  When
+ * *d_num_instances exceeds capacity nothing is sorted and every range is
+ * empty.  Lists of up to 4096 records are ordered in shared memory, longer
+ * ones in 4096-record chunks merged in the workspace.  The first call on a
+ * device sets the kernels' shared-memory limit: make it outside stream
+ * capture. */
+mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals, const uint32_t *depth_key,
+                          const uint64_t *d_num_instances, uint64_t capacity,
+                          int64_t n_tiles_total, uint32_t *grouped, uint32_t *sorted_vals,
+                          uint32_t *ranges, void *workspace, size_t workspace_bytes,
+                          uint64_t *d_num_sorted, mg_status_word *d_status, mg_stream_t stream);
+size_t mg_sort_by_tile_workspace_bytes(uint64_t capacity, int64_t n_tiles_total);
 /* Bits of a global tile id for a set of views: ceil(log2(n_tiles_total)), >= 1. */
 int32_t mg_tile_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);
 int64_t mg_total_tiles(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);

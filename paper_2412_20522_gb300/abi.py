@@ -24,7 +24,7 @@ MG_GRAD2D_FLOATS = 12
 
 EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes", "mg_bin",
             "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
-            "mg_sort_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render", "mg_render_l1",
+            "mg_sort_workspace_bytes", "mg_sort_by_tile", "mg_sort_by_tile_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render", "mg_render_l1",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
             "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
@@ -64,7 +64,8 @@ class mg_raster_cfg(C.Structure):
                 ("tau", C.c_float), ("seed", C.c_uint64), ("iteration", C.c_uint64),
                 ("mask_mode", C.c_int32), ("mask_apply", C.c_int32), ("given_mask", C.c_void_p),
                 ("lambda_m", C.c_float), ("mask_loss", C.c_int32), ("ste_logit", C.c_float),
-                ("bin_mode", C.c_int32)]
+                ("bin_mode", C.c_int32), ("render_batch", C.c_int32),
+                ("render_batch_bwd", C.c_int32)]
 
 
 class mg_splats(C.Structure):
@@ -118,6 +119,9 @@ def load(build_if_missing: bool = True):
         "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, vp, C.c_int64, vp,
                          C.c_size_t, _P(C.c_int32), vp, vp, vp]),
         "mg_sort_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int32]),
+        "mg_sort_by_tile": (st, [vp, vp, vp, vp, C.c_uint64, C.c_int64, vp, vp, vp, vp,
+                                 C.c_size_t, vp, vp, vp]),
+        "mg_sort_by_tile_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int64]),
         "mg_tile_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_total_tiles": (C.c_int64, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
         "mg_render": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
@@ -224,6 +228,19 @@ def mg_sort(keys, vals, keys_alt, vals_alt, d_num_instances, capacity, key_bits,
 
 def mg_sort_workspace_bytes(capacity, key_bits) -> int:
     return int(load().mg_sort_workspace_bytes(capacity, key_bits))
+
+
+def mg_sort_by_tile(keys, vals, depth_key, d_num_instances, capacity, n_tiles_total, grouped,
+                    sorted_vals, ranges, workspace, workspace_bytes, d_num_sorted, d_status,
+                    stream):
+    _check("mg_sort_by_tile", load().mg_sort_by_tile(
+        ptr(keys), ptr(vals), ptr(depth_key), ptr(d_num_instances), capacity, n_tiles_total,
+        ptr(grouped), ptr(sorted_vals), ptr(ranges), ptr(workspace), workspace_bytes,
+        ptr(d_num_sorted), ptr(d_status), stream))
+
+
+def mg_sort_by_tile_workspace_bytes(capacity, n_tiles_total) -> int:
+    return int(load().mg_sort_by_tile_workspace_bytes(capacity, n_tiles_total))
 
 
 def mg_tile_bits(views, n_views, cfg) -> int:

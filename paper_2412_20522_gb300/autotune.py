@@ -1,12 +1,22 @@
-"""Tile-shape autotuner and CUDA-graph step runner.
+"""Autotuner of the step's launch choices, and the CUDA-graph step runner.
 
-The tile rectangle (and so the image) depends slightly on the tile shape,
-which is why every shape is parity-tested against the oracle (tests run all
-of 16x16, 8x32 and 32x8).  The autotuner times a full masked forward+backward
-step for each shape and remembers the fastest per (GPU, resolution set,
-Gaussian count) in a JSON cache file.  The staging depth (256 splats per
-batch), the pixels per thread (2) and the sort digit width (8 bits) are
-compile-time constants of libmaskgs, chosen by measurement.
+Three choices change the speed of a masked forward+backward step but no
+result the method defines (each is parity-tested against the oracle):
+
+* the tile shape (16x16, 8x32 or 32x8; the image depends slightly on it
+  through the 3-sigma tile rectangle, which is why every shape has its own
+  oracle parity tests);
+* the staging depth of the render kernels: splats staged in shared memory per
+  batch, 256 or 128 in the forward, 128 or 64 in the backward;
+* the digit width of the tile sort: the depth order of the records followed
+  by a stable sort of the instances in 8-bit tile-id digits ("radix8"), or
+  one counting pass over the whole tile id with each tile's list then put in
+  depth order in shared memory ("bucket").
+
+``autotune`` times a captured step for each choice (coordinate search: the
+tile shape first, then the sort, then the staging depths, each with the
+best so far) and caches the winner per (GPU, resolutions, Gaussian count,
+storage) in a JSON file.
 """
 from __future__ import annotations
 
@@ -18,6 +28,9 @@ import torch
 from .rasterize import PARAM_NAMES, RasterConfig, Rasterizer
 
 TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
+SORTS = ("radix8", "bucket")
+FWD_BATCHES = (256, 128)
+BWD_BATCHES = (128, 64)
 
 
 def cache_path() -> str:
@@ -91,34 +104,62 @@ def time_step(fn, steps=5, warmup=2) -> float:
     return a.elapsed_time(b) / steps
 
 
-def autotune_tile(params, cams, target, base_cfg: RasterConfig | None = None, view_ranges=None,
-                  steps=5, use_cache=True) -> tuple:
-    """Fastest tile shape for this workload (cached)."""
-    key = _key(params, cams)
-    path = cache_path()
-    cache = {}
-    if use_cache and os.path.exists(path):
+TUNED = ("tile_w", "tile_h", "sort", "render_batch", "render_batch_bwd")
+
+
+def _load_cache(path):
+    if os.path.exists(path):
         try:
             with open(path) as fh:
-                cache = json.load(fh)
+                return json.load(fh)
         except (OSError, ValueError):
-            cache = {}
-    if use_cache and key in cache:
-        return tuple(cache[key]["tile"])
+            return {}
+    return {}
+
+
+def autotune(params, cams, target, base_cfg: RasterConfig | None = None, view_ranges=None,
+             steps=5, use_cache=True) -> RasterConfig:
+    """The fastest tile shape, sort digit width and staging depths for this
+    workload (cached), as a RasterConfig built on ``base_cfg``."""
     base = base_cfg or RasterConfig()
+    key = _key(params, cams)
+    path = cache_path()
+    cache = _load_cache(path) if use_cache else {}
+    if use_cache and key in cache and all(k in cache[key] for k in TUNED):
+        return RasterConfig(**{**base.__dict__, **{k: cache[key][k] for k in TUNED}})
     timings = {}
-    for tw, th in TILE_SHAPES:
-        cfg = RasterConfig(**{**base.__dict__, "tile_w": tw, "tile_h": th})
-        gs = GraphStep(params, cams, cfg, target, view_ranges)
-        timings[(tw, th)] = time_step(gs.replay, steps=steps)
-        del gs
-        torch.cuda.empty_cache()
-    best = min(timings, key=timings.get)
-    cache[key] = {"tile": list(best), "ms": {f"{a}x{b}": v for (a, b), v in timings.items()}}
-    try:
-        os.makedirs(os.path.dirname(path), exist_ok=True)
-        with open(path, "w") as fh:
-            json.dump(cache, fh, indent=1)
-    except OSError:
-        pass
-    return best
+
+    def run(choice):
+        name = "{tile_w}x{tile_h}|{sort}|{render_batch}/{render_batch_bwd}".format(**choice)
+        if name not in timings:
+            cfg = RasterConfig(**{**base.__dict__, **choice})
+            gs = GraphStep(params, cams, cfg, target, view_ranges)
+            timings[name] = time_step(gs.replay, steps=steps)
+            del gs
+            torch.cuda.empty_cache()
+        return timings[name]
+
+    best = dict(tile_w=base.tile_w, tile_h=base.tile_h, sort=base.sort,
+                render_batch=base.render_batch or 256, render_batch_bwd=base.render_batch_bwd or 128)
+    searches = ([dict(tile_w=w, tile_h=h) for w, h in TILE_SHAPES],
+                [dict(sort=m) for m in SORTS],
+                [dict(render_batch=b) for b in FWD_BATCHES],
+                [dict(render_batch_bwd=b) for b in BWD_BATCHES])
+    for options in searches:
+        best = min(({**best, **o} for o in options), key=run)
+    cache[key] = {**best, "ms": timings}
+    if use_cache:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as fh:
+                json.dump(cache, fh, indent=1)
+        except OSError:
+            pass
+    return RasterConfig(**{**base.__dict__, **best})
+
+
+def autotune_tile(params, cams, target, base_cfg: RasterConfig | None = None, view_ranges=None,
+                  steps=5, use_cache=True) -> tuple:
+    """The tile shape of ``autotune``'s choice."""
+    cfg = autotune(params, cams, target, base_cfg, view_ranges, steps, use_cache)
+    return cfg.tile_w, cfg.tile_h

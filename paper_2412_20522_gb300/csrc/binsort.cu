@@ -552,6 +552,254 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     return MG_OK;
 }
 
+// --------------------------------------------------------------------------
+// Tile-bucket sort: the instances grouped by tile in one counting pass over
+// the whole tile id (a digit as wide as the key), then every tile's list
+// ordered by (depth key, record index) in shared memory.  The depth order of
+// the records is not needed beforehand, so the instances may come in record
+// order; the lists equal those of the depth sort + stable tile sort.
+//
+//   count    each block counts the kept instances of a contiguous range per
+//            tile in a shared-memory histogram over the range's tile window,
+//            then adds its non-zero bins to the global tile counts
+//   scan     exclusive scan of the tile counts (the tile starts)
+//   scatter  the same ranges again: each block reserves, per tile, a run of
+//            slots after the starts (one global atomic per tile and block),
+//            and places its instances in them (shared-memory atomics, so the
+//            order inside a tile is arbitrary here)
+//   order    one CTA per tile: (depth_key << 32 | record) keys sorted
+//            bitonically in shared memory; lists longer than kTileSortCap are
+//            sorted in kTileSortCap chunks and merged in global scratch
+// --------------------------------------------------------------------------
+constexpr int kBucketThreads = 256;
+constexpr int kBucketWindow = 16384;          // tile ids per block histogram (64 KB)
+constexpr int kBucketBlocksMax = 1024;
+constexpr int kTileSortThreads = 256;
+constexpr int kTileSortCap = 4096;            // keys sorted in shared memory (32 KB)
+
+__device__ __forceinline__ void block_range(int64_t n, int64_t &b0, int64_t &b1) {
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    b0 = (int64_t)blockIdx.x * per;
+    b1 = b0 + per < n ? b0 + per : n;
+}
+
+// Counts per tile of the kept instances of this block's range: in the shared
+// window sh[0 .. hi - lo] when the range's tiles span at most kBucketWindow
+// ids, else straight into the global counts; match-any aggregates equal tiles
+// of a warp into one atomic.
+__global__ void __launch_bounds__(kBucketThreads)
+bucket_count_kernel(const uint32_t *__restrict__ keys, const uint64_t *d_n, uint64_t capacity,
+                    uint32_t *__restrict__ tile_count, uint2 *__restrict__ window) {
+    extern __shared__ uint32_t sh[];
+    __shared__ uint32_t s_lo, s_hi;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = sort_count(d_n, capacity);
+    int64_t b0, b1;
+    block_range(n, b0, b1);
+    if (threadIdx.x == 0) {
+        s_lo = 0xFFFFFFFFu;
+        s_hi = 0u;
+    }
+    __syncthreads();
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kBucketThreads) {
+        const uint32_t k = keys[i];
+        if (k != kDroppedKey) {
+            lo = min(lo, k);
+            hi = max(hi, k);
+        }
+    }
+    lo = __reduce_min_sync(FULL, lo);
+    hi = __reduce_max_sync(FULL, hi);
+    if (lane == 0 && lo <= hi) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+    }
+    __syncthreads();
+    lo = s_lo;
+    hi = s_hi;
+    if (threadIdx.x == 0) window[blockIdx.x] = make_uint2(lo, hi);
+    if (lo > hi) return;                                    // nothing kept here
+    const bool windowed = hi - lo < (uint32_t)kBucketWindow;
+    if (windowed) {
+        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) sh[w] = 0u;
+        __syncthreads();
+    }
+    for (int64_t i0 = b0; i0 < b1; i0 += kBucketThreads) {   // block-uniform trip count
+        const int64_t i = i0 + threadIdx.x;
+        const uint32_t k = i < b1 ? keys[i] : kDroppedKey;
+        const unsigned peers = __match_any_sync(FULL, k);
+        if (k != kDroppedKey && lane == __ffs(peers) - 1) {
+            if (windowed)
+                atomicAdd(&sh[k - lo], (uint32_t)__popc(peers));
+            else
+                atomicAdd(&tile_count[k], (uint32_t)__popc(peers));
+        }
+    }
+    if (windowed) {
+        __syncthreads();
+        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads)
+            if (sh[w] != 0u) atomicAdd(&tile_count[lo + w], sh[w]);
+    }
+}
+
+// Places the block's kept instances (their values) in their tiles' slots:
+// first reserves a run per tile after its start (cursor[t] counts what the
+// blocks took so far), then hands out the run's slots.
+__global__ void __launch_bounds__(kBucketThreads)
+bucket_scatter_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                      const uint64_t *d_n, uint64_t capacity,
+                      const uint32_t *__restrict__ tile_start, uint32_t *__restrict__ cursor,
+                      const uint2 *__restrict__ window, uint32_t *__restrict__ grouped) {
+    extern __shared__ uint32_t sh[];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = sort_count(d_n, capacity);
+    int64_t b0, b1;
+    block_range(n, b0, b1);
+    const uint2 win = window[blockIdx.x];
+    const uint32_t lo = win.x, hi = win.y;
+    if (lo > hi) return;
+    const bool windowed = hi - lo < (uint32_t)kBucketWindow;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    if (windowed) {
+        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) sh[w] = 0u;
+        __syncthreads();
+        for (int64_t i0 = b0; i0 < b1; i0 += kBucketThreads) {
+            const int64_t i = i0 + threadIdx.x;
+            const uint32_t k = i < b1 ? keys[i] : kDroppedKey;
+            const unsigned peers = __match_any_sync(FULL, k);
+            if (k != kDroppedKey && lane == __ffs(peers) - 1)
+                atomicAdd(&sh[k - lo], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) {
+            const uint32_t c = sh[w];
+            if (c != 0u) sh[w] = tile_start[lo + w] + atomicAdd(&cursor[lo + w], c);
+        }
+        __syncthreads();
+    }
+    for (int64_t i0 = b0; i0 < b1; i0 += kBucketThreads) {
+        const int64_t i = i0 + threadIdx.x;
+        const uint32_t k = i < b1 ? keys[i] : kDroppedKey;
+        const unsigned peers = __match_any_sync(FULL, k);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (k != kDroppedKey && lane == leader)
+            base = windowed ? atomicAdd(&sh[k - lo], (uint32_t)__popc(peers))
+                            : tile_start[k] + atomicAdd(&cursor[k], (uint32_t)__popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        if (k != kDroppedKey) grouped[base + __popc(peers & lanemask_lt)] = vals[i];
+    }
+}
+
+// Bitonic sort of sk[0 .. n) (n a power of two, <= kTileSortCap) by the whole
+// CTA, ascending.
+__device__ __forceinline__ void bitonic_sort_smem(uint64_t *sk, int n) {
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < (n >> 1); p += kTileSortThreads) {
+                const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                const int l = i + j;
+                const uint64_t a = sk[i], b = sk[l];
+                const bool up = (i & k) == 0;
+                if ((a > b) == up) {
+                    sk[i] = b;
+                    sk[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_ceil(int m) {
+    int n = 2;
+    while (n < m) n <<= 1;
+    return n;
+}
+
+// Merge of the sorted runs a[0 .. la) and b[0 .. lb) into out by the whole
+// CTA: each thread takes an equal share of the output and finds where it
+// starts on the merge path by a binary search (keys are distinct).
+__device__ void merge_runs(const uint64_t *a, int64_t la, const uint64_t *b, int64_t lb,
+                           uint64_t *out) {
+    const int64_t total = la + lb;
+    const int64_t d0 = total * threadIdx.x / kTileSortThreads;
+    const int64_t d1 = total * (threadIdx.x + 1) / kTileSortThreads;
+    int64_t lo = d0 > lb ? d0 - lb : 0, hi = d0 < la ? d0 : la;
+    while (lo < hi) {                      // elements of a among the first d0 outputs
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < b[d0 - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    int64_t ia = lo, ib = d0 - lo;
+    for (int64_t d = d0; d < d1; ++d) {
+        const bool take_a = ib >= lb || (ia < la && a[ia] < b[ib]);
+        out[d] = take_a ? a[ia++] : b[ib++];
+    }
+}
+
+// One CTA per tile: its list [start, start + count) of grouped records in
+// (depth_key, record) order into sorted, and the tile's range.
+__global__ void __launch_bounds__(kTileSortThreads)
+tile_depth_sort_kernel(const uint32_t *__restrict__ tile_start,
+                       const uint32_t *__restrict__ tile_count,
+                       const uint32_t *__restrict__ grouped, const uint32_t *__restrict__ depth_key,
+                       uint32_t *__restrict__ sorted, uint32_t *__restrict__ ranges,
+                       uint64_t *__restrict__ tmp_a, uint64_t *__restrict__ tmp_b) {
+    __shared__ uint64_t sk[kTileSortCap];
+    const int64_t t = blockIdx.x;
+    const uint32_t s = tile_start[t], L = tile_count[t];
+    if (threadIdx.x == 0) {
+        ranges[2 * t] = s;
+        ranges[2 * t + 1] = s + L;
+    }
+    if (L == 0u) return;
+    if (L == 1u) {
+        if (threadIdx.x == 0) sorted[s] = grouped[s];
+        return;
+    }
+    // chunks of at most kTileSortCap keys, each sorted in shared memory
+    uint64_t *A = tmp_a + s, *B = tmp_b + s;
+    for (uint32_t c0 = 0; c0 < L; c0 += kTileSortCap) {
+        const int m = (int)min(L - c0, (uint32_t)kTileSortCap);
+        const int n = pow2_ceil(m);
+        for (int i = threadIdx.x; i < n; i += kTileSortThreads) {
+            uint64_t key = ~0ull;
+            if (i < m) {
+                const uint32_t r = grouped[s + c0 + i];
+                key = ((uint64_t)depth_key[r] << 32) | r;
+            }
+            sk[i] = key;
+        }
+        __syncthreads();
+        bitonic_sort_smem(sk, n);
+        if (L <= (uint32_t)kTileSortCap) {
+            for (int i = threadIdx.x; i < m; i += kTileSortThreads) sorted[s + i] = (uint32_t)sk[i];
+            return;
+        }
+        for (int i = threadIdx.x; i < m; i += kTileSortThreads) A[c0 + i] = sk[i];
+        __syncthreads();
+    }
+    // long lists: merge the sorted chunks pairwise, in global scratch
+    for (int64_t w = kTileSortCap; w < (int64_t)L; w <<= 1) {
+        __syncthreads();
+        for (int64_t p0 = 0; p0 < (int64_t)L; p0 += 2 * w) {
+            const int64_t la = min(w, (int64_t)L - p0);
+            const int64_t lb = min(w, (int64_t)L - p0 - la);
+            merge_runs(A + p0, la, A + p0 + la, lb, B + p0);
+        }
+        __threadfence_block();
+        uint64_t *x = A;
+        A = B;
+        B = x;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < L; i += kTileSortThreads) sorted[s + i] = (uint32_t)A[i];
+}
+
 }  // namespace mg
 
 using namespace mg;
@@ -679,6 +927,113 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     const int64_t rblocks = (int64_t)((capacity + 1023) / 1024);
     ranges_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), 256, 0, s>>>(
         in_alt ? keys_alt : keys, &ws->n_kept, capacity, ranges, n_tiles_total);
+    return mg_host::launch_status();
+}
+
+// --------------------------------------------------------------------------
+// mg_sort_by_tile: the tile-bucket sort (see the kernels above).
+// --------------------------------------------------------------------------
+namespace {
+
+struct BucketLayout {
+    size_t count, cursor, start, window, scan, n_kept, tmp_a, tmp_b, total;
+    int64_t scan_parts;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+BucketLayout bucket_layout(uint64_t capacity, int64_t n_tiles) {
+    BucketLayout L;
+    size_t o = 0;
+    L.count = o;
+    o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
+    L.cursor = o;
+    o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
+    L.start = o;
+    o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
+    L.window = o;
+    o = align256(o + sizeof(uint2) * (size_t)kBucketBlocksMax);
+    L.scan_parts = (n_tiles + kScanPart - 1) / kScanPart;
+    L.scan = o;
+    o = align256(o + sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(L.scan_parts + 1));
+    L.n_kept = o;
+    o = align256(o + sizeof(uint64_t));
+    L.tmp_a = o;
+    o = align256(o + sizeof(uint64_t) * (size_t)capacity);
+    L.tmp_b = o;
+    o = align256(o + sizeof(uint64_t) * (size_t)capacity);
+    L.total = o;
+    return L;
+}
+
+// The bucket kernels' 64 KB of dynamic shared memory, opted in once per device.
+mg_status bucket_smem_optin() {
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        const int bytes = (int)(sizeof(uint32_t) * kBucketWindow);
+        if (cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(bucket_scatter_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+            return MG_ERR_CUDA;
+        done[dev] = true;
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" size_t mg_sort_by_tile_workspace_bytes(uint64_t capacity, int64_t n_tiles_total) {
+    return bucket_layout(capacity, n_tiles_total > 0 ? n_tiles_total : 0).total;
+}
+
+extern "C" mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals,
+                                     const uint32_t *depth_key, const uint64_t *d_num_instances,
+                                     uint64_t capacity, int64_t n_tiles_total, uint32_t *grouped,
+                                     uint32_t *sorted_vals, uint32_t *ranges, void *workspace,
+                                     size_t workspace_bytes, uint64_t *d_num_sorted,
+                                     mg_status_word *d_status, mg_stream_t stream) {
+    if (!keys || !vals || !depth_key || !d_num_instances || !grouped || !sorted_vals || !ranges ||
+        !workspace || n_tiles_total <= 0 || n_tiles_total >= (int64_t(1) << 31) ||
+        n_tiles_total >= (int64_t)kDroppedKey)
+        return MG_ERR_INVALID_ARG;
+    if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return MG_ERR_INVALID_ARG;
+    const BucketLayout L = bucket_layout(capacity, n_tiles_total);
+    if (workspace_bytes < L.total) return MG_ERR_INVALID_ARG;
+    if (bucket_smem_optin() != MG_OK) return MG_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = reinterpret_cast<char *>(workspace);
+    uint32_t *count = reinterpret_cast<uint32_t *>(ws + L.count);
+    uint32_t *cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
+    uint32_t *start = reinterpret_cast<uint32_t *>(ws + L.start);
+    uint2 *window = reinterpret_cast<uint2 *>(ws + L.window);
+    ScanWS *scan_ws = reinterpret_cast<ScanWS *>(ws + L.scan);
+    uint64_t *n_kept = reinterpret_cast<uint64_t *>(ws + L.n_kept);
+    // the tile counts and cursors, and the scan's look-back words, start at 0
+    if (cudaMemsetAsync(ws + L.count, 0, L.start - L.count, s) != cudaSuccess ||
+        cudaMemsetAsync(ws + L.scan, 0, L.n_kept - L.scan, s) != cudaSuccess)
+        return MG_ERR_CUDA;
+    const int64_t by_size = (int64_t)((capacity + 2047) / 2048);
+    int64_t blocks = 2 * (int64_t)sm_count();
+    if (blocks > by_size) blocks = by_size;
+    if (blocks > kBucketBlocksMax) blocks = kBucketBlocksMax;
+    if (blocks < 1) blocks = 1;
+    const size_t smem = sizeof(uint32_t) * kBucketWindow;
+    bucket_count_kernel<<<(unsigned)blocks, kBucketThreads, smem, s>>>(keys, d_num_instances,
+                                                                        capacity, count, window);
+    scan_kernel<<<(unsigned)L.scan_parts, kScanThreads, 0, s>>>(
+        count, nullptr, n_tiles_total, start, d_num_sorted != nullptr ? d_num_sorted : n_kept,
+        ~0ull, scan_ws, L.scan_parts, d_status, nullptr);
+    bucket_scatter_kernel<<<(unsigned)blocks, kBucketThreads, smem, s>>>(
+        keys, vals, d_num_instances, capacity, start, cursor, window, grouped);
+    tile_depth_sort_kernel<<<(unsigned)n_tiles_total, kTileSortThreads, 0, s>>>(
+        start, count, grouped, depth_key, sorted_vals, ranges,
+        reinterpret_cast<uint64_t *>(ws + L.tmp_a), reinterpret_cast<uint64_t *>(ws + L.tmp_b));
     return mg_host::launch_status();
 }
 

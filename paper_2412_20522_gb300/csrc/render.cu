@@ -25,7 +25,7 @@ namespace mg {
 constexpr int kPix = 2;                          // pixels per thread (one column pair)
 constexpr int kRenderThreads = 256 / kPix;       // threads per CTA (one 256-pixel tile)
 constexpr int kRenderWarps = kRenderThreads / 32;
-constexpr int kBatch = 256;                      // splats staged per batch
+constexpr int kBatch = 256;                      // splats staged per batch (default)
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -177,7 +177,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // L1 = true also takes the L1 render loss in the epilogue, from the colours
 // in registers: dL/dimage = sign(C - target) / (3 W H) and one atomic per CTA
 // adding the CTA's sum of |C - target| / (3 W H) to *loss.
-template <bool COUNT, bool AUX = true, bool L1 = false>
+template <bool COUNT, bool AUX = true, bool L1 = false, int BATCH = kBatch>
 __global__ void __launch_bounds__(kRenderThreads)
 render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ tile_order,
@@ -186,8 +186,8 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count,
                       const float *__restrict__ target = nullptr,
                       float *__restrict__ dL_dimage = nullptr, float *loss = nullptr) {
-    __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
-    __shared__ uint8_t sM[kBatch];
+    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ uint8_t sM[BATCH];
     __shared__ unsigned long long s_frags[4];
     const int64_t t = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const TileInfo ti = tile_info(vt, t);
@@ -208,10 +208,10 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
     }
     if (threadIdx.x < 4) s_frags[threadIdx.x] = 0ull;
 
-    for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
+    for (uint32_t b0 = start; b0 < end; b0 += BATCH) {
         if (__syncthreads_count(all_done(done)) == kRenderThreads) break;
 #pragma unroll
-        for (int h = 0; h < kBatch / kRenderThreads; ++h) {
+        for (int h = 0; h < (BATCH + kRenderThreads - 1) / kRenderThreads; ++h) {
             const int i = threadIdx.x + h * kRenderThreads;
             if (b0 + i < end) {
                 const uint32_t r = vals[b0 + i];
@@ -226,7 +226,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
             }
         }
         __syncthreads();
-        const int cnt = (int)min(end - b0, (uint32_t)kBatch);
+        const int cnt = (int)min(end - b0, (uint32_t)BATCH);
         if (COUNT) {
             // diagnostic counts over every position (culled or not) up to the stop
 #pragma unroll
@@ -419,8 +419,8 @@ constexpr int kAcc = 10;
 // Eight CTAs per SM (32 warps): the register cap this asks for (64) holds
 // without spills, and eight copies of the 27.3 KB of shared memory fit (a
 // ninth does not).
-constexpr int kBatchB = 128;                    // splats staged per backward batch
-template <bool COUNT>
+constexpr int kBatchB = 128;                    // splats staged per backward batch (default)
+template <bool COUNT, int BATCHB = kBatchB>
 __global__ void __launch_bounds__(kRenderThreads, 1024 / kRenderThreads)
 render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
@@ -429,10 +429,10 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        const uint32_t *__restrict__ n_contrib, const float *__restrict__ dL_dimage,
                        float *__restrict__ grad2d, unsigned long long *counters) {
     unsigned long long cnt_it = 0, cnt_m = 0, cnt_cu = 0, cnt_cm = 0, cnt_pix = 0, cnt_b = 0;
-    __shared__ float4 sA[kBatchB], sB[kBatchB], sC[kBatchB];
-    __shared__ uint32_t sR[kBatchB];
-    __shared__ uint8_t sM[kBatchB];
-    __shared__ float sG[kRenderWarps][kBatchB][kAcc];   // per-warp sums: plain stores
+    __shared__ float4 sA[BATCHB], sB[BATCHB], sC[BATCHB];
+    __shared__ uint32_t sR[BATCHB];
+    __shared__ uint8_t sM[BATCHB];
+    __shared__ float sG[kRenderWarps][BATCHB][kAcc];   // per-warp sums: plain stores
     __shared__ uint32_t s_maxstop;
     __shared__ uint32_t s_wstop[kRenderWarps];
     const int64_t t = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
@@ -476,7 +476,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     __syncthreads();
     const uint32_t maxstop = min(s_maxstop, end - start);
     if (maxstop == 0) return;
-    const int nb = (int)((maxstop + kBatchB - 1) / kBatchB);
+    const int nb = (int)((maxstop + BATCHB - 1) / BATCHB);
     if (COUNT) cnt_b = nb;
     uint32_t wstop = tstop;                                    // warp's largest stop
 #pragma unroll
@@ -484,11 +484,11 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
     if (lane == 0) s_wstop[warp] = wstop;
 
     for (int bi = nb - 1; bi >= 0; --bi) {
-        const uint32_t pos0 = (uint32_t)bi * kBatchB;
-        const int cnt = (int)min(maxstop - pos0, (uint32_t)kBatchB);
+        const uint32_t pos0 = (uint32_t)bi * BATCHB;
+        const int cnt = (int)min(maxstop - pos0, (uint32_t)BATCHB);
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < kBatchB / kRenderThreads; ++h) {
+        for (int h = 0; h < (BATCHB + kRenderThreads - 1) / kRenderThreads; ++h) {
             const int i = threadIdx.x + h * kRenderThreads;
             if (i < cnt) {
                 const uint32_t r = vals[start + pos0 + i];
@@ -591,7 +591,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
         }
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < kBatchB / kRenderThreads; ++h) {
+        for (int h = 0; h < (BATCHB + kRenderThreads - 1) / kRenderThreads; ++h) {
             const int i = threadIdx.x + h * kRenderThreads;
             if (i >= cnt) continue;
             float4 *G4 = reinterpret_cast<float4 *>(grad2d) + 3 * (int64_t)sR[i];
@@ -698,6 +698,18 @@ __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ imag
 
 using namespace mg;
 
+// Staging depths the kernels are built for (mg_raster_cfg.render_batch and
+// render_batch_bwd; 0 = the default).
+static bool fwd_batch(const mg_raster_cfg *cfg, int *b) {
+    *b = cfg->render_batch == 0 ? kBatch : cfg->render_batch;
+    return *b == 128 || *b == 256;
+}
+
+static bool bwd_batch(const mg_raster_cfg *cfg, int *b) {
+    *b = cfg->render_batch_bwd == 0 ? kBatchB : cfg->render_batch_bwd;
+    return *b == 64 || *b == 128;
+}
+
 extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
                                   const uint32_t *ranges, const uint32_t *tile_order,
                                   const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
@@ -713,11 +725,19 @@ extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorte
     if (st != MG_OK) return st;
     const int64_t tiles = vt.tile_off[n_views];
     if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
+    int batch;
+    if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
-    render_forward_kernel<false, true, true>
-        <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
-            final_T, n_contrib, nullptr, target, dL_dimage, loss);
+    if (batch == 128)
+        render_forward_kernel<false, true, true, 128>
+            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+                vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
+                image, final_T, n_contrib, nullptr, target, dL_dimage, loss);
+    else
+        render_forward_kernel<false, true, true>
+            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+                vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
+                image, final_T, n_contrib, nullptr, target, dL_dimage, loss);
     return mg_host::launch_status();
 }
 
@@ -734,11 +754,18 @@ extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_v
     if (st != MG_OK) return st;
     const int64_t tiles = vt.tile_off[n_views];
     if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
+    int batch;
+    if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
-    if (frag_count != nullptr)
+    if (frag_count != nullptr)      // the counting variant: default staging depth
         render_forward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
             final_T, n_contrib, reinterpret_cast<unsigned long long *>(frag_count));
+    else if (batch == 128)
+        render_forward_kernel<false, true, false, 128>
+            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+                vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
+                image, final_T, n_contrib, nullptr);
     else
         render_forward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
@@ -759,9 +786,18 @@ extern "C" mg_status mg_render_inference(const mg_splats *splats, const uint32_t
     if (st != MG_OK) return st;
     const int64_t tiles = vt.tile_off[n_views];
     if (tiles >= (int64_t(1) << 31)) return MG_ERR_INVALID_ARG;
-    render_forward_kernel<false, false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-        vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, tile_order,
-        cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
+    int batch;
+    if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
+    if (batch == 128)
+        render_forward_kernel<false, false, false, 128>
+            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+                vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges,
+                tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
+    else
+        render_forward_kernel<false, false>
+            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
+                vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges,
+                tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
     return mg_host::launch_status();
 }
 
@@ -783,6 +819,8 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
     if (st != MG_OK) return st;
     const int64_t tiles = vt.tile_off[n_views];
     const int64_t R = vt.rec_off[n_views];
+    int batch;
+    if (!bwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (R > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * MG_GRAD2D_FLOATS * (size_t)R, s) !=
                      cudaSuccess)
@@ -792,6 +830,10 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
         render_backward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
             n_contrib, dL_dimage, grad2d, reinterpret_cast<unsigned long long *>(counters));
+    else if (batch == 64)
+        render_backward_kernel<false, 64><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
+            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
+            n_contrib, dL_dimage, grad2d, nullptr);
     else
         render_backward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,

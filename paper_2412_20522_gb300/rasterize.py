@@ -33,6 +33,14 @@ class RasterConfig:
     mask_loss: int = abi.MG_MASK_LOSS_L2       # Eq. 7, or the L1 form
     ste_logit: float = 0.0                     # MG_MASK_STE threshold on l_0 - l_1
     bin_mode: int = abi.MG_BIN_FILTERED        # or MG_BIN_RECT (whole 3-sigma rectangles)
+    # tile lists: "bucket" = one counting pass over the whole tile id and a
+    # per-tile depth sort (mg_sort_by_tile); "radix8" = depth order of the
+    # records, then a stable sort by tile id in 8-bit digits (mg_sort)
+    sort: str = "radix8"
+    # splats staged per batch by the render kernels (0 = the defaults: 256
+    # forward, 128 backward; also 128 forward, 64 backward)
+    render_batch: int = 0
+    render_batch_bwd: int = 0
 
     @staticmethod
     def ste_logit_of(theta: float) -> float:
@@ -56,6 +64,8 @@ class RasterConfig:
         cfg.mask_loss = int(self.mask_loss)
         cfg.ste_logit = float(self.ste_logit)
         cfg.bin_mode = int(self.bin_mode)
+        cfg.render_batch = int(self.render_batch)
+        cfg.render_batch_bwd = int(self.render_batch_bwd)
         return cfg
 
 
@@ -137,6 +147,7 @@ class Rasterizer:
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.num_sorted = torch.zeros(1, dtype=torch.int64, device=self.device)
         self._l1_fused = False
+        self._sort_mode = "radix8"
 
     # -- buffers -------------------------------------------------------------
     def _get(self, name, numel, dtype):
@@ -162,12 +173,14 @@ class Rasterizer:
         s.depth_key = self._get("depth_key", R, torch.int32).data_ptr()
         return s
 
-    def _ensure_sort_buffers(self, cap, key_bits):
+    def _ensure_sort_buffers(self, cap, key_bits, tiles, bucket):
         self._get("keys", cap, torch.int32)
         self._get("vals", cap, torch.int32)
         self._get("keys_alt", cap, torch.int32)
         self._get("vals_alt", cap, torch.int32)
-        self._get("sort_ws", abi.mg_sort_workspace_bytes(cap, key_bits), torch.uint8)
+        ws = (abi.mg_sort_by_tile_workspace_bytes(cap, tiles) if bucket
+              else abi.mg_sort_workspace_bytes(cap, key_bits))
+        self._get("sort_ws", ws, torch.uint8)
 
     # -- forward --------------------------------------------------------------
     def forward(self, params: dict, cams, cfg: RasterConfig, view_ranges=None, check=True,
@@ -198,13 +211,22 @@ class Rasterizer:
         ev.begin("preprocess")
         abi.mg_preprocess(g, views, V, ccfg, splats, self.status, stream)
         ev.end("preprocess")
-        # depth order of the records, then instances in that order
-        order = self._get("order", R, torch.int32)
-        dws = self._get("depth_ws", abi.mg_depth_order_workspace_bytes(R), torch.uint8)
+        bucket = cfg.sort == "bucket"
         ev.begin("bin")
-        abi.mg_depth_order(splats, views, V, ccfg, order, self._get("order_alt", R, torch.int32),
-                           self._get("dkeys", R, torch.int32), self._get("dkeys_alt", R, torch.int32),
-                           dws, dws.numel(), self.status, stream)
+        if bucket:
+            # instances in record order; each tile's list is put in depth
+            # order by the sort itself
+            order = None
+            self._buf.pop("order", None)
+        else:
+            # depth order of the records, then instances in that order
+            order = self._get("order", R, torch.int32)
+            dws = self._get("depth_ws", abi.mg_depth_order_workspace_bytes(R), torch.uint8)
+            abi.mg_depth_order(splats, views, V, ccfg, order,
+                               self._get("order_alt", R, torch.int32),
+                               self._get("dkeys", R, torch.int32),
+                               self._get("dkeys_alt", R, torch.int32),
+                               dws, dws.numel(), self.status, stream)
         offsets = self._get("offsets", R, torch.int32)
         bin_ws = self._get("bin_ws", abi.mg_bin_workspace_bytes(R), torch.uint8)
         if self.capacity <= 0:
@@ -214,7 +236,7 @@ class Rasterizer:
             k = int(self.num_instances.item())
             self.capacity = max(int(k * self.headroom), 1024)
             self.status.zero_()
-        self._ensure_sort_buffers(self.capacity, key_bits)
+        self._ensure_sort_buffers(self.capacity, key_bits, tiles, bucket)
         abi.mg_bin(splats, views, V, ccfg, order, offsets, self._buf["keys"], self._buf["vals"],
                    self.capacity, self.num_instances, bin_ws, bin_ws.numel(), self.status, stream)
         ev.end("bin")
@@ -222,7 +244,7 @@ class Rasterizer:
             st = abi.mg_read_status(self.status, stream)
             if st.status == abi.MG_ERR_CAPACITY:
                 self.capacity = int(st.required * self.headroom) + 1024
-                self._ensure_sort_buffers(self.capacity, key_bits)
+                self._ensure_sort_buffers(self.capacity, key_bits, tiles, bucket)
                 self.status.zero_()
                 abi.mg_bin(splats, views, V, ccfg, order, offsets, self._buf["keys"],
                            self._buf["vals"], self.capacity, self.num_instances, bin_ws,
@@ -232,24 +254,41 @@ class Rasterizer:
         ranges_buf = self._get("ranges", 2 * tiles, torch.int32)
         sort_ws = self._buf["sort_ws"]
         ev.begin("sort")
-        # instances arrive in depth order: a stable sort by tile id suffices
-        alt = abi.mg_sort(self._buf["keys"], self._buf["vals"], self._buf["keys_alt"],
-                          self._buf["vals_alt"], self.num_instances, self.capacity, key_bits,
-                          ranges_buf, tiles, sort_ws, sort_ws.numel(), self.num_sorted,
-                          self.status, stream)
+        if bucket:
+            # one counting pass over the whole tile id, then each tile's list
+            # in depth order
+            abi.mg_sort_by_tile(self._buf["keys"], self._buf["vals"], splats.depth_key,
+                                self.num_instances, self.capacity, tiles, self._buf["keys_alt"],
+                                self._buf["vals_alt"], ranges_buf, sort_ws, sort_ws.numel(),
+                                self.num_sorted, self.status, stream)
+            sorted_vals = self._buf["vals_alt"]
+        else:
+            # instances arrive in depth order: a stable sort by tile id suffices
+            alt = abi.mg_sort(self._buf["keys"], self._buf["vals"], self._buf["keys_alt"],
+                              self._buf["vals_alt"], self.num_instances, self.capacity, key_bits,
+                              ranges_buf, tiles, sort_ws, sort_ws.numel(), self.num_sorted,
+                              self.status, stream)
+            sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
         ev.end("sort")
-        sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
         # longest tile lists first (launch order only)
         tile_order = self._get("tile_order", tiles, torch.int32) if self.tile_order else None
         if tile_order is not None:
             abi.mg_tile_order(ranges_buf, tiles, tile_order, stream)
         image = self._get("image", 3 * pix, torch.float32)
+        # kernels of ours per forward: preprocess (with the depth keys); with
+        # the radix sort: histogram, offsets and 4 digit passes of the depth
+        # order, scan, duplicate, histogram, offsets, one pass per tile digit,
+        # ranges; with the bucket sort: scan, duplicate, count, scan, scatter,
+        # order; then the tile order and the render
+        sort_launches = 4 if bucket else 6 + 2 + 3 + (key_bits + 7) // 8
+        self._fwd_launches = 1 + sort_launches + (2 if bucket else 0) + 1 + \
+            (tile_order is not None)
+        self._sort_mode = cfg.sort
         if inference:
             ev.begin("render")
             abi.mg_render_inference(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg,
                                     image, stream)
             ev.end("render")
-            self._fwd_launches = 1 + 6 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
             self._state = None
             if check:
                 st = abi.mg_read_status(self.status, stream)
@@ -274,10 +313,6 @@ class Rasterizer:
                           final_T, n_contrib, self.frag_count if count_fragments else None, stream)
         ev.end("render")
         self._l1_fused = fused
-        # kernels of ours per forward: preprocess (with the depth keys);
-        # histogram, offsets, 4 digit passes; scan, duplicate; histogram,
-        # offsets, one per tile digit pass, ranges; tile order; render
-        self._fwd_launches = 1 + 6 + 2 + 3 + (key_bits + 7) // 8 + 1 + (tile_order is not None)
         self._state = dict(g=g, views=views, V=V, cfg=ccfg, splats=splats, R=R, n=n, pix=pix,
                            sorted_vals=sorted_vals, ranges=ranges_buf, tiles=tiles,
                            tile_order=tile_order,
@@ -401,7 +436,8 @@ class Rasterizer:
     def splat_outputs(self):
         s = self._state
         R, n = s["R"], s["n"]
-        return dict(record=self._buf["record"][:R * 12].view(R, 12), order=self._buf["order"][:R],
+        order = self._buf["order"][:R] if "order" in self._buf else None
+        return dict(record=self._buf["record"][:R * 12].view(R, 12), order=order,
                     tiles=self._buf["tiles"][:R], radius=self._buf["radius"][:R],
                     clamp=self._buf["clamp"][:R], mask=self._buf["mask"][:n],
                     mask_soft=self._buf["mask_soft"][:n], offsets=self._buf["offsets"][:R],
@@ -413,7 +449,14 @@ class Rasterizer:
                     grad2d=self._buf.get("grad2d"))
 
     def sorted_keys(self):
+        """Tile id of every sorted instance (the bucket sort keeps the ids
+        implicit in the ranges: rebuilt from them here)."""
         s = self._state
+        if self._sort_mode == "bucket":
+            r = s["ranges"][:2 * s["tiles"]].view(-1, 2).long()
+            counts = r[:, 1] - r[:, 0]
+            return torch.repeat_interleave(torch.arange(s["tiles"], device=self.device),
+                                           counts).to(torch.int32)
         return self._buf["keys_alt"] if s["sorted_vals"] is self._buf["vals_alt"] else self._buf["keys"]
 
 

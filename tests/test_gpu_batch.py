@@ -115,15 +115,26 @@ def test_uneven_scene_batch_matches_oracle_per_scene(lambda_m):
 
 
 def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    """The autotuner chooses the tile shape, the sort digit width and both
+    staging depths, records all of them (with every timing it took) in the
+    cache, and returns the cached choice on the next call."""
+    import json
     from paper_2412_20522_gb300 import autotune
     monkeypatch.setenv("MASKGS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     g, cams, tgt = scenes.tiny_workload(8000)
     p = to_device(g)
     t = torch.as_tensor(tgt).cuda().reshape(-1)
-    best = autotune.autotune_tile(p, cams, t, steps=2)
-    assert best in autotune.TILE_SHAPES
-    assert (tmp_path / "tune.json").exists()
-    assert autotune.autotune_tile(p, cams, t, steps=2) == best      # from the cache
+    best = autotune.autotune(p, cams, t, steps=2)
+    assert (best.tile_w, best.tile_h) in autotune.TILE_SHAPES
+    assert best.sort in autotune.SORTS
+    assert best.render_batch in autotune.FWD_BATCHES
+    assert best.render_batch_bwd in autotune.BWD_BATCHES
+    entry = next(iter(json.load(open(tmp_path / "tune.json")).values()))
+    assert all(k in entry for k in autotune.TUNED)
+    assert len(entry["ms"]) >= len(autotune.TILE_SHAPES) + 3
+    again = autotune.autotune(p, cams, t, steps=2)                    # from the cache
+    assert all(getattr(again, k) == getattr(best, k) for k in autotune.TUNED)
+    assert autotune.autotune_tile(p, cams, t) == (best.tile_w, best.tile_h)
 
 
 def test_l1_loss_grad_views_at_every_alignment():

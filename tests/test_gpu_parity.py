@@ -55,11 +55,16 @@ def _oracle(g, cams, cfg_kw=None, tile=(16, 16)):
 def _check_discrete(rast, views, M, cams):
     so = rast.splat_outputs()
     assert np.array_equal(so["mask"].cpu().numpy(), M), "sampled masks differ"
-    # depth order of all records (all views), and the scan in that order
+    # depth order of all records (all views), and the scan in that order; the
+    # bucket sort needs no depth order: its scan runs in record order
     tiles_all = np.concatenate([v.fp32["tiles"] for v in views]).astype(np.int64)
-    order = binning.depth_order(np.concatenate([v.fp32["depth_bits"] for v in views]),
-                                np.concatenate([v.fp32["tiles"] > 0 for v in views]))
-    assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order), "depth order differs"
+    if so["order"] is None:
+        order = np.arange(tiles_all.size)
+    else:
+        order = binning.depth_order(np.concatenate([v.fp32["depth_bits"] for v in views]),
+                                    np.concatenate([v.fp32["tiles"] > 0 for v in views]))
+        assert np.array_equal(so["order"].cpu().numpy().view(np.uint32), order), \
+            "depth order differs"
     exp_off = np.concatenate([[0], np.cumsum(tiles_all[order])[:-1]]) if order.size else order
     assert np.array_equal(so["offsets"].cpu().numpy().view(np.uint32).astype(np.int64), exp_off), \
         "scan offsets differ"
