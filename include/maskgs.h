@@ -340,8 +340,7 @@ size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);
  * Pairs keyed 0xFFFFFFFF are dropped.  Outputs: sorted_vals (u32[capacity]):
  * the records of tile t at [ranges[2t], ranges[2t+1]); *d_num_sorted
  * (nullable) = the number kept.  The lists equal mg_sort's on depth-ordered
- * instances bit for bit.  grouped: u32[capacity] scratch (the tile-grouped,
- * not yet ordered records).  workspace: mg_sort_by_tile_workspace_bytes(
+ * instances bit for bit.  workspace: mg_sort_by_tile_workspace_bytes(
  * capacity, n_tiles_total) bytes, 16-byte aligned, any content.  When
  * *d_num_instances exceeds capacity nothing is sorted and every range is
  * empty.  Lists of up to 4096 records are ordered in shared memory, longer
@@ -350,9 +349,9 @@ size_t mg_sort_workspace_bytes(uint64_t capacity, int32_t key_bits);
  * capture. */
 mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals, const uint32_t *depth_key,
                           const uint64_t *d_num_instances, uint64_t capacity,
-                          int64_t n_tiles_total, uint32_t *grouped, uint32_t *sorted_vals,
-                          uint32_t *ranges, void *workspace, size_t workspace_bytes,
-                          uint64_t *d_num_sorted, mg_status_word *d_status, mg_stream_t stream);
+                          int64_t n_tiles_total, uint32_t *sorted_vals, uint32_t *ranges,
+                          void *workspace, size_t workspace_bytes, uint64_t *d_num_sorted,
+                          mg_status_word *d_status, mg_stream_t stream);
 size_t mg_sort_by_tile_workspace_bytes(uint64_t capacity, int64_t n_tiles_total);
 /* Bits of a global tile id for a set of views: ceil(log2(n_tiles_total)), >= 1. */
 int32_t mg_tile_bits(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg);

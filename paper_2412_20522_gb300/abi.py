@@ -119,7 +119,7 @@ def load(build_if_missing: bool = True):
         "mg_sort": (st, [vp, vp, vp, vp, vp, C.c_uint64, C.c_int32, vp, C.c_int64, vp,
                          C.c_size_t, _P(C.c_int32), vp, vp, vp]),
         "mg_sort_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int32]),
-        "mg_sort_by_tile": (st, [vp, vp, vp, vp, C.c_uint64, C.c_int64, vp, vp, vp, vp,
+        "mg_sort_by_tile": (st, [vp, vp, vp, vp, C.c_uint64, C.c_int64, vp, vp, vp,
                                  C.c_size_t, vp, vp, vp]),
         "mg_sort_by_tile_workspace_bytes": (C.c_size_t, [C.c_uint64, C.c_int64]),
         "mg_tile_bits": (C.c_int32, [_P(mg_view), C.c_int32, _P(mg_raster_cfg)]),
@@ -230,12 +230,12 @@ def mg_sort_workspace_bytes(capacity, key_bits) -> int:
     return int(load().mg_sort_workspace_bytes(capacity, key_bits))
 
 
-def mg_sort_by_tile(keys, vals, depth_key, d_num_instances, capacity, n_tiles_total, grouped,
+def mg_sort_by_tile(keys, vals, depth_key, d_num_instances, capacity, n_tiles_total,
                     sorted_vals, ranges, workspace, workspace_bytes, d_num_sorted, d_status,
                     stream):
     _check("mg_sort_by_tile", load().mg_sort_by_tile(
         ptr(keys), ptr(vals), ptr(depth_key), ptr(d_num_instances), capacity, n_tiles_total,
-        ptr(grouped), ptr(sorted_vals), ptr(ranges), ptr(workspace), workspace_bytes,
+        ptr(sorted_vals), ptr(ranges), ptr(workspace), workspace_bytes,
         ptr(d_num_sorted), ptr(d_status), stream))
 
 

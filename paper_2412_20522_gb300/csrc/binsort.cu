@@ -555,27 +555,37 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
 // --------------------------------------------------------------------------
 // Tile-bucket sort: the instances grouped by tile in one counting pass over
 // the whole tile id (a digit as wide as the key), then every tile's list
-// ordered by (depth key, record index) in shared memory.  The depth order of
-// the records is not needed beforehand, so the instances may come in record
-// order; the lists equal those of the depth sort + stable tile sort.
+// ordered by (depth key, record index).  The depth order of the records is
+// not needed beforehand, so the instances may come in record order; the lists
+// equal those of the depth sort + stable tile sort.
 //
-//   count    each block counts the kept instances of a contiguous range per
-//            tile in a shared-memory histogram over the range's tile window,
-//            then adds its non-zero bins to the global tile counts
+//   count    block b counts the kept instances of a contiguous range per tile
+//            (shared-memory histogram over the range's tile window) into row
+//            b of a B x T matrix H
+//   columns  per tile, H's column becomes its exclusive prefix over the
+//            blocks (block b's base inside the tile) and the tile's count
 //   scan     exclusive scan of the tile counts (the tile starts)
-//   scatter  the same ranges again: each block reserves, per tile, a run of
-//            slots after the starts (one global atomic per tile and block),
-//            and places its instances in them (shared-memory atomics, so the
-//            order inside a tile is arbitrary here)
-//   order    one CTA per tile: (depth_key << 32 | record) keys sorted
-//            bitonically in shared memory; lists longer than kTileSortCap are
-//            sorted in kTileSortCap chunks and merged in global scratch
+//   scatter  block b places its instances at start[t] + H[b][t] onwards,
+//            shared-memory atomics handing out the slots (so the order
+//            inside a tile is arbitrary here), as 64-bit (depth_key << 32 |
+//            record) keys
+//   order    each tile's keys sorted by a bitonic network held in registers
+//            (8 keys per thread; warp shuffles for distances up to 128,
+//            shared memory only across warps): lists of up to 1024 keys by
+//            128-thread CTAs, longer ones by 512-thread CTAs, in 4096-key
+//            chunks merged in global scratch past 4096
+// No global atomics on contended addresses: the per-tile bases come from
+// the column prefixes.  Every loop over instances issues kBucketIlp
+// independent loads per thread before using any of them.
 // --------------------------------------------------------------------------
 constexpr int kBucketThreads = 256;
-constexpr int kBucketWindow = 16384;          // tile ids per block histogram (64 KB)
+constexpr int kBucketIlp = 8;
+constexpr int kBucketTile = kBucketThreads * kBucketIlp;
+constexpr int kBucketWindow = 8192;           // tile ids per block histogram (32 KB)
 constexpr int kBucketBlocksMax = 1024;
-constexpr int kTileSortThreads = 256;
-constexpr int kTileSortCap = 4096;            // keys sorted in shared memory (32 KB)
+constexpr int kSortE = 8;                     // keys per thread in the register sort
+constexpr int kSortSmallThreads = 128;        // lists of up to 1024 keys
+constexpr int kSortLargeThreads = 512;        // lists of up to 4096 keys per chunk
 
 __device__ __forceinline__ void block_range(int64_t n, int64_t &b0, int64_t &b1) {
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
@@ -583,151 +593,265 @@ __device__ __forceinline__ void block_range(int64_t n, int64_t &b0, int64_t &b1)
     b1 = b0 + per < n ? b0 + per : n;
 }
 
-// Counts per tile of the kept instances of this block's range: in the shared
-// window sh[0 .. hi - lo] when the range's tiles span at most kBucketWindow
-// ids, else straight into the global counts; match-any aggregates equal tiles
-// of a warp into one atomic.
+// kBucketIlp keys of the block's range starting at i0 (kDroppedKey past b1,
+// and for tile ids outside [0, n_tiles)).
+__device__ __forceinline__ void load_keys(const uint32_t *__restrict__ keys, int64_t i0, int64_t b1,
+                                          int64_t n_tiles, uint32_t k[kBucketIlp]) {
+#pragma unroll
+    for (int u = 0; u < kBucketIlp; ++u) {
+        const int64_t i = i0 + u * kBucketThreads + threadIdx.x;
+        const uint32_t x = i < b1 ? __ldg(keys + i) : kDroppedKey;
+        k[u] = (int64_t)x < n_tiles ? x : kDroppedKey;
+    }
+}
+
+// The tile window [lo, hi] of the block's range (lo > hi: nothing kept).
+__device__ __forceinline__ uint2 range_window(const uint32_t *__restrict__ keys, int64_t b0,
+                                              int64_t b1, int64_t n_tiles, uint32_t *s_lo,
+                                              uint32_t *s_hi) {
+    const unsigned FULL = 0xffffffffu;
+    if (threadIdx.x == 0) {
+        *s_lo = 0xFFFFFFFFu;
+        *s_hi = 0u;
+    }
+    __syncthreads();
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (int64_t i0 = b0; i0 < b1; i0 += kBucketTile) {
+        uint32_t k[kBucketIlp];
+        load_keys(keys, i0, b1, n_tiles, k);
+#pragma unroll
+        for (int u = 0; u < kBucketIlp; ++u)
+            if (k[u] != kDroppedKey) {
+                lo = min(lo, k[u]);
+                hi = max(hi, k[u]);
+            }
+    }
+    lo = __reduce_min_sync(FULL, lo);
+    hi = __reduce_max_sync(FULL, hi);
+    if ((threadIdx.x & 31) == 0 && lo <= hi) {
+        atomicMin(s_lo, lo);
+        atomicMax(s_hi, hi);
+    }
+    __syncthreads();
+    return make_uint2(*s_lo, *s_hi);
+}
+
+// Row b of H (zeroed beforehand): the block's kept instances per tile.
 __global__ void __launch_bounds__(kBucketThreads)
 bucket_count_kernel(const uint32_t *__restrict__ keys, const uint64_t *d_n, uint64_t capacity,
-                    uint32_t *__restrict__ tile_count, uint2 *__restrict__ window) {
-    extern __shared__ uint32_t sh[];
+                    int64_t n_tiles, uint32_t *__restrict__ H, uint2 *__restrict__ window) {
+    __shared__ uint32_t sh[kBucketWindow];
     __shared__ uint32_t s_lo, s_hi;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t n = sort_count(d_n, capacity);
     int64_t b0, b1;
     block_range(n, b0, b1);
-    if (threadIdx.x == 0) {
-        s_lo = 0xFFFFFFFFu;
-        s_hi = 0u;
-    }
-    __syncthreads();
-    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += kBucketThreads) {
-        const uint32_t k = keys[i];
-        if (k != kDroppedKey) {
-            lo = min(lo, k);
-            hi = max(hi, k);
-        }
-    }
-    lo = __reduce_min_sync(FULL, lo);
-    hi = __reduce_max_sync(FULL, hi);
-    if (lane == 0 && lo <= hi) {
-        atomicMin(&s_lo, lo);
-        atomicMax(&s_hi, hi);
-    }
-    __syncthreads();
-    lo = s_lo;
-    hi = s_hi;
-    if (threadIdx.x == 0) window[blockIdx.x] = make_uint2(lo, hi);
+    const uint2 win = range_window(keys, b0, b1, n_tiles, &s_lo, &s_hi);
+    const uint32_t lo = win.x, hi = win.y;
+    if (threadIdx.x == 0) window[blockIdx.x] = win;
     if (lo > hi) return;                                    // nothing kept here
+    uint32_t *row = H + (int64_t)blockIdx.x * n_tiles;
     const bool windowed = hi - lo < (uint32_t)kBucketWindow;
     if (windowed) {
         for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) sh[w] = 0u;
         __syncthreads();
     }
-    for (int64_t i0 = b0; i0 < b1; i0 += kBucketThreads) {   // block-uniform trip count
-        const int64_t i = i0 + threadIdx.x;
-        const uint32_t k = i < b1 ? keys[i] : kDroppedKey;
-        const unsigned peers = __match_any_sync(FULL, k);
-        if (k != kDroppedKey && lane == __ffs(peers) - 1) {
-            if (windowed)
-                atomicAdd(&sh[k - lo], (uint32_t)__popc(peers));
-            else
-                atomicAdd(&tile_count[k], (uint32_t)__popc(peers));
+    for (int64_t i0 = b0; i0 < b1; i0 += kBucketTile) {      // block-uniform trip count
+        uint32_t k[kBucketIlp];
+        load_keys(keys, i0, b1, n_tiles, k);
+#pragma unroll
+        for (int u = 0; u < kBucketIlp; ++u) {
+            if (windowed) {
+                if (k[u] != kDroppedKey) atomicAdd(&sh[k[u] - lo], 1u);
+            } else {
+                const unsigned peers = __match_any_sync(FULL, k[u]);
+                if (k[u] != kDroppedKey && lane == __ffs(peers) - 1)
+                    atomicAdd(&row[k[u]], (uint32_t)__popc(peers));
+            }
         }
     }
     if (windowed) {
         __syncthreads();
-        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads)
-            if (sh[w] != 0u) atomicAdd(&tile_count[lo + w], sh[w]);
+        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) row[lo + w] = sh[w];
     }
 }
 
-// Places the block's kept instances (their values) in their tiles' slots:
-// first reserves a run per tile after its start (cursor[t] counts what the
-// blocks took so far), then hands out the run's slots.
+// Per tile: H's column -> its exclusive prefix over the blocks, and the
+// tile's count.  A CTA takes 32 tiles (one per lane); its 8 warps split the
+// blocks into 8 segments, summed, scanned across warps, then rewritten.
+constexpr int kColWarps = 8;
+__global__ void __launch_bounds__(32 * kColWarps)
+bucket_columns_kernel(uint32_t *__restrict__ H, int64_t n_blocks, int64_t n_tiles,
+                      uint32_t *__restrict__ tile_count) {
+    __shared__ uint32_t seg[kColWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t per = (n_blocks + kColWarps - 1) / kColWarps;
+    const int64_t r0 = warp * per, r1 = min(r0 + per, n_blocks);
+    uint32_t sum = 0u;
+    if (t < n_tiles)
+        for (int64_t r = r0; r < r1; ++r) sum += H[r * n_tiles + t];
+    seg[warp][lane] = sum;
+    __syncthreads();
+    uint32_t run = 0u;
+    for (int w = 0; w < warp; ++w) run += seg[w][lane];
+    if (t < n_tiles) {
+        for (int64_t r = r0; r < r1; ++r) {
+            const uint32_t c = H[r * n_tiles + t];
+            H[r * n_tiles + t] = run;
+            run += c;
+        }
+        if (warp == kColWarps - 1) tile_count[t] = run;
+    }
+}
+
+// Block b places its kept instances at start[t] + H[b][t] onwards as
+// (depth_key << 32 | record) keys.  The records of a block's range are nearly
+// consecutive, so their depth keys are read almost in order.
 __global__ void __launch_bounds__(kBucketThreads)
 bucket_scatter_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                      const uint64_t *d_n, uint64_t capacity,
-                      const uint32_t *__restrict__ tile_start, uint32_t *__restrict__ cursor,
-                      const uint2 *__restrict__ window, uint32_t *__restrict__ grouped) {
-    extern __shared__ uint32_t sh[];
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+                      const uint32_t *__restrict__ depth_key, const uint64_t *d_n,
+                      uint64_t capacity, int64_t n_tiles, const uint32_t *__restrict__ tile_start,
+                      uint32_t *__restrict__ H, const uint2 *__restrict__ window,
+                      uint64_t *__restrict__ grouped) {
+    __shared__ uint32_t sh[kBucketWindow];
     const int64_t n = sort_count(d_n, capacity);
     int64_t b0, b1;
     block_range(n, b0, b1);
     const uint2 win = window[blockIdx.x];
     const uint32_t lo = win.x, hi = win.y;
     if (lo > hi) return;
+    uint32_t *row = H + (int64_t)blockIdx.x * n_tiles;
     const bool windowed = hi - lo < (uint32_t)kBucketWindow;
-    const uint32_t lanemask_lt = (1u << lane) - 1u;
     if (windowed) {
-        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) sh[w] = 0u;
-        __syncthreads();
-        for (int64_t i0 = b0; i0 < b1; i0 += kBucketThreads) {
-            const int64_t i = i0 + threadIdx.x;
-            const uint32_t k = i < b1 ? keys[i] : kDroppedKey;
-            const unsigned peers = __match_any_sync(FULL, k);
-            if (k != kDroppedKey && lane == __ffs(peers) - 1)
-                atomicAdd(&sh[k - lo], (uint32_t)__popc(peers));
-        }
-        __syncthreads();
-        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads) {
-            const uint32_t c = sh[w];
-            if (c != 0u) sh[w] = tile_start[lo + w] + atomicAdd(&cursor[lo + w], c);
-        }
+        for (uint32_t w = threadIdx.x; w <= hi - lo; w += kBucketThreads)
+            sh[w] = tile_start[lo + w] + row[lo + w];
         __syncthreads();
     }
-    for (int64_t i0 = b0; i0 < b1; i0 += kBucketThreads) {
-        const int64_t i = i0 + threadIdx.x;
-        const uint32_t k = i < b1 ? keys[i] : kDroppedKey;
-        const unsigned peers = __match_any_sync(FULL, k);
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0u;
-        if (k != kDroppedKey && lane == leader)
-            base = windowed ? atomicAdd(&sh[k - lo], (uint32_t)__popc(peers))
-                            : tile_start[k] + atomicAdd(&cursor[k], (uint32_t)__popc(peers));
-        base = __shfl_sync(FULL, base, leader);
-        if (k != kDroppedKey) grouped[base + __popc(peers & lanemask_lt)] = vals[i];
+    for (int64_t i0 = b0; i0 < b1; i0 += kBucketTile) {
+        uint32_t k[kBucketIlp], v[kBucketIlp], d[kBucketIlp];
+        load_keys(keys, i0, b1, n_tiles, k);
+#pragma unroll
+        for (int u = 0; u < kBucketIlp; ++u) {
+            const int64_t i = i0 + u * kBucketThreads + threadIdx.x;
+            v[u] = k[u] != kDroppedKey ? __ldg(vals + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kBucketIlp; ++u) d[u] = k[u] != kDroppedKey ? __ldg(depth_key + v[u]) : 0u;
+#pragma unroll
+        for (int u = 0; u < kBucketIlp; ++u) {
+            if (k[u] == kDroppedKey) continue;
+            const uint32_t pos = windowed ? atomicAdd(&sh[k[u] - lo], 1u)
+                                          : tile_start[k[u]] + atomicAdd(&row[k[u]], 1u);
+            grouped[pos] = ((uint64_t)d[u] << 32) | v[u];
+        }
     }
 }
 
-// Bitonic sort of sk[0 .. n) (n a power of two, <= kTileSortCap) by the whole
-// CTA, ascending.
-__device__ __forceinline__ void bitonic_sort_smem(uint64_t *sk, int n) {
+// ---- register bitonic sort -------------------------------------------------
+// Thread t holds keys t E .. t E + E - 1 (E = kSortE) of a list of n keys (n a
+// power of two, n >= E, padded with ~0).  Stage (k, j) compare-exchanges i
+// and i ^ j (i & j == 0), ascending where i & k == 0.  Distances j < E are
+// inside a thread, E <= j < 32 E between lanes of a warp (shuffles), larger
+// ones across warps through shared memory.
+
+__device__ __forceinline__ void ce_reg(uint64_t &a, uint64_t &b, bool asc) {
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    a = asc ? lo : hi;
+    b = asc ? hi : lo;
+}
+
+// shared-memory slot of key e: e with bits 0-2 xor bits 3-5 (a bijection in
+// every 64-key block) so that a warp's per-thread rows and its consecutive
+// pairs both hit distinct banks
+__device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 7); }
+
+template <int THREADS>
+__device__ __forceinline__ void bitonic_regs(uint64_t (&v)[kSortE], int n, uint64_t *sk) {
+    const int t = threadIdx.x;
+    const int base = t * kSortE;
     for (int k = 2; k <= n; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int p = threadIdx.x; p < (n >> 1); p += kTileSortThreads) {
-                const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-                const int l = i + j;
-                const uint64_t a = sk[i], b = sk[l];
-                const bool up = (i & k) == 0;
-                if ((a > b) == up) {
-                    sk[i] = b;
-                    sk[l] = a;
+        int j = k >> 1;
+        if (j >= 32 * kSortE) {
+            // cross-warp distances: through shared memory
+#pragma unroll
+            for (int r = 0; r < kSortE; ++r) sk[swz(base + r)] = v[r];
+            __syncthreads();
+            for (; j >= 32 * kSortE; j >>= 1) {
+                for (int p = t; p < (n >> 1); p += THREADS) {
+                    const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                    const int l = i + j;
+                    uint64_t a = sk[swz(i)], b = sk[swz(l)];
+                    ce_reg(a, b, (i & k) == 0);
+                    sk[swz(i)] = a;
+                    sk[swz(l)] = b;
                 }
+                __syncthreads();
             }
+#pragma unroll
+            for (int r = 0; r < kSortE; ++r) v[r] = sk[swz(base + r)];
             __syncthreads();
         }
+        // distances between lanes of a warp
+        for (; j >= kSortE; j >>= 1) {
+            const int m = j / kSortE;
+            const bool asc = (base & k) == 0;
+            const bool low = (base & j) == 0;
+#pragma unroll
+            for (int r = 0; r < kSortE; ++r) {
+                const uint64_t o = __shfl_xor_sync(0xffffffffu, v[r], m);
+                const uint64_t mn = v[r] < o ? v[r] : o, mx = v[r] < o ? o : v[r];
+                v[r] = (low == asc) ? mn : mx;
+            }
+        }
+        // distances inside the thread (j = 4, 2, 1 as k allows)
+        if (k >= 8) {
+            const bool asc = (base & k) == 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ce_reg(v[r], v[r + 4], asc);
+        }
+        if (k >= 4) {
+#pragma unroll
+            for (int r = 0; r < kSortE; r += 4) {
+                const bool asc = ((base + r) & k) == 0;
+                ce_reg(v[r], v[r + 2], asc);
+                ce_reg(v[r + 1], v[r + 3], asc);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kSortE; r += 2) ce_reg(v[r], v[r + 1], ((base + r) & k) == 0);
     }
 }
 
 __device__ __forceinline__ int pow2_ceil(int m) {
-    int n = 2;
+    int n = kSortE;
     while (n < m) n <<= 1;
     return n;
+}
+
+// Sorts keys[0 .. m) (m <= THREADS E) in registers: loaded, sorted, and left
+// in v (threads past the list's power-of-two size hold ~0).
+template <int THREADS>
+__device__ __forceinline__ void sort_chunk(const uint64_t *keys, int m, uint64_t (&v)[kSortE],
+                                           uint64_t *sk) {
+    const int n = pow2_ceil(m);
+    const int base = threadIdx.x * kSortE;
+#pragma unroll
+    for (int r = 0; r < kSortE; ++r) v[r] = base + r < m ? keys[base + r] : ~0ull;
+    // threads past n / E join the shuffles and barriers with padding keys
+    bitonic_regs<THREADS>(v, n, sk);
 }
 
 // Merge of the sorted runs a[0 .. la) and b[0 .. lb) into out by the whole
 // CTA: each thread takes an equal share of the output and finds where it
 // starts on the merge path by a binary search (keys are distinct).
+template <int THREADS>
 __device__ void merge_runs(const uint64_t *a, int64_t la, const uint64_t *b, int64_t lb,
                            uint64_t *out) {
     const int64_t total = la + lb;
-    const int64_t d0 = total * threadIdx.x / kTileSortThreads;
-    const int64_t d1 = total * (threadIdx.x + 1) / kTileSortThreads;
+    const int64_t d0 = total * threadIdx.x / THREADS;
+    const int64_t d1 = total * (threadIdx.x + 1) / THREADS;
     int64_t lo = d0 > lb ? d0 - lb : 0, hi = d0 < la ? d0 : la;
     while (lo < hi) {                      // elements of a among the first d0 outputs
         const int64_t mid = (lo + hi) >> 1;
@@ -741,63 +865,73 @@ __device__ void merge_runs(const uint64_t *a, int64_t la, const uint64_t *b, int
     }
 }
 
-// One CTA per tile: its list [start, start + count) of grouped records in
-// (depth_key, record) order into sorted, and the tile's range.
-__global__ void __launch_bounds__(kTileSortThreads)
-tile_depth_sort_kernel(const uint32_t *__restrict__ tile_start,
+// Lists of 2 .. 1024 keys, one 128-thread CTA per tile (other tiles return);
+// also writes every tile's range and the one-key lists.
+__global__ void __launch_bounds__(kSortSmallThreads)
+tile_sort_small_kernel(const uint32_t *__restrict__ tile_start,
                        const uint32_t *__restrict__ tile_count,
-                       const uint32_t *__restrict__ grouped, const uint32_t *__restrict__ depth_key,
-                       uint32_t *__restrict__ sorted, uint32_t *__restrict__ ranges,
-                       uint64_t *__restrict__ tmp_a, uint64_t *__restrict__ tmp_b) {
-    __shared__ uint64_t sk[kTileSortCap];
+                       const uint64_t *__restrict__ grouped, uint32_t *__restrict__ sorted,
+                       uint32_t *__restrict__ ranges) {
+    __shared__ uint64_t sk[kSortSmallThreads * kSortE];
     const int64_t t = blockIdx.x;
     const uint32_t s = tile_start[t], L = tile_count[t];
     if (threadIdx.x == 0) {
         ranges[2 * t] = s;
         ranges[2 * t + 1] = s + L;
+        if (L == 1u) sorted[s] = (uint32_t)grouped[s];
     }
-    if (L == 0u) return;
-    if (L == 1u) {
-        if (threadIdx.x == 0) sorted[s] = grouped[s];
-        return;
-    }
-    // chunks of at most kTileSortCap keys, each sorted in shared memory
-    uint64_t *A = tmp_a + s, *B = tmp_b + s;
-    for (uint32_t c0 = 0; c0 < L; c0 += kTileSortCap) {
-        const int m = (int)min(L - c0, (uint32_t)kTileSortCap);
-        const int n = pow2_ceil(m);
-        for (int i = threadIdx.x; i < n; i += kTileSortThreads) {
-            uint64_t key = ~0ull;
-            if (i < m) {
-                const uint32_t r = grouped[s + c0 + i];
-                key = ((uint64_t)depth_key[r] << 32) | r;
-            }
-            sk[i] = key;
-        }
+    if (L < 2u || L > (uint32_t)(kSortSmallThreads * kSortE)) return;
+    uint64_t v[kSortE];
+    sort_chunk<kSortSmallThreads>(grouped + s, (int)L, v, sk);
+    const int base = threadIdx.x * kSortE;
+#pragma unroll
+    for (int r = 0; r < kSortE; ++r)
+        if (base + r < (int)L) sorted[s + base + r] = (uint32_t)v[r];
+}
+
+// Lists longer than 1024 keys, one 512-thread CTA per tile (other tiles
+// return): chunks of up to 4096 keys sorted in registers; longer lists
+// merged pairwise in global scratch (grouped and tmp, the tile's own range).
+__global__ void __launch_bounds__(kSortLargeThreads)
+tile_sort_large_kernel(const uint32_t *__restrict__ tile_start,
+                       const uint32_t *__restrict__ tile_count, uint64_t *__restrict__ grouped,
+                       uint32_t *__restrict__ sorted, uint64_t *__restrict__ tmp) {
+    constexpr int kCap = kSortLargeThreads * kSortE;
+    __shared__ uint64_t sk[kCap];
+    const int64_t t = blockIdx.x;
+    const uint32_t s = tile_start[t], L = tile_count[t];
+    if (L <= (uint32_t)(kSortSmallThreads * kSortE)) return;
+    const int base = threadIdx.x * kSortE;
+    uint64_t *A = grouped + s, *B = tmp + s;
+    for (uint32_t c0 = 0; c0 < L; c0 += kCap) {
+        const int m = (int)min(L - c0, (uint32_t)kCap);
+        uint64_t v[kSortE];
+        sort_chunk<kSortLargeThreads>(A + c0, m, v, sk);
         __syncthreads();
-        bitonic_sort_smem(sk, n);
-        if (L <= (uint32_t)kTileSortCap) {
-            for (int i = threadIdx.x; i < m; i += kTileSortThreads) sorted[s + i] = (uint32_t)sk[i];
+        if (L <= (uint32_t)kCap) {
+#pragma unroll
+            for (int r = 0; r < kSortE; ++r)
+                if (base + r < m) sorted[s + base + r] = (uint32_t)v[r];
             return;
         }
-        for (int i = threadIdx.x; i < m; i += kTileSortThreads) A[c0 + i] = sk[i];
+#pragma unroll
+        for (int r = 0; r < kSortE; ++r)
+            if (base + r < m) A[c0 + base + r] = v[r];
         __syncthreads();
     }
-    // long lists: merge the sorted chunks pairwise, in global scratch
-    for (int64_t w = kTileSortCap; w < (int64_t)L; w <<= 1) {
+    for (int64_t w = kCap; w < (int64_t)L; w <<= 1) {
         __syncthreads();
         for (int64_t p0 = 0; p0 < (int64_t)L; p0 += 2 * w) {
             const int64_t la = min(w, (int64_t)L - p0);
             const int64_t lb = min(w, (int64_t)L - p0 - la);
-            merge_runs(A + p0, la, A + p0 + la, lb, B + p0);
+            merge_runs<kSortLargeThreads>(A + p0, la, A + p0 + la, lb, B + p0);
         }
-        __threadfence_block();
         uint64_t *x = A;
         A = B;
         B = x;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < L; i += kTileSortThreads) sorted[s + i] = (uint32_t)A[i];
+    for (uint32_t i = threadIdx.x; i < L; i += kSortLargeThreads) sorted[s + i] = (uint32_t)A[i];
 }
 
 }  // namespace mg
@@ -936,18 +1070,26 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
 namespace {
 
 struct BucketLayout {
-    size_t count, cursor, start, window, scan, n_kept, tmp_a, tmp_b, total;
-    int64_t scan_parts;
+    size_t count, start, window, scan, n_kept, hist, grouped, tmp, total;
+    int64_t scan_parts, blocks;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-BucketLayout bucket_layout(uint64_t capacity, int64_t n_tiles) {
+// three blocks per SM, at least 4096 instances per block
+int64_t bucket_blocks(uint64_t capacity) {
+    const int64_t by_size = (int64_t)((capacity + 4095) / 4096);
+    int64_t blocks = 3 * (int64_t)sm_count();
+    if (blocks > by_size) blocks = by_size;
+    if (blocks > kBucketBlocksMax) blocks = kBucketBlocksMax;
+    return blocks < 1 ? 1 : blocks;
+}
+
+BucketLayout bucket_layout(uint64_t capacity, int64_t n_tiles, int64_t blocks) {
     BucketLayout L;
+    L.blocks = blocks;
     size_t o = 0;
     L.count = o;
-    o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
-    L.cursor = o;
     o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
     L.start = o;
     o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
@@ -958,82 +1100,66 @@ BucketLayout bucket_layout(uint64_t capacity, int64_t n_tiles) {
     o = align256(o + sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(L.scan_parts + 1));
     L.n_kept = o;
     o = align256(o + sizeof(uint64_t));
-    L.tmp_a = o;
+    L.hist = o;
+    o = align256(o + sizeof(uint32_t) * (size_t)n_tiles * (size_t)blocks);
+    L.grouped = o;
     o = align256(o + sizeof(uint64_t) * (size_t)capacity);
-    L.tmp_b = o;
+    L.tmp = o;
     o = align256(o + sizeof(uint64_t) * (size_t)capacity);
     L.total = o;
     return L;
 }
 
-// The bucket kernels' 64 KB of dynamic shared memory, opted in once per device.
-mg_status bucket_smem_optin() {
-    static std::mutex mu;
-    static bool done[256] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return MG_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!done[dev]) {
-        const int bytes = (int)(sizeof(uint32_t) * kBucketWindow);
-        if (cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes) != cudaSuccess ||
-            cudaFuncSetAttribute(bucket_scatter_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
-            return MG_ERR_CUDA;
-        done[dev] = true;
-    }
-    return MG_OK;
-}
-
 }  // namespace
 
 extern "C" size_t mg_sort_by_tile_workspace_bytes(uint64_t capacity, int64_t n_tiles_total) {
-    return bucket_layout(capacity, n_tiles_total > 0 ? n_tiles_total : 0).total;
+    if (n_tiles_total < 0) n_tiles_total = 0;
+    return bucket_layout(capacity, n_tiles_total, bucket_blocks(capacity)).total;
 }
 
 extern "C" mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals,
                                      const uint32_t *depth_key, const uint64_t *d_num_instances,
-                                     uint64_t capacity, int64_t n_tiles_total, uint32_t *grouped,
+                                     uint64_t capacity, int64_t n_tiles_total,
                                      uint32_t *sorted_vals, uint32_t *ranges, void *workspace,
                                      size_t workspace_bytes, uint64_t *d_num_sorted,
                                      mg_status_word *d_status, mg_stream_t stream) {
-    if (!keys || !vals || !depth_key || !d_num_instances || !grouped || !sorted_vals || !ranges ||
+    if (!keys || !vals || !depth_key || !d_num_instances || !sorted_vals || !ranges ||
         !workspace || n_tiles_total <= 0 || n_tiles_total >= (int64_t(1) << 31) ||
         n_tiles_total >= (int64_t)kDroppedKey)
         return MG_ERR_INVALID_ARG;
     if (capacity > (uint64_t)kValMask) return MG_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return MG_ERR_INVALID_ARG;
-    const BucketLayout L = bucket_layout(capacity, n_tiles_total);
+    const int64_t blocks = bucket_blocks(capacity);
+    const BucketLayout L = bucket_layout(capacity, n_tiles_total, blocks);
     if (workspace_bytes < L.total) return MG_ERR_INVALID_ARG;
-    if (bucket_smem_optin() != MG_OK) return MG_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = reinterpret_cast<char *>(workspace);
     uint32_t *count = reinterpret_cast<uint32_t *>(ws + L.count);
-    uint32_t *cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
     uint32_t *start = reinterpret_cast<uint32_t *>(ws + L.start);
     uint2 *window = reinterpret_cast<uint2 *>(ws + L.window);
     ScanWS *scan_ws = reinterpret_cast<ScanWS *>(ws + L.scan);
     uint64_t *n_kept = reinterpret_cast<uint64_t *>(ws + L.n_kept);
-    // the tile counts and cursors, and the scan's look-back words, start at 0
-    if (cudaMemsetAsync(ws + L.count, 0, L.start - L.count, s) != cudaSuccess ||
-        cudaMemsetAsync(ws + L.scan, 0, L.n_kept - L.scan, s) != cudaSuccess)
+    uint32_t *H = reinterpret_cast<uint32_t *>(ws + L.hist);
+    uint64_t *grouped = reinterpret_cast<uint64_t *>(ws + L.grouped);
+    // the scan's look-back words and the block-by-tile counts start at 0
+    if (cudaMemsetAsync(ws + L.scan, 0, L.n_kept - L.scan, s) != cudaSuccess ||
+        cudaMemsetAsync(H, 0, sizeof(uint32_t) * (size_t)n_tiles_total * (size_t)blocks, s) !=
+            cudaSuccess)
         return MG_ERR_CUDA;
-    const int64_t by_size = (int64_t)((capacity + 2047) / 2048);
-    int64_t blocks = 2 * (int64_t)sm_count();
-    if (blocks > by_size) blocks = by_size;
-    if (blocks > kBucketBlocksMax) blocks = kBucketBlocksMax;
-    if (blocks < 1) blocks = 1;
-    const size_t smem = sizeof(uint32_t) * kBucketWindow;
-    bucket_count_kernel<<<(unsigned)blocks, kBucketThreads, smem, s>>>(keys, d_num_instances,
-                                                                        capacity, count, window);
+    bucket_count_kernel<<<(unsigned)blocks, kBucketThreads, 0, s>>>(
+        keys, d_num_instances, capacity, n_tiles_total, H, window);
+    bucket_columns_kernel<<<(unsigned)((n_tiles_total + 31) / 32), 32 * kColWarps, 0, s>>>(
+        H, blocks, n_tiles_total, count);
     scan_kernel<<<(unsigned)L.scan_parts, kScanThreads, 0, s>>>(
         count, nullptr, n_tiles_total, start, d_num_sorted != nullptr ? d_num_sorted : n_kept,
         ~0ull, scan_ws, L.scan_parts, d_status, nullptr);
-    bucket_scatter_kernel<<<(unsigned)blocks, kBucketThreads, smem, s>>>(
-        keys, vals, d_num_instances, capacity, start, cursor, window, grouped);
-    tile_depth_sort_kernel<<<(unsigned)n_tiles_total, kTileSortThreads, 0, s>>>(
-        start, count, grouped, depth_key, sorted_vals, ranges,
-        reinterpret_cast<uint64_t *>(ws + L.tmp_a), reinterpret_cast<uint64_t *>(ws + L.tmp_b));
+    bucket_scatter_kernel<<<(unsigned)blocks, kBucketThreads, 0, s>>>(
+        keys, vals, depth_key, d_num_instances, capacity, n_tiles_total, start, H, window,
+        grouped);
+    tile_sort_small_kernel<<<(unsigned)n_tiles_total, kSortSmallThreads, 0, s>>>(
+        start, count, grouped, sorted_vals, ranges);
+    tile_sort_large_kernel<<<(unsigned)n_tiles_total, kSortLargeThreads, 0, s>>>(
+        start, count, grouped, sorted_vals, reinterpret_cast<uint64_t *>(ws + L.tmp));
     return mg_host::launch_status();
 }
 

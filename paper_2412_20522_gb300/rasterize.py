@@ -258,9 +258,9 @@ class Rasterizer:
             # one counting pass over the whole tile id, then each tile's list
             # in depth order
             abi.mg_sort_by_tile(self._buf["keys"], self._buf["vals"], splats.depth_key,
-                                self.num_instances, self.capacity, tiles, self._buf["keys_alt"],
-                                self._buf["vals_alt"], ranges_buf, sort_ws, sort_ws.numel(),
-                                self.num_sorted, self.status, stream)
+                                self.num_instances, self.capacity, tiles, self._buf["vals_alt"],
+                                ranges_buf, sort_ws, sort_ws.numel(), self.num_sorted,
+                                self.status, stream)
             sorted_vals = self._buf["vals_alt"]
         else:
             # instances arrive in depth order: a stable sort by tile id suffices

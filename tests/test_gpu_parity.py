@@ -42,8 +42,12 @@ def _run(rz, g, cams, targets, cfg_kw=None, tile=(16, 16), view_ranges=None, cap
     return rast, dev, img
 
 
+# launch choices of the GPU path that change no result the oracle defines
+LAUNCH_ONLY = ("sort", "render_batch", "render_batch_bwd")
+
+
 def _oracle(g, cams, cfg_kw=None, tile=(16, 16)):
-    cfg_kw = dict(cfg_kw or {})
+    cfg_kw = {k: v for k, v in (cfg_kw or {}).items() if k not in LAUNCH_ONLY}
     gm = cfg_kw.pop("given_mask", None)
     ocfg = pipeline.OracleConfig(tile_w=tile[0], tile_h=tile[1], eps=EPS, **cfg_kw)
     if gm is not None:
