@@ -39,6 +39,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // alpha = min(0.99, o 2^e), e = h1 p1^2 + h2 p2^2, p1 = d.u, p2 = d.u_perp,
 // d = pixel centre - mean.  A = (mx, my, ux, uy), B = (h1, h2, +-o, e_min):
@@ -467,6 +474,10 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
         }
         gb[k] = fmaf(g2[k], bg2, fmaf(g1[k], bg1, g0[k] * bg0));   // b_{N+1} = background
     }
+    // the pixel pair's state as pairs for the paired FP32 arithmetic
+    float2 T2 = make_float2(T[0], T[1]), GB = make_float2(gb[0], gb[1]);
+    const float2 G0 = make_float2(g0[0], g0[1]), G1 = make_float2(g1[0], g1[1]),
+                 G2 = make_float2(g2[0], g2[1]);
     uint32_t tstop = 0;
 #pragma unroll
     for (int k = 0; k < kPix; ++k) tstop = max(tstop, stop[k]);
@@ -527,41 +538,72 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                         continue;
                     }
                     const float4 c = sC[j];
-                    // the mask is uniform over the warp: two straight-line paths
+                    // the mask is uniform over the warp: two straight-line paths.  A
+                    // pixel that is off (under the floor, or at or past its stop)
+                    // takes alpha = 0: its T and colour behind then stay exactly as
+                    // they are and it adds nothing, so the pixel arithmetic has no
+                    // per-lane branches
+                    const float2 a = make_float2(on[0] ? al[0] : 0.0f, on[1] ? al[1] : 0.0f);
                     float v[10];
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) v[q] = 0.0f;
                     if (masked) {
                         // M = 0: T and the colour behind are unchanged; only dL/dM
-#pragma unroll
-                        for (int k = 0; k < kPix; ++k) {
-                            if (!on[k]) continue;
-                            const float gcb =
-                                fmaf(g2[k], c.z, fmaf(g1[k], c.y, g0[k] * c.x)) - gb[k];
-                            v[9] = fmaf(al[k] * T[k], gcb, v[9]);   // Eq. 6 + Appendix A
-                        }
+                        const float gc0 = fmaf(G2.x, c.z, fmaf(G1.x, c.y, G0.x * c.x)) - GB.x;
+                        const float gc1 = fmaf(G2.y, c.z, fmaf(G1.y, c.y, G0.y * c.x)) - GB.y;
+                        v[9] = fmaf(a.y * T2.y, gc1, (a.x * T2.x) * gc0);   // Eq. 6 + Appendix A
                     } else {
-                        float s1 = 0.0f;
-#pragma unroll
-                        for (int k = 0; k < kPix; ++k) {
-                            if (!on[k]) continue;
-                            const float alpha = al[k];
-                            const float Tj = __fdividef(T[k], 1.0f - alpha);
-                            const float gcb =
-                                fmaf(g2[k], c.z, fmaf(g1[k], c.y, g0[k] * c.x)) - gb[k];
-                            const float wt = alpha * Tj;
-                            const float dm = wt * gcb;
-                            v[9] += dm;                                   // Eq. 6 + Appendix A
-                            v[6] = fmaf(wt, g0[k], v[6]);
-                            v[7] = fmaf(wt, g1[k], v[7]);
-                            v[8] = fmaf(wt, g2[k], v[8]);
-                            gb[k] = fmaf(alpha, gcb, gb[k]);  // b_i = b_{i+1} + alpha (c_i - b_{i+1})
-                            T[k] = Tj;
-                            // dL/dalpha * alpha (0 through the 0.99 clamp)
-                            const float m = ar[k] < kAlphaMax ? dm : 0.0f;
-                            v[0] += m;
-                            if (k == 1) s1 = kRowStep * m;
+                        // T_i = T_{i+1} / (1 - alpha) = T_{i+1} + T_{i+1} alpha / (1 - alpha)
+                        // (exactly T_{i+1} for alpha = 0); b_i = b_{i+1} + alpha (c_i -
+                        // b_{i+1}); dL/dM = alpha T_i g.(c_i - b_{i+1}) (Eq. 6 + Appendix
+                        // A), dL/dc = alpha T_i g, dL/dalpha alpha = dL/dM unless clamped
+                        const bool any0 = __any_sync(0xffffffffu, on[0]);
+                        const bool any1 = __any_sync(0xffffffffu, on[1]);
+                        float m0 = 0.0f, m1 = 0.0f;
+                        if (any0 && any1) {
+                            // both pixel rows of the warp: paired FP32, one instruction per pair
+                            const float2 om = fma2(a, bcast2(-1.0f), bcast2(1.0f));
+                            const float2 r = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                            const float2 Tj = fma2(mul2(T2, a), r, T2);
+                            const float2 gc = fma2(G2, bcast2(c.z),
+                                                   fma2(G1, bcast2(c.y),
+                                                        fma2(G0, bcast2(c.x), neg2(GB))));
+                            const float2 wt = mul2(a, Tj);
+                            const float2 dm = mul2(wt, gc);
+                            v[9] = dm.x + dm.y;
+                            v[6] = fmaf(wt.y, G0.y, wt.x * G0.x);
+                            v[7] = fmaf(wt.y, G1.y, wt.x * G1.x);
+                            v[8] = fmaf(wt.y, G2.y, wt.x * G2.x);
+                            GB = fma2(a, gc, GB);
+                            T2 = Tj;
+                            m0 = ar[0] < kAlphaMax ? dm.x : 0.0f;
+                            m1 = ar[1] < kAlphaMax ? dm.y : 0.0f;
+                        } else if (any0) {
+                            // only the first row: the second pixels all contribute nothing
+                            const float Tj = fmaf(T2.x * a.x, rcp_approx(1.0f - a.x), T2.x);
+                            const float gc = fmaf(G2.x, c.z, fmaf(G1.x, c.y, G0.x * c.x)) - GB.x;
+                            const float wt = a.x * Tj;
+                            const float dm = wt * gc;
+                            v[9] = dm;
+                            v[6] = wt * G0.x;
+                            v[7] = wt * G1.x;
+                            v[8] = wt * G2.x;
+                            GB.x = fmaf(a.x, gc, GB.x);
+                            T2.x = Tj;
+                            m0 = ar[0] < kAlphaMax ? dm : 0.0f;
+                        } else {
+                            const float Tj = fmaf(T2.y * a.y, rcp_approx(1.0f - a.y), T2.y);
+                            const float gc = fmaf(G2.y, c.z, fmaf(G1.y, c.y, G0.y * c.x)) - GB.y;
+                            const float wt = a.y * Tj;
+                            const float dm = wt * gc;
+                            v[9] = dm;
+                            v[6] = wt * G0.y;
+                            v[7] = wt * G1.y;
+                            v[8] = wt * G2.y;
+                            GB.y = fmaf(a.y, gc, GB.y);
+                            T2.y = Tj;
+                            m1 = ar[1] < kAlphaMax ? dm : 0.0f;
                         }
+                        v[0] = m0 + m1;
+                        const float s1 = kRowStep * m1;
                         // the pair shares dx and its dy differ by kRowStep: the
                         // moments follow from the sum of m and the second's m
                         v[1] = v[0] * f.dx;                               // sum m dx
