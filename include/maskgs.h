@@ -66,7 +66,9 @@ typedef enum {
     MG_ERR_CUDA = 2,
     MG_ERR_CAPACITY = 3,     /* more (tile, Gaussian) instances than the buffers hold */
     MG_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
-    MG_ERR_UNSUPPORTED = 5
+    MG_ERR_UNSUPPORTED = 5,
+    MG_ERR_BOUNDS = 6        /* an index or range outside its buffer (mg_validate_lists, or
+                                a build with the bounds checks compiled in) */
 } mg_status;
 
 /* Mask modes (mg_raster_cfg.mask_mode):
@@ -494,6 +496,28 @@ mg_status mg_render_inference(const mg_splats *splats, const uint32_t *sorted_va
                               const uint32_t *ranges, const uint32_t *tile_order,
                               const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
                               float *image, mg_stream_t stream);
+
+/* ---- checks ------------------------------------------------------------------- */
+/* Validates the tile lists the render calls consume (the paper has no
+ * counterpart; a check in place of a memory sanitiser): for every tile t the
+ * range [ranges[2t], ranges[2t+1]) is ordered and inside [0, *d_num_sorted),
+ * the non-empty ranges of consecutive tiles do not overlap and their lengths
+ * sum to *d_num_sorted, and every value sorted_vals[i] < n_records is a
+ * record index.  A violation raises MG_ERR_BOUNDS in *d_status (detail 7:
+ * a range, 8: a value, 9: the total; required = the offending tile, position
+ * or total).  Only reads inside the given buffers: sorted_vals holds at least
+ * *d_num_sorted values (nothing past capacity is read), ranges 2
+ * n_tiles_total values.
+ *
+ * Builds with MG_DEBUG_BOUNDS defined (the library's debug build) also check,
+ * inside the binning and sort kernels, every computed write position against
+ * its buffer (a scatter slot against the instance count or capacity, a
+ * duplication chunk's owner against the record count) and skip an
+ * out-of-range write, raising MG_ERR_BOUNDS with the bad index. */
+mg_status mg_validate_lists(const uint32_t *sorted_vals, const uint32_t *ranges,
+                            int64_t n_tiles_total, const uint64_t *d_num_sorted,
+                            uint64_t capacity, int64_t n_records, mg_status_word *d_status,
+                            mg_stream_t stream);
 
 /* ---- helpers ------------------------------------------------------------------ */
 /* Synchronises `stream` and copies the device status word to *h_out (host). */

@@ -12,7 +12,8 @@ import os
 
 from . import build as _build
 
-MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_CAPACITY, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = range(6)
+(MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_CAPACITY, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED,
+ MG_ERR_BOUNDS) = range(7)
 MG_MASK_GUMBEL, MG_MASK_ALL_ONES, MG_MASK_GIVEN, MG_MASK_STE = 0, 1, 2, 3
 MG_APPLY_RASTER, MG_APPLY_OPACITY = 0, 1
 MG_MASK_LOSS_L2, MG_MASK_LOSS_L1 = 0, 1
@@ -28,7 +29,8 @@ EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
             "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
             "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
-            "mg_version", "mg_selftest_wait_timeout", "mg_selftest_warp_wait_timeout")
+            "mg_version", "mg_selftest_wait_timeout", "mg_selftest_warp_wait_timeout",
+            "mg_validate_lists")
 
 
 class MaskgsError(RuntimeError):
@@ -88,18 +90,24 @@ _P = C.POINTER
 _lib = None
 
 
+def debug_library() -> bool:
+    """MASKGS_LIBRARY=debug selects the build with the in-kernel bounds checks."""
+    return os.environ.get("MASKGS_LIBRARY", "") == "debug"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.DEBUG_LIB if debug_library() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libmaskgs.so (building it first when absent and nvcc is present)."""
+    """Load libmaskgs.so, or libmaskgs_debug.so under MASKGS_LIBRARY=debug
+    (building it first when absent and nvcc is present)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = lib_path()
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(debug=debug_library())
     if not os.path.exists(path):
         raise RuntimeError(f"libmaskgs not found at {path}; run paper_2412_20522_gb300/build.py")
     lib = C.CDLL(path)
@@ -147,6 +155,7 @@ def load(build_if_missing: bool = True):
         "mg_version": (C.c_char_p, []),
         "mg_selftest_wait_timeout": (st, [C.c_int32, vp, vp]),
         "mg_selftest_warp_wait_timeout": (st, [C.c_int32, vp, vp]),
+        "mg_validate_lists": (st, [vp, vp, C.c_int64, vp, C.c_uint64, C.c_int64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -332,3 +341,10 @@ def mg_read_status(d_status, stream) -> mg_status_word:
     h = mg_status_word()
     _check("mg_read_status", load().mg_read_status(ptr(d_status), C.byref(h), stream))
     return h
+
+
+def mg_validate_lists(sorted_vals, ranges, n_tiles_total, d_num_sorted, capacity, n_records,
+                      d_status, stream):
+    _check("mg_validate_lists", load().mg_validate_lists(
+        ptr(sorted_vals), ptr(ranges), n_tiles_total, ptr(d_num_sorted), capacity, n_records,
+        ptr(d_status), stream))

@@ -1,7 +1,9 @@
 """Build libmaskgs.so (the C-ABI CUDA library) in-tree with nvcc for sm_103a.
 
 The translation units compile in parallel; the result is
-``paper_2412_20522_gb300/_build/libmaskgs.so``.
+``paper_2412_20522_gb300/_build/libmaskgs.so``.  ``build(debug=True)`` builds
+the same sources with the in-kernel bounds checks compiled in
+(``-DMG_DEBUG_BOUNDS``) as ``libmaskgs_debug.so``.
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmaskgs.so")
+DEBUG_LIB = os.path.join(OUT_DIR, "libmaskgs_debug.so")
 SOURCES = ["abi.cu", "preprocess.cu", "binsort.cu", "render.cu", "prune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -35,17 +38,21 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
+    lib = DEBUG_LIB if debug else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps():
+        return lib
     cc = nvcc()
     flags = [f for f in NVCC_FLAGS if f != "--use_fast_math=false"]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    if debug:
+        flags += ["-DMG_DEBUG_BOUNDS"]
+    tag = "dbg." if debug else ""
 
     def one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}{os.getpid()}.o"))
         cmd = [cc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -58,18 +65,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, err in results:
             sys.stderr.write(err)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
     cmd = [cc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp,
            "-Xlinker", f"-rpath={cuda_lib}"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o in objs:
         os.remove(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                debug="--debug" in sys.argv))

@@ -78,6 +78,7 @@ const char *mg_status_string(int32_t status) {
         case MG_ERR_INVALID_ARG: return "invalid argument";
         case MG_ERR_CUDA: return "CUDA error";
         case MG_ERR_CAPACITY: return "instance capacity exceeded";
+        case MG_ERR_BOUNDS: return "index or range outside its buffer";
         case MG_ERR_TIMEOUT: return "device-side wait timed out";
         case MG_ERR_UNSUPPORTED: return "unsupported";
         default: return "unknown status";

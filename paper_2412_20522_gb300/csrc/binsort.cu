@@ -73,8 +73,11 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k)
-            v[k] = (base + k < n) ? in[order ? order[base + k] : base + k] : 0u;
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t idx = order ? (int64_t)order[base + k < n ? base + k : 0] : base + k;
+            if (base + k < n && !MG_IN_BOUNDS(idx < n, st, 1, idx)) idx = n;   // skipped
+            v[k] = (base + k < n && idx < n) ? in[idx] : 0u;
+        }
     }
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) sum += v[k];
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(256)
 duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restrict__ order,
                  const uint32_t *__restrict__ offsets, int64_t n_records, const uint64_t *__restrict__ d_num_instances,
                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t capacity,
-                 int tile_w, int tile_h, bool filter) {
+                 int tile_w, int tile_h, bool filter, mg_status_word *st) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -154,6 +157,7 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
     // owner of slot s0 (the last position i with offsets[i] <= s0), marked
     // by the scan in the slot's value
     const int64_t lo = (int64_t)vals[s0];
+    if (!MG_IN_BOUNDS(lo < n_records, st, 1, lo)) return;     // warp-uniform
     const uint32_t total32 = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
 
     uint64_t s = s0;
@@ -161,9 +165,11 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
         const int64_t ip = i + lane;
         uint32_t off = 0xFFFFFFFFu, nxt = total32, r = 0, xy0 = 0, w = 1, first = 0, gx = 1;
         float4 b0 = make_float4(0.f, 0.f, 1.f, 0.f), b1 = make_float4(1.f, 0.f, 0.f, 0.f);
+        bool rec_ok = true;
         if (ip < n_records) {
             off = offsets[ip];
             r = order ? order[ip] : (uint32_t)ip;
+            rec_ok = MG_IN_BOUNDS((int64_t)r < n_records, st, 1, r);
             if (lane == 31 && ip + 1 < n_records) nxt = offsets[ip + 1];
         }
         // a position's slot count is the step to the next offset (the last
@@ -171,7 +177,7 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
         const uint32_t down = __shfl_down_sync(FULL, off, 1);
         if (lane < 31 && ip + 1 < n_records) nxt = down;
         const uint32_t nt = ip < n_records ? nxt - off : 0u;
-        if (nt != 0) {
+        if (nt != 0 && rec_ok) {
             const float4 *br = bin_record + 3 * (int64_t)r;
             b0 = br[0];
             b1 = br[1];
@@ -210,7 +216,10 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
                 (int)(xy & 0xFFFFu) + rem, (int)(xy >> 16) + (int)q, tile_w, tile_h);
             const uint32_t fl = __shfl_sync(FULL, first, L);     // every lane shuffles
             const uint32_t gl = __shfl_sync(FULL, gx, L);
-            const uint32_t key = hit ? fl + q * gl + (uint32_t)rem : kDroppedKey;
+            // (debug build: a position whose record index was out of range has
+            // its slots dropped, so nothing later reads with it)
+            const bool okl = __shfl_sync(FULL, (int)rec_ok, L) != 0;
+            const uint32_t key = hit && okl ? fl + q * gl + (uint32_t)rem : kDroppedKey;
             const uint32_t rr = __shfl_sync(FULL, r, L);
             if (p < gend) {
                 keys[p] = key;
@@ -413,6 +422,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
         for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
             const K kk = sk[j];
             const int64_t dst = gbase[((uint64_t)kk >> shift) & 0xFF] + j;
+            if (!MG_IN_BOUNDS(dst >= 0 && dst < n, st, 2, dst)) continue;
             keys_out[dst] = kk;
             vals_out[dst] = sv[j];
         }
@@ -714,7 +724,7 @@ bucket_scatter_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restr
                       const uint32_t *__restrict__ depth_key, const uint64_t *d_n,
                       uint64_t capacity, int64_t n_tiles, const uint32_t *__restrict__ tile_start,
                       uint32_t *__restrict__ H, const uint2 *__restrict__ window,
-                      uint64_t *__restrict__ grouped) {
+                      uint64_t *__restrict__ grouped, mg_status_word *st) {
     __shared__ uint32_t sh[kBucketWindow];
     const int64_t n = sort_count(d_n, capacity);
     int64_t b0, b1;
@@ -744,6 +754,7 @@ bucket_scatter_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restr
             if (k[u] == kDroppedKey) continue;
             const uint32_t pos = windowed ? atomicAdd(&sh[k[u] - lo], 1u)
                                           : tile_start[k[u]] + atomicAdd(&row[k[u]], 1u);
+            if (!MG_IN_BOUNDS((uint64_t)pos < (uint64_t)n, st, 3, pos)) continue;
             grouped[pos] = ((uint64_t)d[u] << 32) | v[u];
         }
     }
@@ -1022,7 +1033,7 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
         duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
             reinterpret_cast<const float4 *>(splats->bin_record), order,
             offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
-            cfg->bin_mode == MG_BIN_FILTERED);
+            cfg->bin_mode == MG_BIN_FILTERED, d_status);
     return mg_host::launch_status();
 }
 
@@ -1155,11 +1166,100 @@ extern "C" mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals,
         ~0ull, scan_ws, L.scan_parts, d_status, nullptr);
     bucket_scatter_kernel<<<(unsigned)blocks, kBucketThreads, 0, s>>>(
         keys, vals, depth_key, d_num_instances, capacity, n_tiles_total, start, H, window,
-        grouped);
+        grouped, d_status);
     tile_sort_small_kernel<<<(unsigned)n_tiles_total, kSortSmallThreads, 0, s>>>(
         start, count, grouped, sorted_vals, ranges);
     tile_sort_large_kernel<<<(unsigned)n_tiles_total, kSortLargeThreads, 0, s>>>(
         start, count, grouped, sorted_vals, reinterpret_cast<uint64_t *>(ws + L.tmp));
+    return mg_host::launch_status();
+}
+
+// --------------------------------------------------------------------------
+// mg_validate_lists: the tile lists checked against their bounds.
+// --------------------------------------------------------------------------
+namespace mg {
+
+constexpr int kValidateThreads = 1024;
+
+// One block walks the tiles in order: every range ordered and inside
+// [0, n), a non-empty range starting at or after the largest end of the
+// non-empty ranges before it (a running maximum carried over block-wide
+// max-scans), and the lengths summing to n.
+__global__ void __launch_bounds__(kValidateThreads)
+validate_ranges_kernel(const uint32_t *__restrict__ ranges, int64_t n_tiles,
+                       const uint64_t *d_n, uint64_t capacity, mg_status_word *st) {
+    __shared__ uint32_t s_warp[kValidateThreads / 32];
+    __shared__ uint32_t s_run;
+    __shared__ unsigned long long s_total;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t dn = *d_n;
+    if (dn > capacity) {
+        if (threadIdx.x == 0) raise_status(st, MG_ERR_BOUNDS, 9, dn);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        s_run = 0u;
+        s_total = 0ull;
+    }
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < n_tiles; t0 += kValidateThreads) {
+        const int64_t t = t0 + threadIdx.x;
+        uint32_t s = 0u, e = 0u;
+        if (t < n_tiles) {
+            s = ranges[2 * t];
+            e = ranges[2 * t + 1];
+            if (e < s || (uint64_t)e > dn) raise_status(st, MG_ERR_BOUNDS, 7, (uint64_t)t);
+        }
+        const bool nonempty = t < n_tiles && e > s;
+        // exclusive max over this chunk's earlier tiles of the non-empty ends
+        uint32_t inc = nonempty ? e : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc = max(inc, x);
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        uint32_t before = s_run;
+        for (int w = 0; w < warp; ++w) before = max(before, s_warp[w]);
+        const uint32_t lane_prev = __shfl_up_sync(FULL, inc, 1);
+        if (lane > 0) before = max(before, lane_prev);
+        if (nonempty) {
+            if (s < before) raise_status(st, MG_ERR_BOUNDS, 7, (uint64_t)t);
+            atomicAdd(&s_total, (unsigned long long)(e - s));
+        }
+        __syncthreads();
+        if (threadIdx.x == kValidateThreads - 1) s_run = max(before, inc);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && s_total != dn) raise_status(st, MG_ERR_BOUNDS, 9, s_total);
+}
+
+__global__ void validate_values_kernel(const uint32_t *__restrict__ vals, const uint64_t *d_n,
+                                       uint64_t capacity, int64_t n_records, mg_status_word *st) {
+    const uint64_t dn = *d_n;
+    const int64_t n = (int64_t)(dn < capacity ? dn : capacity);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        if ((int64_t)vals[i] >= n_records) raise_status(st, MG_ERR_BOUNDS, 8, (uint64_t)i);
+}
+
+}  // namespace mg
+
+extern "C" mg_status mg_validate_lists(const uint32_t *sorted_vals, const uint32_t *ranges,
+                                       int64_t n_tiles_total, const uint64_t *d_num_sorted,
+                                       uint64_t capacity, int64_t n_records,
+                                       mg_status_word *d_status, mg_stream_t stream) {
+    if (!sorted_vals || !ranges || !d_num_sorted || !d_status || n_tiles_total <= 0 ||
+        n_records < 0)
+        return MG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    validate_ranges_kernel<<<1, kValidateThreads, 0, s>>>(ranges, n_tiles_total, d_num_sorted,
+                                                         capacity, d_status);
+    const int64_t blocks = (int64_t)((capacity + 1023) / 1024);
+    validate_values_kernel<<<(unsigned)(blocks < 2048 ? (blocks > 0 ? blocks : 1) : 2048), 256, 0,
+                             s>>>(sorted_vals, d_num_sorted, capacity, n_records, d_status);
     return mg_host::launch_status();
 }
 
@@ -1250,6 +1350,6 @@ extern "C" mg_status mg_bin_noalloc(const mg_splats *splats, const mg_view *view
         duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
             reinterpret_cast<const float4 *>(splats->bin_record), order,
             offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
-            cfg->bin_mode == MG_BIN_FILTERED);
+            cfg->bin_mode == MG_BIN_FILTERED, d_status);
     return mg_host::launch_status();
 }

@@ -37,6 +37,17 @@ __device__ __forceinline__ void raise_status(mg_status_word *w, int32_t st, int3
     atomicCAS(&w->detail, 0, detail);
 }
 
+// Bounds checks of the debug build (MG_DEBUG_BOUNDS): true when the access
+// may go ahead; otherwise MG_ERR_BOUNDS is raised with the offending value
+// and the caller skips the access.  In the ordinary build the test is not
+// compiled.
+#ifdef MG_DEBUG_BOUNDS
+#define MG_IN_BOUNDS(cond, st, detail, value)                                                   \
+    ((cond) ? true : (::mg::raise_status((st), MG_ERR_BOUNDS, (detail), (uint64_t)(value)), false))
+#else
+#define MG_IN_BOUNDS(cond, st, detail, value) true
+#endif
+
 // single-pass scans (decoupled look-back) ------------------------------------
 // A partition's 64-bit status word: flag in the top two bits (1 = aggregate
 // only, 2 = inclusive prefix), value below.

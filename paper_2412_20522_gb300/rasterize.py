@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 from dataclasses import dataclass
 
 import torch
@@ -116,18 +117,25 @@ def _gaussians_struct(p: dict, sh_degree: int) -> abi.mg_gaussians:
 
 
 class _Events:
-    """Optional per-stage CUDA events {name: (start, end)} on the current stream."""
+    """Optional per-stage CUDA events {name: (start, end)} on the current
+    stream, and optional NVTX ranges named after the stages (for a profiler's
+    timeline)."""
 
-    def __init__(self, events):
+    def __init__(self, events, nvtx=False):
         self.events = events
+        self.nvtx = nvtx
 
     def begin(self, name):
+        if self.nvtx:
+            torch.cuda.nvtx.range_push(f"maskgs:{name}")
         if self.events is not None and name in self.events:
             self.events[name][0].record()
 
     def end(self, name):
         if self.events is not None and name in self.events:
             self.events[name][1].record()
+        if self.nvtx:
+            torch.cuda.nvtx.range_pop()
 
 
 class Rasterizer:
@@ -135,9 +143,15 @@ class Rasterizer:
     C-ABI calls on the current torch stream."""
 
     def __init__(self, device="cuda", capacity: int = 0, capacity_headroom: float = 1.25,
-                 tile_order: bool = True):
+                 tile_order: bool = True, validate: bool = False, nvtx: bool | None = None):
         self.device = torch.device(device)
         self.tile_order = tile_order
+        # check the sorted tile lists against their bounds (mg_validate_lists)
+        # before any render call reads them
+        self.validate = validate
+        # NVTX ranges per stage (maskgs:preprocess, :bin, :sort, :render, :loss,
+        # :render_bwd, :preprocess_bwd), or MASKGS_NVTX=1
+        self.nvtx = nvtx if nvtx is not None else os.environ.get("MASKGS_NVTX", "") == "1"
         self.capacity = int(capacity)
         self.headroom = capacity_headroom
         self._buf = {}
@@ -205,7 +219,7 @@ class Rasterizer:
         tiles = abi.mg_total_tiles(views, V, ccfg)
         key_bits = abi.mg_tile_bits(views, V, ccfg)
         stream = self._stream()
-        ev = _Events(stage_events)
+        ev = _Events(stage_events, self.nvtx)
         self.status.zero_()
         splats = self._splats(R, n, V)
         ev.begin("preprocess")
@@ -270,6 +284,13 @@ class Rasterizer:
                               self.status, stream)
             sorted_vals = self._buf["vals_alt"] if alt else self._buf["vals"]
         ev.end("sort")
+        if self.validate:
+            abi.mg_validate_lists(sorted_vals, ranges_buf, tiles, self.num_sorted, self.capacity, R,
+                                  self.status, stream)
+            st = abi.mg_read_status(self.status, stream)
+            if st.status != abi.MG_OK:
+                raise abi.MaskgsError(f"tile lists (detail {st.detail}, at {st.required})",
+                                      st.status)
         # longest tile lists first (launch order only)
         tile_order = self._get("tile_order", tiles, torch.int32) if self.tile_order else None
         if tile_order is not None:
@@ -343,7 +364,7 @@ class Rasterizer:
             loss, dimg = self.l1_loss_grad(image, target)
             return image, loss, dimg
         s = self._state
-        ev = _Events(stage_events)
+        ev = _Events(stage_events, self.nvtx)
         ev.begin("loss")
         loss = self._buf["loss"][:1]
         if s["cfg"].lambda_m != 0.0:
@@ -406,7 +427,7 @@ class Rasterizer:
                                "forward was an inference forward)")
         buf = s["buffers"] if "buffers" in s else self._buf
         stream = self._stream()
-        ev = _Events(stage_events)
+        ev = _Events(stage_events, self.nvtx)
         cfg = s["cfg"]
         if lambda_m is not None and float(lambda_m) != cfg.lambda_m:
             cfg = abi.mg_raster_cfg.from_buffer_copy(cfg)
