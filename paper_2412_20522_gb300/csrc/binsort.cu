@@ -699,18 +699,32 @@ bucket_columns_kernel(uint32_t *__restrict__ H, int64_t n_blocks, int64_t n_tile
     const int64_t t = (int64_t)blockIdx.x * 32 + lane;
     const int64_t per = (n_blocks + kColWarps - 1) / kColWarps;
     const int64_t r0 = warp * per, r1 = min(r0 + per, n_blocks);
+    // 8 rows per round trip: the loads of a round are independent
+    constexpr int U = 8;
     uint32_t sum = 0u;
     if (t < n_tiles)
-        for (int64_t r = r0; r < r1; ++r) sum += H[r * n_tiles + t];
+        for (int64_t r = r0; r < r1; r += U) {
+            uint32_t c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) c[u] = r + u < r1 ? H[(r + u) * n_tiles + t] : 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) sum += c[u];
+        }
     seg[warp][lane] = sum;
     __syncthreads();
     uint32_t run = 0u;
     for (int w = 0; w < warp; ++w) run += seg[w][lane];
     if (t < n_tiles) {
-        for (int64_t r = r0; r < r1; ++r) {
-            const uint32_t c = H[r * n_tiles + t];
-            H[r * n_tiles + t] = run;
-            run += c;
+        for (int64_t r = r0; r < r1; r += U) {
+            uint32_t c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) c[u] = r + u < r1 ? H[(r + u) * n_tiles + t] : 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (r + u < r1) {
+                    H[(r + u) * n_tiles + t] = run;
+                    run += c[u];
+                }
         }
         if (warp == kColWarps - 1) tile_count[t] = run;
     }
@@ -760,98 +774,94 @@ bucket_scatter_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restr
     }
 }
 
-// ---- register bitonic sort -------------------------------------------------
-// Thread t holds keys t E .. t E + E - 1 (E = kSortE) of a list of n keys (n a
-// power of two, n >= E, padded with ~0).  Stage (k, j) compare-exchanges i
-// and i ^ j (i & j == 0), ascending where i & k == 0.  Distances j < E are
-// inside a thread, E <= j < 32 E between lanes of a warp (shuffles), larger
-// ones across warps through shared memory.
+// ---- per-tile merge sort -------------------------------------------------------
+// A tile's keys (distinct 64-bit (depth_key << 32 | record)) sorted by one
+// CTA: each thread sorts kSortE keys in registers (Batcher's 19-comparator
+// network for 8), then runs are merged pairwise in shared memory, every
+// thread producing kSortE outputs of its pair after a merge-path binary
+// search for where its share starts.  O(n log n) work: a bitonic network's
+// O(n log^2 n) cost 4-5x more on these lists.
 
-__device__ __forceinline__ void ce_reg(uint64_t &a, uint64_t &b, bool asc) {
+__device__ __forceinline__ void ce_asc(uint64_t &a, uint64_t &b) {
     const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-    a = asc ? lo : hi;
-    b = asc ? hi : lo;
+    a = lo;
+    b = hi;
 }
 
-// shared-memory slot of key e: e with bits 0-2 xor bits 3-5 (a bijection in
-// every 64-key block) so that a warp's per-thread rows and its consecutive
-// pairs both hit distinct banks
-__device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 7); }
+__device__ __forceinline__ void sort8_regs(uint64_t (&v)[kSortE]) {
+    ce_asc(v[0], v[1]); ce_asc(v[2], v[3]); ce_asc(v[4], v[5]); ce_asc(v[6], v[7]);
+    ce_asc(v[0], v[2]); ce_asc(v[1], v[3]); ce_asc(v[4], v[6]); ce_asc(v[5], v[7]);
+    ce_asc(v[1], v[2]); ce_asc(v[5], v[6]);
+    ce_asc(v[0], v[4]); ce_asc(v[1], v[5]); ce_asc(v[2], v[6]); ce_asc(v[3], v[7]);
+    ce_asc(v[2], v[4]); ce_asc(v[3], v[5]);
+    ce_asc(v[1], v[2]); ce_asc(v[3], v[4]); ce_asc(v[5], v[6]);
+}
 
+// Shared-memory slot of key e: the low three bits XORed with a hash of the
+// thread row (e >> 3), so that the 32 threads of a warp writing their 8-key
+// rows hit distinct banks.
+__device__ __forceinline__ int swz(int e) { return e ^ (((e >> 3) ^ (e >> 6)) & 7); }
+
+// Sorts keys[0 .. L) (L <= THREADS kSortE) into out (records: the low 32
+// bits), using S0 and S1 (THREADS kSortE keys each) in shared memory.
 template <int THREADS>
-__device__ __forceinline__ void bitonic_regs(uint64_t (&v)[kSortE], int n, uint64_t *sk) {
-    const int t = threadIdx.x;
-    const int base = t * kSortE;
-    for (int k = 2; k <= n; k <<= 1) {
-        int j = k >> 1;
-        if (j >= 32 * kSortE) {
-            // cross-warp distances: through shared memory
+__device__ void merge_sort_tile(const uint64_t *__restrict__ keys, int L,
+                                uint32_t *__restrict__ out, uint64_t *S0, uint64_t *S1) {
+    const int n8 = (L + kSortE - 1) & ~(kSortE - 1);          // runs of kSortE, padded with ~0
+    const int base = threadIdx.x * kSortE;
+    const bool mine = base < n8;
+    uint64_t v[kSortE];
 #pragma unroll
-            for (int r = 0; r < kSortE; ++r) sk[swz(base + r)] = v[r];
-            __syncthreads();
-            for (; j >= 32 * kSortE; j >>= 1) {
-                for (int p = t; p < (n >> 1); p += THREADS) {
-                    const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-                    const int l = i + j;
-                    uint64_t a = sk[swz(i)], b = sk[swz(l)];
-                    ce_reg(a, b, (i & k) == 0);
-                    sk[swz(i)] = a;
-                    sk[swz(l)] = b;
-                }
-                __syncthreads();
+    for (int r = 0; r < kSortE; ++r) v[r] = base + r < L ? keys[base + r] : ~0ull;
+    if (mine) {
+        sort8_regs(v);
+#pragma unroll
+        for (int r = 0; r < kSortE; ++r) S0[swz(base + r)] = v[r];
+    }
+    __syncthreads();
+    uint64_t *cur = S0, *nxt = S1;
+    for (int w = kSortE; w < n8; w <<= 1) {
+        if (mine) {
+            const int a0 = (base / (2 * w)) * (2 * w);
+            const int la = min(w, n8 - a0);
+            const int b0 = a0 + la;
+            const int lb = min(w, n8 - b0);
+            const int d0 = base - a0;                          // this thread's first output
+            int lo = d0 > lb ? d0 - lb : 0, hi = d0 < la ? d0 : la;
+            while (lo < hi) {                                  // A's share of the first d0
+                const int mid = (lo + hi) >> 1;
+                if (cur[swz(a0 + mid)] < cur[swz(b0 + d0 - 1 - mid)]) lo = mid + 1;
+                else hi = mid;
             }
-#pragma unroll
-            for (int r = 0; r < kSortE; ++r) v[r] = sk[swz(base + r)];
-            __syncthreads();
-        }
-        // distances between lanes of a warp
-        for (; j >= kSortE; j >>= 1) {
-            const int m = j / kSortE;
-            const bool asc = (base & k) == 0;
-            const bool low = (base & j) == 0;
+            int ia = lo, ib = d0 - lo;
+            uint64_t x = ia < la ? cur[swz(a0 + ia)] : ~0ull;
+            uint64_t y = ib < lb ? cur[swz(b0 + ib)] : ~0ull;
 #pragma unroll
             for (int r = 0; r < kSortE; ++r) {
-                const uint64_t o = __shfl_xor_sync(0xffffffffu, v[r], m);
-                const uint64_t mn = v[r] < o ? v[r] : o, mx = v[r] < o ? o : v[r];
-                v[r] = (low == asc) ? mn : mx;
+                const bool take_a = x < y;                     // keys are distinct; ~0 pads last
+                v[r] = take_a ? x : y;
+                if (take_a) {
+                    ++ia;
+                    x = ia < la ? cur[swz(a0 + ia)] : ~0ull;
+                } else {
+                    ++ib;
+                    y = ib < lb ? cur[swz(b0 + ib)] : ~0ull;
+                }
             }
         }
-        // distances inside the thread (j = 4, 2, 1 as k allows)
-        if (k >= 8) {
-            const bool asc = (base & k) == 0;
+        __syncthreads();
+        if (mine) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) ce_reg(v[r], v[r + 4], asc);
+            for (int r = 0; r < kSortE; ++r) nxt[swz(base + r)] = v[r];
         }
-        if (k >= 4) {
-#pragma unroll
-            for (int r = 0; r < kSortE; r += 4) {
-                const bool asc = ((base + r) & k) == 0;
-                ce_reg(v[r], v[r + 2], asc);
-                ce_reg(v[r + 1], v[r + 3], asc);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kSortE; r += 2) ce_reg(v[r], v[r + 1], ((base + r) & k) == 0);
+        __syncthreads();
+        uint64_t *t = cur;
+        cur = nxt;
+        nxt = t;
     }
-}
-
-__device__ __forceinline__ int pow2_ceil(int m) {
-    int n = kSortE;
-    while (n < m) n <<= 1;
-    return n;
-}
-
-// Sorts keys[0 .. m) (m <= THREADS E) in registers: loaded, sorted, and left
-// in v (threads past the list's power-of-two size hold ~0).
-template <int THREADS>
-__device__ __forceinline__ void sort_chunk(const uint64_t *keys, int m, uint64_t (&v)[kSortE],
-                                           uint64_t *sk) {
-    const int n = pow2_ceil(m);
-    const int base = threadIdx.x * kSortE;
 #pragma unroll
-    for (int r = 0; r < kSortE; ++r) v[r] = base + r < m ? keys[base + r] : ~0ull;
-    // threads past n / E join the shuffles and barriers with padding keys
-    bitonic_regs<THREADS>(v, n, sk);
+    for (int r = 0; r < kSortE; ++r)
+        if (base + r < L) out[base + r] = (uint32_t)v[r];
 }
 
 // Merge of the sorted runs a[0 .. la) and b[0 .. lb) into out by the whole
@@ -882,52 +892,50 @@ __global__ void __launch_bounds__(kSortSmallThreads)
 tile_sort_small_kernel(const uint32_t *__restrict__ tile_start,
                        const uint32_t *__restrict__ tile_count,
                        const uint64_t *__restrict__ grouped, uint32_t *__restrict__ sorted,
-                       uint32_t *__restrict__ ranges) {
-    __shared__ uint64_t sk[kSortSmallThreads * kSortE];
+                       uint32_t *__restrict__ ranges, uint32_t *__restrict__ long_tiles,
+                       uint32_t *long_count) {
+    __shared__ uint64_t S0[kSortSmallThreads * kSortE], S1[kSortSmallThreads * kSortE];
     const int64_t t = blockIdx.x;
     const uint32_t s = tile_start[t], L = tile_count[t];
     if (threadIdx.x == 0) {
         ranges[2 * t] = s;
         ranges[2 * t + 1] = s + L;
         if (L == 1u) sorted[s] = (uint32_t)grouped[s];
+        // longer lists go to the large sort's work list
+        if (L > (uint32_t)(kSortSmallThreads * kSortE)) long_tiles[atomicAdd(long_count, 1u)] = (uint32_t)t;
     }
     if (L < 2u || L > (uint32_t)(kSortSmallThreads * kSortE)) return;
-    uint64_t v[kSortE];
-    sort_chunk<kSortSmallThreads>(grouped + s, (int)L, v, sk);
-    const int base = threadIdx.x * kSortE;
-#pragma unroll
-    for (int r = 0; r < kSortE; ++r)
-        if (base + r < (int)L) sorted[s + base + r] = (uint32_t)v[r];
+    merge_sort_tile<kSortSmallThreads>(grouped + s, (int)L, sorted + s, S0, S1);
 }
 
-// Lists longer than 1024 keys, one 512-thread CTA per tile (other tiles
-// return): chunks of up to 4096 keys sorted in registers; longer lists
-// merged pairwise in global scratch (grouped and tmp, the tile's own range).
-__global__ void __launch_bounds__(kSortLargeThreads)
-tile_sort_large_kernel(const uint32_t *__restrict__ tile_start,
-                       const uint32_t *__restrict__ tile_count, uint64_t *__restrict__ grouped,
-                       uint32_t *__restrict__ sorted, uint64_t *__restrict__ tmp) {
+// Lists longer than 1024 keys, from the work list the small sort filled: a
+// persistent grid of 512-thread CTAs takes them in turn.  Chunks of up to
+// 4096 keys are merge-sorted in shared memory; longer lists are merged
+// pairwise in global scratch (grouped and tmp, the tile's own range).
+__device__ void sort_long_tile(uint32_t s, uint32_t L, uint64_t *__restrict__ grouped,
+                               uint32_t *__restrict__ sorted, uint64_t *__restrict__ tmp,
+                               uint64_t *S0, uint64_t *S1) {
     constexpr int kCap = kSortLargeThreads * kSortE;
-    __shared__ uint64_t sk[kCap];
-    const int64_t t = blockIdx.x;
-    const uint32_t s = tile_start[t], L = tile_count[t];
-    if (L <= (uint32_t)(kSortSmallThreads * kSortE)) return;
-    const int base = threadIdx.x * kSortE;
+    if (L <= (uint32_t)kCap) {
+        merge_sort_tile<kSortLargeThreads>(grouped + s, (int)L, sorted + s, S0, S1);
+        __syncthreads();
+        return;
+    }
+    // chunks sorted in shared memory and written back, then merged pairwise
     uint64_t *A = grouped + s, *B = tmp + s;
     for (uint32_t c0 = 0; c0 < L; c0 += kCap) {
         const int m = (int)min(L - c0, (uint32_t)kCap);
-        uint64_t v[kSortE];
-        sort_chunk<kSortLargeThreads>(A + c0, m, v, sk);
+        // sort the chunk; its records land in sorted (overwritten later) and
+        // its keys are read back from shared memory in order
+        merge_sort_tile<kSortLargeThreads>(A + c0, m, sorted + s + c0, S0, S1);
         __syncthreads();
-        if (L <= (uint32_t)kCap) {
-#pragma unroll
-            for (int r = 0; r < kSortE; ++r)
-                if (base + r < m) sorted[s + base + r] = (uint32_t)v[r];
-            return;
-        }
-#pragma unroll
-        for (int r = 0; r < kSortE; ++r)
-            if (base + r < m) A[c0 + base + r] = v[r];
+        // the sorted chunk: recover the keys in order (run order after the
+        // last pass is in whichever buffer the passes ended on)
+        const int n8 = (m + kSortE - 1) & ~(kSortE - 1);
+        int passes = 0;
+        for (int w = kSortE; w < n8; w <<= 1) ++passes;
+        const uint64_t *fin = (passes & 1) ? S1 : S0;
+        for (int i = threadIdx.x; i < m; i += kSortLargeThreads) A[c0 + i] = fin[swz(i)];
         __syncthreads();
     }
     for (int64_t w = kCap; w < (int64_t)L; w <<= 1) {
@@ -943,6 +951,22 @@ tile_sort_large_kernel(const uint32_t *__restrict__ tile_start,
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < L; i += kSortLargeThreads) sorted[s + i] = (uint32_t)A[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSortLargeThreads)
+tile_sort_large_kernel(const uint32_t *__restrict__ tile_start,
+                       const uint32_t *__restrict__ tile_count,
+                       const uint32_t *__restrict__ long_tiles, const uint32_t *long_count,
+                       uint64_t *__restrict__ grouped, uint32_t *__restrict__ sorted,
+                       uint64_t *__restrict__ tmp) {
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    uint64_t *S0 = reinterpret_cast<uint64_t *>(sort_smem), *S1 = S0 + kSortLargeThreads * kSortE;
+    const uint32_t n_long = *long_count;
+    for (uint32_t i = blockIdx.x; i < n_long; i += gridDim.x) {
+        const uint32_t t = long_tiles[i];
+        sort_long_tile(tile_start[t], tile_count[t], grouped, sorted, tmp, S0, S1);
+    }
 }
 
 }  // namespace mg
@@ -1081,7 +1105,7 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
 namespace {
 
 struct BucketLayout {
-    size_t count, start, window, scan, n_kept, hist, grouped, tmp, total;
+    size_t count, start, window, scan, long_count, n_kept, long_tiles, hist, grouped, tmp, total;
     int64_t scan_parts, blocks;
 };
 
@@ -1094,6 +1118,24 @@ int64_t bucket_blocks(uint64_t capacity) {
     if (blocks > by_size) blocks = by_size;
     if (blocks > kBucketBlocksMax) blocks = kBucketBlocksMax;
     return blocks < 1 ? 1 : blocks;
+}
+
+constexpr size_t kTileSortLargeSmem = 2 * sizeof(uint64_t) * kSortLargeThreads * kSortE;
+
+// The large tile sort's 64 KB of dynamic shared memory, opted in once per device.
+mg_status tile_sort_smem_optin() {
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(tile_sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kTileSortLargeSmem) != cudaSuccess)
+            return MG_ERR_CUDA;
+        done[dev] = true;
+    }
+    return MG_OK;
 }
 
 BucketLayout bucket_layout(uint64_t capacity, int64_t n_tiles, int64_t blocks) {
@@ -1109,8 +1151,12 @@ BucketLayout bucket_layout(uint64_t capacity, int64_t n_tiles, int64_t blocks) {
     L.scan_parts = (n_tiles + kScanPart - 1) / kScanPart;
     L.scan = o;
     o = align256(o + sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(L.scan_parts + 1));
+    L.long_count = o;                     // zeroed with the scan's words
+    o = align256(o + sizeof(uint32_t));
     L.n_kept = o;
     o = align256(o + sizeof(uint64_t));
+    L.long_tiles = o;
+    o = align256(o + sizeof(uint32_t) * (size_t)n_tiles);
     L.hist = o;
     o = align256(o + sizeof(uint32_t) * (size_t)n_tiles * (size_t)blocks);
     L.grouped = o;
@@ -1143,6 +1189,7 @@ extern "C" mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals,
     const int64_t blocks = bucket_blocks(capacity);
     const BucketLayout L = bucket_layout(capacity, n_tiles_total, blocks);
     if (workspace_bytes < L.total) return MG_ERR_INVALID_ARG;
+    if (tile_sort_smem_optin() != MG_OK) return MG_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = reinterpret_cast<char *>(workspace);
     uint32_t *count = reinterpret_cast<uint32_t *>(ws + L.count);
@@ -1167,10 +1214,14 @@ extern "C" mg_status mg_sort_by_tile(const uint32_t *keys, const uint32_t *vals,
     bucket_scatter_kernel<<<(unsigned)blocks, kBucketThreads, 0, s>>>(
         keys, vals, depth_key, d_num_instances, capacity, n_tiles_total, start, H, window,
         grouped, d_status);
+    uint32_t *long_tiles = reinterpret_cast<uint32_t *>(ws + L.long_tiles);
+    uint32_t *long_count = reinterpret_cast<uint32_t *>(ws + L.long_count);
     tile_sort_small_kernel<<<(unsigned)n_tiles_total, kSortSmallThreads, 0, s>>>(
-        start, count, grouped, sorted_vals, ranges);
-    tile_sort_large_kernel<<<(unsigned)n_tiles_total, kSortLargeThreads, 0, s>>>(
-        start, count, grouped, sorted_vals, reinterpret_cast<uint64_t *>(ws + L.tmp));
+        start, count, grouped, sorted_vals, ranges, long_tiles, long_count);
+    const int64_t long_grid = min((int64_t)2 * sm_count(), n_tiles_total);
+    tile_sort_large_kernel<<<(unsigned)long_grid, kSortLargeThreads, kTileSortLargeSmem, s>>>(
+        start, count, long_tiles, long_count, grouped, sorted_vals,
+        reinterpret_cast<uint64_t *>(ws + L.tmp));
     return mg_host::launch_status();
 }
 
