@@ -18,8 +18,9 @@
 //
 // The radix sort is "onesweep" (Adinets & Merrill, "Onesweep: a faster least
 // significant digit radix sort for GPUs", 2022): 8-bit digits, one kernel per
-// digit, local ranking by warp match-any multi-split, global offsets by
-// decoupled look-back.
+// digit, local ranking by warp multi-split (lanes with equal digits found
+// through per-warp mask words in shared memory), global offsets by decoupled
+// look-back.
 //
 // Every cross-block wait is bounded: after kMaxTimeoutSpins polls the kernel
 // records MG_ERR_TIMEOUT in the status word and carries on (results are then
@@ -325,6 +326,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
     K *sk = reinterpret_cast<K *>(sort_stage);
     uint32_t *sv = reinterpret_cast<uint32_t *>(sort_stage + sizeof(K) * kSortPart);
     __shared__ uint32_t whist[kSortWarps][256];
+    __shared__ uint32_t wmatch[kSortWarps][256];
     __shared__ uint32_t dstart[256];
     __shared__ int64_t gbase[256];
     __shared__ uint64_t sm_warp[33];
@@ -336,6 +338,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
     uint32_t *status = ws->status + (int64_t)(pass & 1) * max_parts * 256;
     uint32_t *status_next = ws->status + (int64_t)((pass + 1) & 1) * max_parts * 256;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&wmatch[0][0])[i] = 0u;
 
     for (;;) {
         __syncthreads();
@@ -360,14 +363,22 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
             const bool kept = valid && !(DROP && (uint32_t)k[i] == kDroppedKey);
             dig[i] = kept ? (int)(((uint64_t)k[i] >> shift) & 0xFF) : 256;
         }
+        // lanes with equal digits find each other through a per-warp mask
+        // word per digit (shared-memory atomicOr, read back, reset by the
+        // group's highest lane)
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
-            const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
-            const int leader = __ffs(peers) - 1;
+            const bool kept = dig[i] < 256;
+            if (kept) atomicOr(&wmatch[warp][dig[i]], 1u << lane);
+            __syncwarp();
+            const unsigned peers = kept ? wmatch[warp][dig[i]] : 0u;
+            __syncwarp();
+            const int leader = kept ? 31 - __clz(peers) : lane;
             uint32_t old = 0;
-            if (lane == leader && dig[i] < 256) {
+            if (kept && lane == leader) {
                 old = whist[warp][dig[i]];
                 whist[warp][dig[i]] = old + __popc(peers);
+                wmatch[warp][dig[i]] = 0u;
             }
             old = __shfl_sync(0xffffffffu, old, leader);
             rank[i] = old + __popc(peers & lanemask_lt);
