@@ -304,6 +304,16 @@ def test_degenerate_cases(rz):
     assert final_T[36, 40] <= 0.0101                            # one clamped blend, then stop
 
 
+@pytest.mark.parametrize("wh", [(1, 1), (17, 1), (3, 2), (1, 33)])
+def test_frames_smaller_than_a_tile(rz, wh):
+    """Frames of a few pixels: one tile (or a row of them) with most of its
+    pixels outside the frame; every warp block is partly or wholly outside."""
+    w, h = wh
+    g = scenes.uniform_gaussians(2000, seed=71)
+    cam = scenes.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), w, h, 40.0)
+    _full_check(rz, g, [cam], [scenes.target_image(h, w, seed=72)], dict(bg=(0.1, 0.5, 0.3)))
+
+
 def test_every_gaussian_masked(rz):
     """M = 0 everywhere: the image is the background and only dL/dM (hence
     the mask scores' gradient) is non-zero."""
