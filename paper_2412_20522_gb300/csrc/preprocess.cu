@@ -282,6 +282,10 @@ __device__ __forceinline__ void sh_colour(const void *sh, int64_t i, const float
     for_sh_row<ST, ROW>(sh, i, [&](int e, float v) { acc[e % 3] = fmaf(Y[e / 3], v, acc[e % 3]); });
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // The SH rows are read only for Gaussians that are visible in a view, one
 // row per lane with 128-bit loads (no row of an invisible Gaussian is read).
 // Eight CTAs per SM: the 64 registers this leaves hold the kernel without
@@ -339,6 +343,7 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
 
     const float op = 1.0f / (1.0f + __expf(-ol));
 
+    bool sh_requested = false;
     for (int v = 0; v < vt.n_views; ++v) {
         if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
         const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
@@ -351,6 +356,16 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
             out.clamp[r] = 0;
             if (out.depth_key != nullptr) out.depth_key[r] = 0xFFFFFFFFu;
             continue;
+        }
+        if (!sh_requested) {
+            // the SH row towards L2 now: the binning and eigen work below
+            // runs while it travels
+            constexpr int RB = 3 * (DEG + 1) * (DEG + 1) * (int)sizeof(ST);
+            const char *sp0 = reinterpret_cast<const char *>(g.sh) + i * RB;
+#pragma unroll
+            for (int o = 0; o < RB; o += 128) prefetch_l2(sp0 + o);
+            prefetch_l2(sp0 + RB - 1);
+            sh_requested = true;
         }
         // the binning's candidate tiles: the whole 3-sigma rectangle, or (tile
         // filter) its tiles that the filter can keep
@@ -552,10 +567,6 @@ __device__ __forceinline__ void cov_backward(const CovState &S, const mg_camera 
                 dJ12 * fy * S.tyc * itz3 * (clampy ? 1.0f : 2.0f);
     if (!clampx) dL_dt[0] += -dJ02 * fx * itz2;
     if (!clampy) dL_dt[1] += -dJ12 * fy * itz2;
-}
-
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // dL/dsh accumulates over views in a per-warp shared-memory tile (one row
