@@ -161,18 +161,27 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
     if (!MG_IN_BOUNDS(lo < n_records, st, 1, lo)) return;     // warp-uniform
     const uint32_t total32 = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
 
-    uint64_t s = s0;
-    for (int64_t i = lo; s < s1; i += 32) {
-        const int64_t ip = i + lane;
-        uint32_t off = 0xFFFFFFFFu, nxt = total32, r = 0, xy0 = 0, w = 1, first = 0, gx = 1;
-        float4 b0 = make_float4(0.f, 0.f, 1.f, 0.f), b1 = make_float4(1.f, 0.f, 0.f, 0.f);
-        bool rec_ok = true;
+    // the offsets and record indices of the next 32 positions are loaded
+    // one group ahead, so they travel during the current group's slots
+    auto load_group = [&](int64_t ip, uint32_t &off, uint32_t &r, uint32_t &nxt) {
+        off = 0xFFFFFFFFu;
+        r = 0;
+        nxt = total32;
         if (ip < n_records) {
             off = offsets[ip];
             r = order ? order[ip] : (uint32_t)ip;
-            rec_ok = MG_IN_BOUNDS((int64_t)r < n_records, st, 1, r);
             if (lane == 31 && ip + 1 < n_records) nxt = offsets[ip + 1];
         }
+    };
+    uint32_t off_n, r_n, nxt_n;
+    load_group(lo + lane, off_n, r_n, nxt_n);
+    uint64_t s = s0;
+    for (int64_t i = lo; s < s1; i += 32) {
+        const int64_t ip = i + lane;
+        uint32_t off = off_n, nxt = nxt_n, r = r_n, xy0 = 0, w = 1, first = 0, gx = 1;
+        float4 b0 = make_float4(0.f, 0.f, 1.f, 0.f), b1 = make_float4(1.f, 0.f, 0.f, 0.f);
+        bool rec_ok = true;
+        if (ip < n_records) rec_ok = MG_IN_BOUNDS((int64_t)r < n_records, st, 1, r);
         // a position's slot count is the step to the next offset (the last
         // position ends at the total; offsets below the capacity are exact)
         const uint32_t down = __shfl_down_sync(FULL, off, 1);
@@ -193,6 +202,7 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
         const uint64_t last = ip < n_records ? (uint64_t)off + nt : K;
         const uint64_t gend_all = __shfl_sync(FULL, last, 31);
         const uint64_t gend = gend_all < s1 ? gend_all : s1;
+        if (gend < s1) load_group(ip + 32, off_n, r_n, nxt_n);    // another group follows
         for (uint64_t base = s; base < gend; base += 32) {      // warp-uniform trip count
             const uint64_t p = base + lane;
             const uint32_t pp = (uint32_t)p;
