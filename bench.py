@@ -209,7 +209,8 @@ def run_ours(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
 
-    g, cams, target = scenes.scene_workload()
+    w2 = scenes.workload("c2_scene")
+    g, cams, target = w2.gaussians, w2.cams, w2.targets[0]
     W, H = cams[0].width, cams[0].height
     params = {k: torch.as_tensor(np.ascontiguousarray(getattr(g, k))).to(dev)
               for k in PARAM_NAMES}
@@ -570,13 +571,6 @@ def _device_params(g, dev, storage=None):
     return p
 
 
-def _concat_scenes(scs):
-    from paper_2412_20522_gb300 import scenes
-    cat = {k: np.concatenate([getattr(s, k) for s in scs]) for k in
-           ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")}
-    return scenes.Gaussians(**cat, sh_degree=scs[0].sh_degree)
-
-
 def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
     """The batched and reduced-storage forms, each against the plain FP32
     single-view form measured above (same GPU, same run)."""
@@ -590,48 +584,47 @@ def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
 
     # multi-view batch: 8 ring cameras, one shared mask sample, summed
     # gradients, one captured launch sequence, autotuned tile shape
-    cams8 = [scenes.ring_camera(2 * math.pi * k / 8, 4.0, 1557, 1038, 1150.0) for k in range(8)]
-    p = _device_params(g, dev)
-    tgt8 = torch.as_tensor(np.concatenate([target.reshape(-1)] * 8)).to(dev)
+    w3 = scenes.workload("c3_multiview")         # the same scene as g, 8 ring cameras
+    cams8 = w3.cams
+    p = _device_params(w3.gaussians, dev)
+    tgt8 = torch.as_tensor(np.concatenate([t.reshape(-1) for t in w3.targets])).to(dev)
     tuned = autotune(p, cams8, tgt8, steps=3)
     gs = GraphStep(p, cams8, tuned, tgt8)
     ms = time_step(gs.replay, steps=steps)
-    pix = 8 * 1557 * 1038
-    forms["multiview_graph"] = {"views": 8, "tile": f"{tuned.tile_w}x{tuned.tile_h}",
+    pix = sum(c.width * c.height for c in cams8)
+    forms["multiview_graph"] = {"views": len(cams8), "tile": f"{tuned.tile_w}x{tuned.tile_h}",
                                 "sort": tuned.sort,
                                 "staging": [tuned.render_batch, tuned.render_batch_bwd],
                                 "ms_per_step": ms, "mpix_per_s": pix / 1e6 / (ms * 1e-3),
                                 "status": gs.status()}
-    del gs, p
+    del gs, p, w3
     torch.cuda.empty_cache()
 
     # precision variant: 3M Gaussians, 4 views at 1957x1297, BF16 / FP16 storage
-    g3 = scenes.cluster_gaussians(3_000_000, seed=2024125)
-    f4 = 1150.0 * 1957 / 1557
-    cams4 = [scenes.ring_camera(2 * math.pi * k / 4, 4.0, 1957, 1297, f4) for k in range(4)]
-    tgt4 = torch.as_tensor(np.concatenate(
-        [scenes.target_image(1297, 1957, seed=2024126 + k).reshape(-1) for k in range(4)])).to(dev)
+    w4 = scenes.workload("c4_precision")
+    g3, cams4 = w4.gaussians, w4.cams
+    tgt4 = torch.as_tensor(np.concatenate([t.reshape(-1) for t in w4.targets])).to(dev)
+    pix4 = sum(c.width * c.height for c in cams4)
     for name, dt in (("precision_bf16", torch.bfloat16), ("precision_fp16", torch.float16),
                      ("precision_fp32", None)):
         p = _device_params(g3, dev, dt)
         gs = GraphStep(p, cams4, RasterConfig(), tgt4)
         ms = time_step(gs.replay, steps=max(3, steps // 2))
-        forms[name] = {"gaussians": g3.n, "views": 4, "ms_per_step": ms,
-                       "mpix_per_s": 4 * 1957 * 1297 / 1e6 / (ms * 1e-3), "status": gs.status()}
+        forms[name] = {"gaussians": g3.n, "views": len(cams4), "ms_per_step": ms,
+                       "mpix_per_s": pix4 / 1e6 / (ms * 1e-3), "status": gs.status()}
         del gs, p
         torch.cuda.empty_cache()
-    del g3
+    del g3, w4
 
     # uneven batch: 6 scenes, one camera each, BF16 storage, one launch sequence
-    sizes = [150_000, 400_000, 800_000, 1_200_000, 2_000_000, 3_000_000]
-    res = [(779, 519), (1039, 692), (1297, 865), (1557, 1038), (1751, 1167), (1957, 1297)]
-    scs = [scenes.cluster_gaussians(n, seed=2024130 + k) for k, n in enumerate(sizes)]
-    camsu = [scenes.ring_camera(0.5 * k, 4.0, w, h, 1150.0 * w / 1557) for k, (w, h) in enumerate(res)]
-    tgtu = torch.as_tensor(np.concatenate(
-        [scenes.target_image(h, w, seed=2024140 + k).reshape(-1) for k, (w, h) in enumerate(res)])).to(dev)
-    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
-    ranges = [(int(o), n) for o, n in zip(offs, sizes)]
-    p = _device_params(_concat_scenes(scs), dev, torch.bfloat16)
+    w5 = scenes.workload("c5_uneven")
+    scs = [part[0] for part in w5.parts]
+    sizes = [sc.n for sc in scs]
+    camsu = w5.cams
+    res = [(c.width, c.height) for c in camsu]
+    tgtu = torch.as_tensor(np.concatenate([t.reshape(-1) for t in w5.targets])).to(dev)
+    ranges = w5.view_ranges
+    p = _device_params(w5.gaussians, dev, torch.bfloat16)
     gs = GraphStep(p, camsu, RasterConfig(), tgtu, view_ranges=ranges)
     ms = time_step(gs.replay, steps=max(3, steps // 2))
     pix = sum(w * h for w, h in res)
@@ -641,7 +634,7 @@ def run_forms(dev, g, cams, target, plain_ms, plain_pix, steps=10):
     for k, sc in enumerate(scs):
         pk = _device_params(sc, dev, torch.bfloat16)
         w, h = res[k]
-        tk = torch.as_tensor(scenes.target_image(h, w, seed=2024140 + k)).to(dev).reshape(-1)
+        tk = torch.as_tensor(w5.targets[k]).to(dev).reshape(-1)
         gk = GraphStep(pk, [camsu[k]], RasterConfig(), tk)
         mk = time_step(gk.replay, steps=max(3, steps // 2))
         per_scene.append({"gaussians": sizes[k], "resolution": f"{w}x{h}", "ms_per_step": mk,
@@ -769,7 +762,8 @@ def cpu_baseline_sample(steps=1, crop=None):
     centre ``crop`` (w, h)."""
     from oracle import pipeline
     from paper_2412_20522_gb300 import scenes
-    g, cams, target = scenes.scene_workload()
+    w2 = scenes.workload("c2_scene")
+    g, cams, target = w2.gaussians, w2.cams, w2.targets[0]
     cam, tgt = cams[0], target
     if crop is not None:
         cw, ch = crop
@@ -899,17 +893,17 @@ def oracle_step_and_parity(dev, params, g, cam, target):
 
 
 def c4_crop_workload():
-    """The precision configuration: 3M clustered Gaussians (seed 2024125),
-    view 0 of four ring views at 1957x1297 (f = 1150 * 1957 / 1557), its
-    centre 64x64 crop as a camera, and the crop of view 0's target."""
+    """The precision configuration (c4_precision: 3M clustered Gaussians,
+    four ring views at 1957x1297): the centre crop of its error view as a
+    camera, and the same crop of that view's target."""
     from paper_2412_20522_gb300 import scenes
-    g3 = scenes.cluster_gaussians(3_000_000, seed=2024125)
-    f4 = 1150.0 * 1957 / 1557
-    full = scenes.ring_camera(0.0, 4.0, 1957, 1297, f4)
-    cam = _crop_camera(full, 64, 64)
-    x0, y0 = (full.width - 64) // 2, (full.height - 64) // 2
-    tgt = scenes.target_image(1297, 1957, seed=2024126)[:, y0:y0 + 64, x0:x0 + 64].copy()
-    return g3, cam, tgt
+    w4 = scenes.workload("c4_precision")
+    v, n = w4.spec["error_crop"]["view"], w4.spec["error_crop"]["size"]
+    full = w4.cams[v]
+    cam = _crop_camera(full, n, n)
+    x0, y0 = (full.width - n) // 2, (full.height - n) // 2
+    tgt = w4.targets[v][:, y0:y0 + n, x0:x0 + n].copy()
+    return w4.gaussians, cam, tgt
 
 
 def precision_c4_error(dev):

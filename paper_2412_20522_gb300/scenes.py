@@ -20,7 +20,9 @@ Conventions (shared with the C ABI, ``include/maskgs.h``):
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -197,3 +199,122 @@ def converged_mask_logits(n, absent_fraction=0.624, seed=SCENE_SEED + 7) -> np.n
     out = np.zeros((n, 2), np.float32)
     out[:, 0] = d.astype(np.float32)
     return out
+
+
+# --- workload definitions (workloads.json) and scene files ------------------
+
+WORKLOADS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
+
+
+@dataclass
+class Workload:
+    """A named workload: every scene's Gaussians concatenated, the cameras,
+    one target image per camera, each camera's (first, count) range of the
+    concatenation (None: every camera sees all of it), the storage types the
+    workload is measured with, and per scene (Gaussians, cameras, targets)."""
+    name: str
+    gaussians: Gaussians
+    cams: list
+    targets: list
+    view_ranges: list | None
+    storage: tuple
+    parts: list
+    spec: dict
+
+
+def load_workloads(path: str | None = None) -> dict:
+    with open(path or WORKLOADS_FILE) as fh:
+        return json.load(fh)
+
+
+def concat_gaussians(gs) -> Gaussians:
+    """One Gaussians holding the given ones in order (a scene batch)."""
+    cat = {k: np.concatenate([getattr(s, k) for s in gs]) for k in
+           ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")}
+    return Gaussians(**cat, sh_degree=gs[0].sh_degree)
+
+
+def _scene_of(spec: dict) -> Gaussians:
+    kind = spec["distribution"]
+    if kind == "uniform":
+        return uniform_gaussians(spec["gaussians"], seed=spec["seed"])
+    if kind == "clusters":
+        return cluster_gaussians(spec["gaussians"], seed=spec["seed"])
+    raise ValueError(f"unknown scene distribution {kind!r}")
+
+
+def _cameras_of(spec: dict, n_scenes: int) -> list:
+    kind = spec["kind"]
+    if kind == "look_at":
+        w, h = spec["width"], spec["height"]
+        f = (w / 2.0) / math.tan(math.radians(spec["fov_deg"] / 2.0))
+        return [look_at_camera(tuple(spec["eye"]), tuple(spec["target"]), w, h, f)]
+    if kind == "ring":
+        w, h, k_n = spec["width"], spec["height"], spec["count"]
+        f = spec["focal"] * w / spec["focal_width"]
+        return [ring_camera(2 * math.pi * k / k_n, spec["radius"], w, h, f) for k in range(k_n)]
+    if kind == "ring_per_scene":
+        res = spec["resolutions"]
+        if len(res) != n_scenes:
+            raise ValueError("one resolution per scene")
+        return [ring_camera(spec["theta_step"] * k, spec["radius"], w, h,
+                            spec["focal"] * w / spec["focal_width"])
+                for k, (w, h) in enumerate(res)]
+    raise ValueError(f"unknown camera kind {kind!r}")
+
+
+def workload(name: str, path: str | None = None) -> Workload:
+    """Build the named workload of workloads.json (c1_tiny ... c5_uneven)."""
+    spec = load_workloads(path)[name]
+    scs = [_scene_of(s) for s in spec["scenes"]]
+    cams = _cameras_of(spec["cameras"], len(scs))
+    seeds = spec["target_seeds"]
+    if len(seeds) != len(cams):
+        raise ValueError("one target seed per camera")
+    targets = [target_image(c.height, c.width, seed=s) for c, s in zip(cams, seeds)]
+    if len(scs) == 1:
+        g, ranges, parts = scs[0], None, [(scs[0], cams, targets)]
+    else:
+        if len(cams) != len(scs):
+            raise ValueError("a scene batch has one camera per scene")
+        g = concat_gaussians(scs)
+        offs = np.concatenate([[0], np.cumsum([s.n for s in scs])[:-1]])
+        ranges = [(int(o), s.n) for o, s in zip(offs, scs)]
+        parts = [(s, [c], [t]) for s, c, t in zip(scs, cams, targets)]
+    return Workload(name, g, cams, targets, ranges, tuple(spec["storage"]), parts, spec)
+
+
+def save_npz(path: str, g: Gaussians, cams=(), targets=()) -> None:
+    """Write a scene (and optionally its cameras and target images) to one
+    .npz file; ``load_npz`` gives back bit-identical arrays."""
+    arrays = {k: getattr(g, k) for k in
+              ("means", "log_scales", "quats", "opacity_logit", "sh", "mask_logits")}
+    arrays["sh_degree"] = np.int64(g.sh_degree)
+    for i, c in enumerate(cams):
+        arrays[f"cam{i}_intrinsics"] = np.array([c.width, c.height, c.fx, c.fy, c.cx, c.cy,
+                                                 c.near], dtype=np.float64)
+        arrays[f"cam{i}_viewmat"] = c.viewmat
+        arrays[f"cam{i}_pos"] = c.cam_pos
+    for i, t in enumerate(targets):
+        arrays[f"target{i}"] = t
+    np.savez(path, **arrays)
+
+
+def load_npz(path: str):
+    """(Gaussians, cameras, targets) from a file written by ``save_npz``."""
+    with np.load(path) as z:
+        g = Gaussians(*(z[k].copy() for k in ("means", "log_scales", "quats", "opacity_logit",
+                                               "sh", "mask_logits")),
+                      sh_degree=int(z["sh_degree"]))
+        cams, targets = [], []
+        i = 0
+        while f"cam{i}_intrinsics" in z:
+            w, h, fx, fy, cx, cy, near = z[f"cam{i}_intrinsics"].tolist()
+            cams.append(Camera(int(w), int(h), fx, fy, cx, cy, z[f"cam{i}_viewmat"].copy(),
+                               z[f"cam{i}_pos"].copy(), near))
+            i += 1
+        i = 0
+        while f"target{i}" in z:
+            targets.append(z[f"target{i}"].copy())
+            i += 1
+    return g, cams, targets
