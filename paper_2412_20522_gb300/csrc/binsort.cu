@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order, int64_t n,
             uint32_t *__restrict__ out, uint64_t *d_total, uint64_t capacity, ScanWS *ws,
             int64_t n_parts, mg_status_word *st, uint32_t *__restrict__ owner_hint) {
+    grid_dependency_wait();
     __shared__ uint64_t sm_warp[33];
     __shared__ uint64_t sm_prefix;
     __shared__ int64_t sm_part;
@@ -146,6 +147,7 @@ duplicate_kernel(const float4 *__restrict__ bin_record, const uint32_t *__restri
                  const uint32_t *__restrict__ offsets, int64_t n_records, const uint64_t *__restrict__ d_num_instances,
                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t capacity,
                  int tile_w, int tile_h, bool filter, mg_status_word *st) {
+    grid_dependency_wait();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -270,6 +272,7 @@ template <typename K>
 __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t *d_n,
                                       uint64_t capacity, int begin_bit, int passes, SortWS *ws,
                                       int64_t max_parts, bool drop) {
+    grid_dependency_wait();
     __shared__ uint32_t h[kMaxPasses][256];
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -313,6 +316,7 @@ __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t
 }
 
 __global__ void sort_offsets_kernel(SortWS *ws) {
+    grid_dependency_wait();
     // one block per pass, 256 threads: exclusive scan of the digit counts
     __shared__ uint64_t sm_warp[33];
     const int p = blockIdx.x;
@@ -330,6 +334,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint64_t *d_n,
                 uint64_t capacity, int pass, int shift, SortWS *ws, int64_t max_parts,
                 mg_status_word *st) {
+    grid_dependency_wait();
     // staged keys and values of the partition: dynamic shared memory (above
     // the 48 KB a kernel may declare statically)
     extern __shared__ __align__(16) unsigned char sort_stage[];
@@ -452,6 +457,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
 
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint64_t *d_n,
                               uint64_t capacity, uint32_t *__restrict__ ranges, int64_t n_tiles) {
+    grid_dependency_wait();
     const int64_t n = sort_count(d_n, capacity);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
@@ -552,10 +558,10 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     const int64_t hblocks = (int64_t)((capacity + 4095) / 4096);
     const int64_t hcap = (int64_t)sms * 2;
     const K *k0 = src_keys != nullptr ? src_keys : keys;
-    sort_histogram_kernel<K><<<(unsigned)(hblocks < hcap ? (hblocks > 0 ? hblocks : 1) : hcap),
-                               512, 0, s>>>(k0, d_n, capacity, begin_bit, passes, ws, max_parts,
-                                            drop);
-    sort_offsets_kernel<<<passes, 256, 0, s>>>(ws);
+    launch_pdl(sort_histogram_kernel<K>,
+        dim3((unsigned)(hblocks < hcap ? (hblocks > 0 ? hblocks : 1) : hcap)), dim3(512), 0, s, k0,
+        d_n, capacity, begin_bit, passes, ws, max_parts, drop);
+    launch_pdl(sort_offsets_kernel, dim3(passes), dim3(256), 0, s, ws);
     const size_t stage_bytes = (sizeof(K) + sizeof(uint32_t)) * (size_t)kSortPart;
     if (sort_smem_optin<K>(stage_bytes) != MG_OK) return MG_ERR_CUDA;
     int per_sm = 1;
@@ -569,14 +575,17 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
         // after a dropping first pass the later ones sort the kept elements
         const uint64_t *np_ = (drop && p > 0) ? &ws->n_kept : d_n;
         if (p == 0 && src_keys != nullptr)
-            onesweep_kernel<K, false, true><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
-                src_keys, nullptr, kout, vout, np_, capacity, p, begin_bit, ws, max_parts, st);
+            launch_pdl(onesweep_kernel<K, false, true>, dim3((unsigned)grid), dim3(kSortThreads),
+                stage_bytes, s, src_keys, nullptr, kout, vout, np_, capacity, p, begin_bit, ws,
+                max_parts, st);
         else if (drop && p == 0)
-            onesweep_kernel<K, true><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
-                kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
+            launch_pdl(onesweep_kernel<K, true>, dim3((unsigned)grid), dim3(kSortThreads),
+                stage_bytes, s, kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws,
+                max_parts, st);
         else
-            onesweep_kernel<K, false><<<(unsigned)grid, kSortThreads, stage_bytes, s>>>(
-                kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws, max_parts, st);
+            launch_pdl(onesweep_kernel<K, false>, dim3((unsigned)grid), dim3(kSortThreads),
+                stage_bytes, s, kin, vin, kout, vout, np_, capacity, p, begin_bit + 8 * p, ws,
+                max_parts, st);
         K *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
@@ -1071,13 +1080,13 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
             return MG_ERR_CUDA;
         return MG_OK;
     }
-    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(splats->tiles_touched, order, R, offsets,
-                                                         d_num_instances, capacity, ws, parts,
-                                                         d_status, capacity > 0 ? vals : nullptr);
+    launch_pdl(scan_kernel, dim3((unsigned)parts), dim3(kScanThreads), 0, s, splats->tiles_touched,
+        order, R, offsets, d_num_instances, capacity, ws, parts, d_status,
+        capacity > 0 ? vals : nullptr);
     if (capacity > 0)
-        duplicate_kernel<<<dup_blocks(capacity), 256, 0, s>>>(
-            reinterpret_cast<const float4 *>(splats->bin_record), order,
-            offsets, R, d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
+        launch_pdl(duplicate_kernel, dim3(dup_blocks(capacity)), dim3(256), 0, s,
+            reinterpret_cast<const float4 *>(splats->bin_record), order, offsets, R,
+            d_num_instances, keys, vals, capacity, cfg->tile_w, cfg->tile_h,
             cfg->bin_mode == MG_BIN_FILTERED, d_status);
     return mg_host::launch_status();
 }
@@ -1115,7 +1124,7 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
             cudaSuccess)
         return MG_ERR_CUDA;
     const int64_t rblocks = (int64_t)((capacity + 1023) / 1024);
-    ranges_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), 256, 0, s>>>(
+    launch_pdl(ranges_kernel, dim3((unsigned)(rblocks < 65535 ? rblocks : 65535)), dim3(256), 0, s,
         in_alt ? keys_alt : keys, &ws->n_kept, capacity, ranges, n_tiles_total);
     return mg_host::launch_status();
 }

@@ -48,6 +48,36 @@ __device__ __forceinline__ void raise_status(mg_status_word *w, int32_t st, int3
 #define MG_IN_BOUNDS(cond, st, detail, value) true
 #endif
 
+// Programmatic dependent launch.  The step's kernels are launched with
+// launch_pdl, which lets the next kernel on the stream be scheduled while
+// the previous one drains; each of them first waits in
+// grid_dependency_wait until the previous kernel has completed and its
+// writes are visible (for a kernel launched the ordinary way, or after a
+// memset or copy, the wait returns at once and stream order holds as usual).
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // every CTA of this kernel has started once all of them get here: the
+    // next kernel may then be scheduled onto the SMs this one frees (its
+    // own wait still holds it until this kernel has completed)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // single-pass scans (decoupled look-back) ------------------------------------
 // A partition's 64-bit status word: flag in the top two bits (1 = aggregate
 // only, 2 = inclusive prefix), value below.

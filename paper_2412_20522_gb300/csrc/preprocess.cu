@@ -294,6 +294,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 template <int DEG, typename ST>
 __global__ void __launch_bounds__(kPreThreads, 8)
 preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out) {
+    grid_dependency_wait();
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     const bool active = i < g.n;
 
@@ -578,6 +579,7 @@ template <int DEG, typename ST>
 __global__ void __launch_bounds__(kPreThreads, 5)
 preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats sp,
                            const float *__restrict__ grad2d, mg_param_grads out) {
+    grid_dependency_wait();
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int ROW = 3 * K;
     constexpr int S_ = StageStride<ROW>::value;
@@ -788,11 +790,14 @@ static void launch_preprocess(int32_t dtype, dim3 grid, cudaStream_t s, const Vi
                               const mg_gaussians &g, const mg_raster_cfg &cfg,
                               const mg_splats &out) {
     if (dtype == MG_DTYPE_BF16)
-        preprocess_kernel<DEG, __nv_bfloat16><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, out);
+        launch_pdl(preprocess_kernel<DEG, __nv_bfloat16>, dim3(grid), dim3(kPreThreads), 0, s, vt,
+            g, cfg, out);
     else if (dtype == MG_DTYPE_F16)
-        preprocess_kernel<DEG, __half><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, out);
+        launch_pdl(preprocess_kernel<DEG, __half>, dim3(grid), dim3(kPreThreads), 0, s, vt, g, cfg,
+            out);
     else
-        preprocess_kernel<DEG, float><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, out);
+        launch_pdl(preprocess_kernel<DEG, float>, dim3(grid), dim3(kPreThreads), 0, s, vt, g, cfg,
+            out);
 }
 
 template <int DEG>
@@ -801,14 +806,14 @@ static void launch_preprocess_backward(int32_t dtype, dim3 grid, cudaStream_t s,
                                        const mg_raster_cfg &cfg, const mg_splats &sp,
                                        const float *grad2d, const mg_param_grads &out) {
     if (dtype == MG_DTYPE_BF16)
-        preprocess_backward_kernel<DEG, __nv_bfloat16><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, sp,
-                                                                                   grad2d, out);
+        launch_pdl(preprocess_backward_kernel<DEG, __nv_bfloat16>, dim3(grid), dim3(kPreThreads), 0,
+            s, vt, g, cfg, sp, grad2d, out);
     else if (dtype == MG_DTYPE_F16)
-        preprocess_backward_kernel<DEG, __half><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, sp, grad2d,
-                                                                            out);
+        launch_pdl(preprocess_backward_kernel<DEG, __half>, dim3(grid), dim3(kPreThreads), 0, s, vt,
+            g, cfg, sp, grad2d, out);
     else
-        preprocess_backward_kernel<DEG, float><<<grid, kPreThreads, 0, s>>>(vt, g, cfg, sp, grad2d,
-                                                                           out);
+        launch_pdl(preprocess_backward_kernel<DEG, float>, dim3(grid), dim3(kPreThreads), 0, s, vt,
+            g, cfg, sp, grad2d, out);
 }
 
 static mg_status check_views(const mg_gaussians *g, const mg_view *views, int32_t n_views,
@@ -905,6 +910,7 @@ struct SceneList {
 
 __global__ void mask_loss_kernel(SceneList sl, const uint32_t *__restrict__ mask_count,
                                  float lambda_m, int32_t kind, float *loss) {
+    grid_dependency_wait();
     if (threadIdx.x != 0) return;
     double acc = 0.0;
     for (int k = 0; k < sl.n; ++k) {
@@ -936,7 +942,7 @@ extern "C" mg_status mg_mask_loss(const mg_splats *splats, const mg_view *views,
         ++sl.n;
     }
     if (sl.n == 0 || cfg->lambda_m == 0.0f) return MG_OK;
-    mask_loss_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(sl, splats->mask_count, cfg->lambda_m,
-                                                        cfg->mask_loss, loss);
+    launch_pdl(mask_loss_kernel, dim3(1), dim3(32), 0, (cudaStream_t)stream, sl, splats->mask_count,
+        cfg->lambda_m, cfg->mask_loss, loss);
     return mg_host::launch_status();
 }

@@ -193,6 +193,7 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count,
                       const float *__restrict__ target = nullptr,
                       float *__restrict__ dL_dimage = nullptr, float *loss = nullptr) {
+    grid_dependency_wait();
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
     __shared__ uint8_t sM[BATCH];
     __shared__ unsigned long long s_frags[4];
@@ -435,6 +436,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                        float bg0, float bg1, float bg2, const float *__restrict__ final_T,
                        const uint32_t *__restrict__ n_contrib, const float *__restrict__ dL_dimage,
                        float *__restrict__ grad2d, unsigned long long *counters) {
+    grid_dependency_wait();
     unsigned long long cnt_it = 0, cnt_m = 0, cnt_cu = 0, cnt_cm = 0, cnt_pix = 0, cnt_b = 0;
     __shared__ float4 sA[BATCHB], sB[BATCHB], sC[BATCHB];
     __shared__ uint32_t sR[BATCHB];
@@ -693,6 +695,7 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
 __global__ void l1_loss_grad_kernel(ViewTable vt, const float *__restrict__ image,
                                     const float *__restrict__ target, float *__restrict__ grad,
                                     float *loss) {
+    grid_dependency_wait();
     const int v = blockIdx.y;
     const int64_t n = 3 * (vt.pix_off[v + 1] - vt.pix_off[v]);
     const int64_t o = 3 * vt.pix_off[v];
@@ -771,15 +774,15 @@ extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorte
     if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (batch == 128)
-        render_forward_kernel<false, true, true, 128>
-            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-                vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
-                image, final_T, n_contrib, nullptr, target, dL_dimage, loss);
+        launch_pdl(render_forward_kernel<false, true, true, 128>, dim3((unsigned)tiles),
+            dim3(kRenderThreads), 0, (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order,
+            cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T, n_contrib, nullptr, target,
+            dL_dimage, loss);
     else
-        render_forward_kernel<false, true, true>
-            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-                vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
-                image, final_T, n_contrib, nullptr, target, dL_dimage, loss);
+        launch_pdl(render_forward_kernel<false, true, true>, dim3((unsigned)tiles),
+            dim3(kRenderThreads), 0, (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order,
+            cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T, n_contrib, nullptr, target,
+            dL_dimage, loss);
     return mg_host::launch_status();
 }
 
@@ -800,18 +803,19 @@ extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_v
     if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (frag_count != nullptr)      // the counting variant: default staging depth
-        render_forward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
-            final_T, n_contrib, reinterpret_cast<unsigned long long *>(frag_count));
+        launch_pdl(render_forward_kernel<true>, dim3((unsigned)tiles), dim3(kRenderThreads), 0,
+            (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1],
+            cfg->bg[2], image, final_T, n_contrib,
+            reinterpret_cast<unsigned long long *>(frag_count), nullptr, nullptr, nullptr);
     else if (batch == 128)
-        render_forward_kernel<false, true, false, 128>
-            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-                vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
-                image, final_T, n_contrib, nullptr);
+        launch_pdl(render_forward_kernel<false, true, false, 128>, dim3((unsigned)tiles),
+            dim3(kRenderThreads), 0, (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order,
+            cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T, n_contrib, nullptr, nullptr,
+            nullptr, nullptr);
     else
-        render_forward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image,
-            final_T, n_contrib, nullptr);
+        launch_pdl(render_forward_kernel<false>, dim3((unsigned)tiles), dim3(kRenderThreads), 0,
+            (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1],
+            cfg->bg[2], image, final_T, n_contrib, nullptr, nullptr, nullptr, nullptr);
     return mg_host::launch_status();
 }
 
@@ -831,15 +835,16 @@ extern "C" mg_status mg_render_inference(const mg_splats *splats, const uint32_t
     int batch;
     if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     if (batch == 128)
-        render_forward_kernel<false, false, false, 128>
-            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-                vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges,
-                tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
+        launch_pdl(render_forward_kernel<false, false, false, 128>, dim3((unsigned)tiles),
+            dim3(kRenderThreads), 0, (cudaStream_t)stream, vt,
+            reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, tile_order,
+            cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr, nullptr, nullptr,
+            nullptr);
     else
-        render_forward_kernel<false, false>
-            <<<(unsigned)tiles, kRenderThreads, 0, (cudaStream_t)stream>>>(
-                vt, reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges,
-                tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr);
+        launch_pdl(render_forward_kernel<false, false>, dim3((unsigned)tiles), dim3(kRenderThreads),
+            0, (cudaStream_t)stream, vt, reinterpret_cast<const float4 *>(splats->record),
+            sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr);
     return mg_host::launch_status();
 }
 
@@ -869,15 +874,15 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
         return MG_ERR_CUDA;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (counters != nullptr)
-        render_backward_kernel<true><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
+        launch_pdl(render_backward_kernel<true>, dim3((unsigned)tiles), dim3(kRenderThreads), 0, s,
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
             n_contrib, dL_dimage, grad2d, reinterpret_cast<unsigned long long *>(counters));
     else if (batch == 64)
-        render_backward_kernel<false, 64><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
-            vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
-            n_contrib, dL_dimage, grad2d, nullptr);
+        launch_pdl(render_backward_kernel<false, 64>, dim3((unsigned)tiles), dim3(kRenderThreads),
+            0, s, vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2],
+            final_T, n_contrib, dL_dimage, grad2d, nullptr);
     else
-        render_backward_kernel<false><<<(unsigned)tiles, kRenderThreads, 0, s>>>(
+        launch_pdl(render_backward_kernel<false>, dim3((unsigned)tiles), dim3(kRenderThreads), 0, s,
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
             n_contrib, dL_dimage, grad2d, nullptr);
     return mg_host::launch_status();
@@ -900,8 +905,8 @@ extern "C" mg_status mg_l1_loss_grad(const float *image, const float *target,
     for (int v = 0; v < n_views; ++v) most = max(most, 3 * (vt.pix_off[v + 1] - vt.pix_off[v]));
     const int64_t bx = (most + 1023) / 1024;
     const dim3 grid((unsigned)(bx < 2048 ? (bx > 0 ? bx : 1) : 2048), (unsigned)n_views);
-    l1_loss_grad_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(vt, image, target, dL_dimage,
-                                                               loss);
+    launch_pdl(l1_loss_grad_kernel, dim3(grid), dim3(256), 0, (cudaStream_t)stream, vt, image,
+        target, dL_dimage, loss);
     return mg_host::launch_status();
 }
 
@@ -924,6 +929,7 @@ __device__ __forceinline__ int length_bucket(uint32_t c) {
 
 __global__ void __launch_bounds__(1024)
 tile_order_kernel(const uint32_t *__restrict__ ranges, int64_t n, uint32_t *__restrict__ order) {
+    grid_dependency_wait();
     __shared__ uint32_t hist[kOrderBuckets];
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) hist[b] = 0u;
     __syncthreads();
@@ -953,6 +959,7 @@ extern "C" mg_status mg_tile_order(const uint32_t *ranges, int64_t n_tiles_total
     if (ranges == nullptr || tile_order == nullptr || n_tiles_total <= 0 ||
         n_tiles_total >= (int64_t(1) << 31) || (reinterpret_cast<uintptr_t>(ranges) & 7u) != 0)
         return MG_ERR_INVALID_ARG;
-    tile_order_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(ranges, n_tiles_total, tile_order);
+    launch_pdl(tile_order_kernel, dim3(1), dim3(1024), 0, (cudaStream_t)stream, ranges,
+        n_tiles_total, tile_order);
     return mg_host::launch_status();
 }
