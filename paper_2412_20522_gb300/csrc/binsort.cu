@@ -455,9 +455,13 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
     }
 }
 
+// Also copies the sorted count to d_num_sorted (nullable), so no copy node
+// sits between the last sort pass and this kernel.
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint64_t *d_n,
-                              uint64_t capacity, uint32_t *__restrict__ ranges, int64_t n_tiles) {
+                              uint64_t capacity, uint32_t *__restrict__ ranges, int64_t n_tiles,
+                              uint64_t *d_num_sorted) {
     grid_dependency_wait();
+    if (d_num_sorted != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *d_num_sorted = *d_n;
     const int64_t n = sort_count(d_n, capacity);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
@@ -1119,13 +1123,9 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     if (st != MG_OK) return st;
     *result_in_alt = in_alt ? 1 : 0;
     if (capacity == 0) return mg_host::launch_status();
-    if (d_num_sorted != nullptr &&
-        cudaMemcpyAsync(d_num_sorted, &ws->n_kept, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s) !=
-            cudaSuccess)
-        return MG_ERR_CUDA;
     const int64_t rblocks = (int64_t)((capacity + 1023) / 1024);
     launch_pdl(ranges_kernel, dim3((unsigned)(rblocks < 65535 ? rblocks : 65535)), dim3(256), 0, s,
-        in_alt ? keys_alt : keys, &ws->n_kept, capacity, ranges, n_tiles_total);
+        in_alt ? keys_alt : keys, &ws->n_kept, capacity, ranges, n_tiles_total, d_num_sorted);
     return mg_host::launch_status();
 }
 

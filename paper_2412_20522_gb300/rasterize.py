@@ -221,6 +221,10 @@ class Rasterizer:
         stream = self._stream()
         ev = _Events(stage_events, self.nvtx)
         self.status.zero_()
+        if l1_target is not None and not count_fragments:
+            # the fused render adds to the loss: zeroed here, ahead of the
+            # kernels, so that nothing but kernels runs between them
+            self._get("loss", 1, torch.float32).zero_()
         splats = self._splats(R, n, V)
         ev.begin("preprocess")
         abi.mg_preprocess(g, views, V, ccfg, splats, self.status, stream)
@@ -323,8 +327,7 @@ class Rasterizer:
         fused = l1_target is not None and not count_fragments
         if fused:
             dimg = self._get("dL_dimage", 3 * pix, torch.float32)
-            loss = self._get("loss", 1, torch.float32)
-            loss.zero_()
+            loss = self._buf["loss"][:1]           # zeroed before the preprocess
         ev.begin("render")
         if fused:
             abi.mg_render_l1(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image,
