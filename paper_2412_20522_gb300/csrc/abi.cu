@@ -4,6 +4,25 @@
 
 #include "internal.cuh"
 
+namespace mg {
+
+// words [0, n) of p set to 0: 128-bit stores over the 16-byte aligned body,
+// 32-bit ones at the ends
+__global__ void zero_kernel(uint32_t *__restrict__ p, int64_t n) {
+    grid_dependency_wait();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    int64_t head = (int64_t)(((16u - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) / 4u);
+    if (head > n) head = n;
+    const int64_t n4 = (n - head) / 4;
+    for (int64_t i = t; i < head; i += nt) p[i] = 0u;
+    uint4 *q = reinterpret_cast<uint4 *>(p + head);
+    for (int64_t i = t; i < n4; i += nt) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = head + 4 * n4 + t; i < n; i += nt) p[i] = 0u;
+}
+
+}  // namespace mg
+
 namespace mg_host {
 
 static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -42,6 +61,18 @@ mg_status build_view_table(const mg_view *views, int32_t n_views, const mg_raste
 
 mg_status launch_status(void) {
     return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+mg_status zero_async(void *p, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return MG_OK;
+    if (p == nullptr || (bytes & 3u) != 0 || (reinterpret_cast<uintptr_t>(p) & 3u) != 0)
+        return MG_ERR_INVALID_ARG;
+    const int64_t words = (int64_t)(bytes / 4);
+    const int64_t blocks = (words / 4 + 255) / 256;
+    const int64_t cap = 4 * 152;
+    mg::launch_pdl(mg::zero_kernel, dim3((unsigned)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap))),
+                   dim3(256), 0, s, static_cast<uint32_t *>(p), words);
+    return launch_status();
 }
 
 }  // namespace mg_host

@@ -553,8 +553,7 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
                             bool drop, SortWS *ws, mg_status_word *st, cudaStream_t s,
                             bool *in_alt, const K *src_keys = nullptr) {
     *in_alt = (passes & 1) != 0;
-    if (cudaMemsetAsync(&ws->hist[0][0], 0, sizeof(ws->hist) + sizeof(ws->counter), s) !=
-        cudaSuccess)
+    if (mg_host::zero_async(&ws->hist[0][0], sizeof(ws->hist) + sizeof(ws->counter), s) != MG_OK)
         return MG_ERR_CUDA;
     if (capacity == 0 || passes == 0) return MG_OK;
     const int sms = sm_count();
@@ -1076,8 +1075,8 @@ extern "C" mg_status mg_bin(const mg_splats *splats, const mg_view *views, int32
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t parts = (R + kScanPart - 1) / kScanPart;
     ScanWS *ws = reinterpret_cast<ScanWS *>(workspace);
-    if (cudaMemsetAsync(ws, 0, sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(parts + 1), s) !=
-        cudaSuccess)
+    if (mg_host::zero_async(ws, sizeof(ScanWS) + sizeof(uint64_t) * (size_t)(parts + 1), s) !=
+        MG_OK)
         return MG_ERR_CUDA;
     if (R == 0) {
         if (cudaMemsetAsync(d_num_instances, 0, sizeof(uint64_t), s) != cudaSuccess)
@@ -1113,8 +1112,7 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     const int passes = (key_bits + 7) / 8;
     cudaStream_t s = (cudaStream_t)stream;
     SortWS *ws = reinterpret_cast<SortWS *>(workspace);
-    if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) !=
-        cudaSuccess)
+    if (mg_host::zero_async(ranges, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) != MG_OK)
         return MG_ERR_CUDA;
     bool in_alt = false;
     // filtered instances (key kDroppedKey) leave in the first pass

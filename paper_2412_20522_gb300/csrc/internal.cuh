@@ -462,4 +462,8 @@ namespace mg_host {
 mg_status build_view_table(const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
                            mg::ViewTable *vt);
 mg_status launch_status(void);
+// Zero `bytes` (a multiple of 4, at a 4-byte aligned address) on the stream
+// with a kernel launched like the step's kernels (launch_pdl), in place of a
+// memset node between two of them.
+mg_status zero_async(void *p, size_t bytes, cudaStream_t s);
 }

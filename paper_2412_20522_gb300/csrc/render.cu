@@ -869,8 +869,8 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
     int batch;
     if (!bwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (R > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * MG_GRAD2D_FLOATS * (size_t)R, s) !=
-                     cudaSuccess)
+    if (R > 0 && mg_host::zero_async(grad2d, sizeof(float) * MG_GRAD2D_FLOATS * (size_t)R, s) !=
+                     MG_OK)
         return MG_ERR_CUDA;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (counters != nullptr)
