@@ -301,11 +301,12 @@ class Rasterizer:
             abi.mg_tile_order(ranges_buf, tiles, tile_order, stream)
         image = self._get("image", 3 * pix, torch.float32)
         # kernels of ours per forward: preprocess (with the depth keys); with
-        # the radix sort: histogram, offsets and 4 digit passes of the depth
-        # order, scan, duplicate, histogram, offsets, one pass per tile digit,
-        # ranges; with the bucket sort: scan, duplicate, count, scan, scatter,
-        # order; then the tile order and the render
-        sort_launches = 4 if bucket else 6 + 2 + 3 + (key_bits + 7) // 8
+        # the radix sort: a workspace reset, histogram, offsets and 4 digit
+        # passes of the depth order, a reset, scan, duplicate, resets of the
+        # ranges and the workspace, histogram, offsets, one pass per tile
+        # digit, ranges; with the bucket sort: a reset, scan, duplicate,
+        # count, scan, scatter, order; then the tile order and the render
+        sort_launches = 5 if bucket else 7 + 3 + 5 + (key_bits + 7) // 8
         self._fwd_launches = 1 + sort_launches + (2 if bucket else 0) + 1 + \
             (tile_order is not None)
         self._sort_mode = cfg.sort
@@ -352,7 +353,7 @@ class Rasterizer:
         return self._fwd_launches
 
     def backward_launches(self):
-        return 2
+        return 3                                  # 2D-gradient reset, render, preprocess
 
     def forward_l1(self, params: dict, cams, cfg: RasterConfig, target, view_ranges=None,
                    check=True, count_fragments=False, stage_events=None):
