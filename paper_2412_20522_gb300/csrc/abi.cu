@@ -52,6 +52,12 @@ mg_status build_view_table(const mg_view *views, int32_t n_views, const mg_raste
         vt->g_cnt[v] = w.gaussian_count;
         vt->gx[v] = (w.cam.width + cfg->tile_w - 1) / cfg->tile_w;
         vt->gy[v] = (w.cam.height + cfg->tile_h - 1) / cfg->tile_h;
+        // FP32 operations, each correctly rounded (no product is added, so
+        // nothing can be contracted): the values the device would compute
+        const float tanx = ((float)w.cam.width * 0.5f) / w.cam.fx;
+        const float tany = ((float)w.cam.height * 0.5f) / w.cam.fy;
+        vt->limx[v] = 1.3f * tanx;
+        vt->limy[v] = 1.3f * tany;
         vt->rec_off[v + 1] = vt->rec_off[v] + w.gaussian_count;
         vt->tile_off[v + 1] = vt->tile_off[v] + (int64_t)vt->gx[v] * vt->gy[v];
         vt->pix_off[v + 1] = vt->pix_off[v] + (int64_t)w.cam.width * w.cam.height;

@@ -26,6 +26,9 @@ struct ViewTable {
     int64_t tile_off[MG_MAX_VIEWS + 1];  // first global tile of the view
     int64_t pix_off[MG_MAX_VIEWS + 1];   // first pixel of the view
     int32_t gx[MG_MAX_VIEWS], gy[MG_MAX_VIEWS];
+    // clamp limits of the Jacobian's point, 1.3 tan(fov/2) = 1.3 ((W/2) / fx)
+    // (and the same in y), each FP32 operation correctly rounded on the host
+    float limx[MG_MAX_VIEWS], limy[MG_MAX_VIEWS];
 };
 
 // device status word helpers -------------------------------------------------
@@ -297,15 +300,22 @@ __device__ __forceinline__ float dot3(float a, float b, float c, float d, float 
     return ad(ad(ml(a, b), ml(c, d)), ml(e, f));
 }
 
+// 2^-k for v = 2^k (the tile sizes): x / v correctly rounded equals x * 2^-k
+// correctly rounded (both round the same real number), so the divisions by a
+// tile size below are exact multiplications.
+__device__ __forceinline__ float inv_pow2(int v) {
+    return __int_as_float((127 - (31 - __clz(v))) << 23);
+}
+
 // Rectangle of tiles overlapped by the square [p - r, p + r] (inclusive),
-// clamped to the grid; false when empty.  Same operations in preprocess and
-// in key duplication, so both see the same rectangle.
+// clamped to the grid; false when empty.
 __device__ __forceinline__ bool tile_rect(float px, float py, float rf, int tw, int th, int gx,
                                           int gy, int &x0, int &x1, int &y0, int &y1) {
-    const float fx0 = fmaxf(floorf(dv(sb(px, rf), (float)tw)), 0.0f);
-    const float fx1 = fminf(floorf(dv(ad(px, rf), (float)tw)), (float)(gx - 1));
-    const float fy0 = fmaxf(floorf(dv(sb(py, rf), (float)th)), 0.0f);
-    const float fy1 = fminf(floorf(dv(ad(py, rf), (float)th)), (float)(gy - 1));
+    const float itw = inv_pow2(tw), ith = inv_pow2(th);
+    const float fx0 = fmaxf(floorf(ml(sb(px, rf), itw)), 0.0f);
+    const float fx1 = fminf(floorf(ml(ad(px, rf), itw)), (float)(gx - 1));
+    const float fy0 = fmaxf(floorf(ml(sb(py, rf), ith)), 0.0f);
+    const float fy1 = fminf(floorf(ml(ad(py, rf), ith)), (float)(gy - 1));
     if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
     x0 = (int)fx0; x1 = (int)fx1; y0 = (int)fy0; y1 = (int)fy1;
     return true;
@@ -437,10 +447,11 @@ __device__ __forceinline__ bool candidate_rect(float px, float py, float a, floa
         __fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(T, a), detk)), kCandGrow), kCandMargin);
     const float hy = __fadd_rn(
         __fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(T, c), detk)), kCandGrow), kCandMargin);
-    const float fx0 = fmaxf((float)x0, floorf(__fdiv_rn(__fsub_rn(px, hx), (float)tw)));
-    const float fx1 = fminf((float)x1, floorf(__fdiv_rn(__fadd_rn(px, hx), (float)tw)));
-    const float fy0 = fmaxf((float)y0, floorf(__fdiv_rn(__fsub_rn(py, hy), (float)th)));
-    const float fy1 = fminf((float)y1, floorf(__fdiv_rn(__fadd_rn(py, hy), (float)th)));
+    const float itw = inv_pow2(tw), ith = inv_pow2(th);
+    const float fx0 = fmaxf((float)x0, floorf(__fmul_rn(__fsub_rn(px, hx), itw)));
+    const float fx1 = fminf((float)x1, floorf(__fmul_rn(__fadd_rn(px, hx), itw)));
+    const float fy0 = fmaxf((float)y0, floorf(__fmul_rn(__fsub_rn(py, hy), ith)));
+    const float fy1 = fminf((float)y1, floorf(__fmul_rn(__fadd_rn(py, hy), ith)));
     if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
     x0 = (int)fx0;
     x1 = (int)fx1;

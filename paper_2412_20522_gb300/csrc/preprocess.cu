@@ -92,9 +92,9 @@ struct Splat32 {
 };
 
 // The FP32 decision path for one Gaussian and one camera (every op rounded).
-__device__ __forceinline__ void splat_fp32(const mg_camera &C, int tw, int th, int gx, int gy,
-                                           float x, float y, float z, const float ls[3],
-                                           const float q[4], Splat32 &S) {
+__device__ __forceinline__ void splat_fp32(const mg_camera &C, float limx, float limy, int tw,
+                                           int th, int gx, int gy, float x, float y, float z,
+                                           const float ls[3], const float q[4], Splat32 &S) {
     const float *V = C.viewmat;
     const float tx = ad(dot3(V[0], x, V[1], y, V[2], z), V[3]);
     const float ty = ad(dot3(V[4], x, V[5], y, V[6], z), V[7]);
@@ -129,9 +129,6 @@ __device__ __forceinline__ void splat_fp32(const mg_camera &C, int tw, int th, i
 #pragma unroll
         for (int k = 0; k < 3; ++k) S.M[j][k] = ml(S.R[j][k], S.s[k]);
 
-    const float tanx = dv(ml((float)C.width, 0.5f), C.fx);
-    const float tany = dv(ml((float)C.height, 0.5f), C.fy);
-    const float limx = ml(1.3f, tanx), limy = ml(1.3f, tany);
     const float cux = fminf(limx, fmaxf(-limx, S.ux));
     const float cuy = fminf(limy, fmaxf(-limy, S.uy));
     S.clampx = cux != S.ux;
@@ -182,9 +179,9 @@ __device__ __forceinline__ void splat_fp32(const mg_camera &C, int tw, int th, i
 // rounding.  The one decision on this chain, whether the Jacobian's point was
 // clamped, is taken exactly as in the forward (the correctly rounded ux, uy
 // against the same limits), so both use the same branch.
-__device__ __forceinline__ void splat_grad_pieces(const mg_camera &C, float x, float y, float z,
-                                                  const float ls[3], const float q[4],
-                                                  Splat32 &S) {
+__device__ __forceinline__ void splat_grad_pieces(const mg_camera &C, float limx, float limy,
+                                                  float x, float y, float z, const float ls[3],
+                                                  const float q[4], Splat32 &S) {
     const float *V = C.viewmat;
     const float tx = ad(dot3(V[0], x, V[1], y, V[2], z), V[3]);
     const float ty = ad(dot3(V[4], x, V[5], y, V[6], z), V[7]);
@@ -192,9 +189,6 @@ __device__ __forceinline__ void splat_grad_pieces(const mg_camera &C, float x, f
     S.tzs = S.tz > C.near_plane ? S.tz : 1.0f;
     S.ux = dv(tx, S.tzs);
     S.uy = dv(ty, S.tzs);
-    const float tanx = dv(ml((float)C.width, 0.5f), C.fx);
-    const float tany = dv(ml((float)C.height, 0.5f), C.fy);
-    const float limx = ml(1.3f, tanx), limy = ml(1.3f, tany);
     const float cux = fminf(limx, fmaxf(-limx, S.ux));
     const float cuy = fminf(limy, fmaxf(-limy, S.uy));
     S.clampx = cux != S.ux;
@@ -205,7 +199,7 @@ __device__ __forceinline__ void splat_grad_pieces(const mg_camera &C, float x, f
     S.s[2] = __expf(ls[2]);
     const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     const float inr = rsqrtf(n2 > 0.0f ? n2 : 1.0f);
-    S.nrm = 1.0f / inr;
+    S.nrm = __fdividef(1.0f, inr);
     const float w = q[0] * inr, qx = q[1] * inr, qy = q[2] * inr, qz = q[3] * inr;
     S.qn[0] = w; S.qn[1] = qx; S.qn[2] = qy; S.qn[3] = qz;
     S.R[0][0] = 1.0f - 2.0f * (qy * qy + qz * qz);
@@ -253,19 +247,24 @@ __device__ __forceinline__ void splat_grad_pieces(const mg_camera &C, float x, f
 
 // Major axis (cos, sin) and the two eigenvalues of [[a, b], [b, c]] from the
 // Cauchy-Binet determinant; continuous, so ordinary fast arithmetic.
+__device__ __forceinline__ float sqrt_fast(float x) {   // x >= 0; a few ulp
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 __device__ __forceinline__ void eigen2(const Splat32 &S, float &uxo, float &uyo, float &lam1,
                                        float &lam2) {
-    const float sq = sqrtf(S.disc);
+    const float sq = sqrt_fast(S.disc);
     lam1 = S.mid + sq;
-    lam2 = S.det / lam1;
+    lam2 = __fdividef(S.det, lam1);
     if (sq > 0.0f) {
-        const float c2 = 0.5f * (S.a - S.c) / sq, s2 = S.b / sq;
+        const float isq = __fdividef(1.0f, sq);
+        const float c2 = 0.5f * (S.a - S.c) * isq, s2 = S.b * isq;
         if (c2 >= 0.0f) {
-            uxo = sqrtf(0.5f * (1.0f + c2));
-            uyo = s2 / (2.0f * uxo);
+            uxo = sqrt_fast(0.5f * (1.0f + c2));
+            uyo = __fdividef(s2, 2.0f * uxo);
         } else {
-            uyo = sqrtf(0.5f * (1.0f - c2));
-            uxo = s2 / (2.0f * uyo);
+            uyo = sqrt_fast(0.5f * (1.0f - c2));
+            uxo = __fdividef(s2, 2.0f * uyo);
         }
     } else {
         uxo = 1.0f;
@@ -320,12 +319,12 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
             const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);  // FP32
             const float d = gumbel_margin(l, x);
             Mf = d >= 0.0f ? 1.0f : 0.0f;
-            out.mask_soft[i] = 1.0f / (1.0f + expf(-d / cfg.tau));
+            out.mask_soft[i] = __fdividef(1.0f, 1.0f + __expf(__fdividef(-d, cfg.tau)));
         } else if (cfg.mask_mode == MG_MASK_STE) {
             const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);
             const float d = sb(l.x, l.y);
             Mf = d > cfg.ste_logit ? 1.0f : 0.0f;
-            out.mask_soft[i] = 1.0f / (1.0f + expf(-d));
+            out.mask_soft[i] = __fdividef(1.0f, 1.0f + __expf(-d));
         } else {
             if (cfg.mask_mode == MG_MASK_GIVEN) Mf = cfg.given_mask[i] ? 1.0f : 0.0f;
             out.mask_soft[i] = 1.0f;
@@ -342,7 +341,7 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
     }
     if (!active) return;
 
-    const float op = 1.0f / (1.0f + __expf(-ol));
+    const float op = __fdividef(1.0f, 1.0f + __expf(-ol));
 
     bool sh_requested = false;
     for (int v = 0; v < vt.n_views; ++v) {
@@ -350,7 +349,8 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         const int64_t r = vt.rec_off[v] + (i - vt.g_off[v]);
         const mg_camera &C = vt.cam[v];
         Splat32 S;
-        splat_fp32(C, vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z, ls, q, S);
+        splat_fp32(C, vt.limx[v], vt.limy[v], vt.tile_w, vt.tile_h, vt.gx[v], vt.gy[v], x, y, z,
+                   ls, q, S);
         if (!S.visible) {
             out.tiles_touched[r] = 0u;
             out.radius[r] = 0;
@@ -414,8 +414,9 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
         // (mask x opacity ablation: the opacity is M o, +0 for a masked splat)
         const bool by_opacity = cfg.mask_apply == MG_APPLY_OPACITY;
         const float o_eff = by_opacity ? Mf * op : op;
-        const float e_min = o_eff >= kAlphaMin ? __log2f(kAlphaMin / o_eff) - 1e-3f : 1.0f;
-        rec[1] = make_float4(-0.5f * kLog2e / l1, -0.5f * kLog2e / l2,
+        const float e_min = o_eff >= kAlphaMin ? __log2f(__fdividef(kAlphaMin, o_eff)) - 1e-3f
+                                               : 1.0f;
+        rec[1] = make_float4(__fdividef(-0.5f * kLog2e, l1), __fdividef(-0.5f * kLog2e, l2),
                              (by_opacity || Mf != 0.0f) ? o_eff : -op, e_min);
         rec[2] = make_float4(rgb[0], rgb[1], rgb[2], S.tz);
     }
@@ -494,7 +495,7 @@ __device__ __forceinline__ void conic_backward(const Splat32 &S, float ux, float
         inverse_backward<double>((double)S.c * id, -(double)S.b * id, (double)S.a * id, dca, dcb,
                                  dcc, dS00, dS01, dS11);
     } else {
-        const float w1 = 1.0f / l1, w2 = 1.0f / l2;
+        const float w1 = __fdividef(1.0f, l1), w2 = __fdividef(1.0f, l2);
         inverse_backward<float>(w1 * ux * ux + w2 * uy * uy, (w1 - w2) * ux * uy,
                                 w1 * uy * uy + w2 * ux * ux, dca, dcb, dcc, dS00, dS01, dS11);
     }
@@ -545,7 +546,7 @@ __device__ __forceinline__ void cov_backward(const CovState &S, const mg_camera 
         const float gz = 2.0f * (w * (dR[1][0] - dR[0][1]) + qx * (dR[2][0] + dR[0][2]) +
                                  qy * (dR[1][2] + dR[2][1])) - 4.0f * qz * (dR[0][0] + dR[1][1]);
         const float dot = gw * w + gx * qx + gy * qy + gz * qz;
-        const float in = 1.0f / S.nrm;
+        const float in = __fdividef(1.0f, S.nrm);
         d_q[0] += (gw - dot * w) * in;
         d_q[1] += (gx - dot * qx) * in;
         d_q[2] += (gy - dot * qy) * in;
@@ -561,7 +562,7 @@ __device__ __forceinline__ void cov_backward(const CovState &S, const mg_camera 
         dJ12 += dT[1][k] * V[8 + k];
     }
     const float fx = C.fx, fy = C.fy;
-    const float itz = 1.0f / S.tzs, itz2 = itz * itz, itz3 = itz2 * itz;
+    const float itz = __fdividef(1.0f, S.tzs), itz2 = itz * itz, itz3 = itz2 * itz;
     // d J02 / d tz: 2 fx txc / tz^3 unclamped, fx txc / tz^3 clamped
     dL_dt[2] += -dJ00 * fx * itz2 - dJ11 * fy * itz2 +
                 dJ02 * fx * S.txc * itz3 * (clampx ? 1.0f : 2.0f) +
@@ -625,7 +626,7 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
         // the lane's own staging row (bank 17 l + c mod 32: no conflicts)
 #pragma unroll
         for (int f = 0; f < ROW; ++f) drow[f] = 0.0f;
-        const float op = 1.0f / (1.0f + __expf(-op_logit));
+        const float op = __fdividef(1.0f, 1.0f + __expf(-op_logit));
 
         float d_mean[3] = {0, 0, 0}, d_ls[3] = {0, 0, 0}, d_q[4] = {0, 0, 0, 0}, d_op = 0.0f,
               d_M = 0.0f;
@@ -640,7 +641,7 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
             d_op += g1.y;
             const mg_camera &C = vt.cam[v];
             Splat32 S;
-            splat_grad_pieces(C, x, y, z, ls, q, S);
+            splat_grad_pieces(C, vt.limx[v], vt.limy[v], x, y, z, ls, q, S);
             const float *V = C.viewmat;
             float dL_dt[3] = {0, 0, 0};   // camera-space centre
 
@@ -685,7 +686,7 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
 
             // ---- 2D mean: px = fx tx/tz + cx, py = fy ty/tz + cy
             {
-                const float itz = 1.0f / S.tzs;
+                const float itz = __fdividef(1.0f, S.tzs);
                 dL_dt[0] += g0.x * C.fx * itz;
                 dL_dt[1] += g0.y * C.fy * itz;
                 dL_dt[2] -= (g0.x * C.fx * S.ux + g0.y * C.fy * S.uy) * itz;
@@ -723,17 +724,17 @@ preprocess_backward_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_s
         if (cfg.lambda_m != 0.0f && sp.mask_count != nullptr) {
             for (int v = 0; v < vt.n_views; ++v) {
                 if (i < vt.g_off[v] || i >= vt.g_off[v] + vt.g_cnt[v]) continue;
-                const float N = (float)vt.g_cnt[v];
+                const float iN = __fdividef(1.0f, (float)vt.g_cnt[v]);
                 d_M += cfg.mask_loss == MG_MASK_LOSS_L1
-                           ? cfg.lambda_m / N
-                           : 2.0f * cfg.lambda_m * ((float)sp.mask_count[v] / N) / N;
+                           ? cfg.lambda_m * iN
+                           : 2.0f * cfg.lambda_m * ((float)sp.mask_count[v] * iN) * iN;
                 break;
             }
         }
         float dl0 = 0.0f;
         if (cfg.mask_mode == MG_MASK_GUMBEL) {
             const float y0 = sp.mask_soft[i];
-            dl0 = d_M * y0 * (1.0f - y0) / cfg.tau;
+            dl0 = __fdividef(d_M * y0 * (1.0f - y0), cfg.tau);
         } else if (cfg.mask_mode == MG_MASK_STE) {
             const float p = sp.mask_soft[i];
             dl0 = d_M * p * (1.0f - p);

@@ -41,6 +41,10 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+__device__ __forceinline__ float sqrt_approx(float x) {   // x >= 0
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -136,12 +140,14 @@ __device__ __forceinline__ uint32_t block_mask(const float4 &A, const float4 &B,
     // 1e-3 in log2 alpha); e_min > 0 marks a splat that never reaches the floor
     const float e_thr = B.w;
     if (!(e_thr < 0.0f)) return 0u;
-    const float r1 = sqrtf(e_thr / B.x) * 1.0001f + 0.02f;   // semi-axis along u
-    const float r2 = sqrtf(e_thr / B.y) * 1.0001f + 0.02f;   // semi-axis along u_perp
+    // approximate square roots and divisions (relative errors of a few 1e-7)
+    // stay far inside the 1e-4 relative and 0.02 px margins
+    const float r1 = sqrt_approx(__fdividef(e_thr, B.x)) * 1.0001f + 0.02f;   // along u
+    const float r2 = sqrt_approx(__fdividef(e_thr, B.y)) * 1.0001f + 0.02f;   // along u_perp
     const float ux = A.z, uy = A.w;
     const float aux = fabsf(ux), auy = fabsf(uy);
-    const float ex = sqrtf(r1 * r1 * ux * ux + r2 * r2 * uy * uy) + 0.02f;
-    const float ey = sqrtf(r1 * r1 * uy * uy + r2 * r2 * ux * ux) + 0.02f;
+    const float ex = sqrt_approx(r1 * r1 * ux * ux + r2 * r2 * uy * uy) + 0.02f;
+    const float ey = sqrt_approx(r1 * r1 * uy * uy + r2 * r2 * ux * ux) + 0.02f;
     // pixel centres of a block span its origin + 0.5 .. + 7.5
     const float hw = 0.5f * (float)(kBlock - 1), hh = hw;
     uint32_t m = 0u;
@@ -674,7 +680,8 @@ render_backward_kernel(ViewTable vt, const float4 *__restrict__ rec,
                 if (dmx != 0.0f || dmy != 0.0f || S[3] != 0.0f || S[4] != 0.0f)
                     atomicAdd(&G4[0], make_float4(dmx, dmy, -0.5f * S[3], -S[4]));
                 if (S[5] != 0.0f || S[0] != 0.0f || S[6] != 0.0f || S[7] != 0.0f)
-                    atomicAdd(&G4[1], make_float4(-0.5f * S[5], S[0] / fabsf(B.z), S[6], S[7]));
+                    atomicAdd(&G4[1], make_float4(-0.5f * S[5], __fdividef(S[0], fabsf(B.z)),
+                                                  S[6], S[7]));
                 if (S[8] != 0.0f || S[9] != 0.0f)
                     atomicAdd(reinterpret_cast<float2 *>(&G4[2]), make_float2(S[8], S[9]));
             }
