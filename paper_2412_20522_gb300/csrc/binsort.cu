@@ -66,13 +66,32 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
     const int64_t part = sm_part;
     if (part >= n_parts) return;
     const int64_t base = part * kScanPart + (int64_t)threadIdx.x * kScanItems;
+    // 128-bit loads of the positions' records and stores of their offsets
+    // where both arrays are 16-byte aligned (base is a multiple of 8)
+    const bool vec =
+        ((reinterpret_cast<uintptr_t>(order) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
     uint32_t v[kScanItems];
     uint64_t sum = 0;
     if (order == nullptr && base + kScanItems <= n) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(in + base);
-        const uint4 b = *reinterpret_cast<const uint4 *>(in + base + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(in + base + 4 * q);
+            v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+        }
+    } else if (order != nullptr && vec && base + kScanItems <= n) {
+        // the positions' records with 128-bit loads, then the gather
+        uint32_t o[kScanItems];
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(order + base + 4 * q);
+            o[4 * q] = a.x; o[4 * q + 1] = a.y; o[4 * q + 2] = a.z; o[4 * q + 3] = a.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t idx = (int64_t)o[k];
+            if (!MG_IN_BOUNDS(idx < n, st, 1, idx)) idx = n;   // skipped
+            v[k] = idx < n ? in[idx] : 0u;
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
@@ -108,9 +127,12 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
     }
     __syncthreads();
     uint64_t run = sm_prefix + excl;
+    const bool whole = vec && base + kScanItems <= n;
+    uint32_t ov[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = run > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)run;
+        ov[k] = run > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)run;
+        if (!whole && base + k < n) out[base + k] = ov[k];
         // the position owns slots [run, run + v): it marks the duplication
         // chunks that start among them (owner_hint[c C] = position, C =
         // kDupChunk), below the capacity
@@ -120,6 +142,12 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ order,
                 owner_hint[c * kDupChunk] = (uint32_t)(base + k);
         }
         run += v[k];
+    }
+    if (whole) {
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q)
+            *reinterpret_cast<uint4 *>(out + base + 4 * q) =
+                make_uint4(ov[4 * q], ov[4 * q + 1], ov[4 * q + 2], ov[4 * q + 3]);
     }
 }
 
