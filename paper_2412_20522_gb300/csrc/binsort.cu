@@ -492,14 +492,26 @@ __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint64_t 
     if (d_num_sorted != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *d_num_sorted = *d_n;
     const int64_t n = sort_count(d_n, capacity);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
     for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+        // the thread's four keys (one 128-bit load where aligned), the one
+        // before and the one after
+        uint32_t k4[5];
+        if (vec && i0 + 4 <= n) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(keys + i0);
+            k4[0] = a.x; k4[1] = a.y; k4[2] = a.z; k4[3] = a.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k4[u] = i0 + u < n ? keys[i0 + u] : 0xFFFFFFFFu;
+        }
+        k4[4] = i0 + 4 < n ? keys[i0 + 4] : 0xFFFFFFFFu;
         uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0xFFFFFFFFu;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t i = i0 + u;
             if (i >= n) break;
-            const uint32_t t = keys[i];
-            const uint32_t next = i + 1 < n ? keys[i + 1] : 0xFFFFFFFFu;
+            const uint32_t t = k4[u];
+            const uint32_t next = i + 1 < n ? k4[u + 1] : 0xFFFFFFFFu;
             if ((int64_t)t < n_tiles) {
                 if (i == 0 || prev != t) ranges[2 * (int64_t)t] = (uint32_t)i;
                 if (i == n - 1 || next != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);

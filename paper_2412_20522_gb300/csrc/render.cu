@@ -948,12 +948,26 @@ tile_order_kernel(const uint32_t *__restrict__ ranges, int64_t n, uint32_t *__re
         atomicAdd(&hist[length_bucket(r.y - r.x)], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {                       // starts, longest bucket first
-        uint32_t run = 0;
-        for (int b = kOrderBuckets - 1; b >= 0; --b) {
-            const uint32_t c = hist[b];
-            hist[b] = run;
-            run += c;
+    static_assert(kOrderBuckets == 4 * 32, "one warp scans the buckets, four per lane");
+    if (threadIdx.x < 32) {                       // starts, longest bucket first
+        const int l = threadIdx.x;
+        uint32_t c[4], own = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = hist[kOrderBuckets - 1 - (4 * l + u)];
+            own += c[u];
+        }
+        uint32_t inc = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (l >= o) inc += y;
+        }
+        uint32_t run = inc - own;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            hist[kOrderBuckets - 1 - (4 * l + u)] = run;
+            run += c[u];
         }
     }
     __syncthreads();
