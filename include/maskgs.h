@@ -179,6 +179,12 @@ typedef struct {
      * defaults (256, 128); other values return MG_ERR_INVALID_ARG. */
     int32_t render_batch;
     int32_t render_batch_bwd;
+    /* Device word (nullable) added to `iteration` by the mask sample: a step
+     * captured in a CUDA graph keeps every argument it was captured with, so
+     * a training loop that replays it draws a new mask each step only if the
+     * iteration lives in device memory and is advanced between replays
+     * (mg_advance_iteration, captured with the step). */
+    const uint64_t *iteration_dev;
 } mg_raster_cfg;
 
 /* Per-view preprocess outputs (R = sum_v gaussian_count_v records):
@@ -449,6 +455,12 @@ mg_status mg_preprocess_backward(const mg_gaussians *g, const mg_view *views,
                                  const mg_param_grads *out, mg_stream_t stream);
 
 /* ---- 8. mask loss (Sec. 3.5, Eq. 7-8) ----------------------------------------- */
+/* *iteration_dev += by on the stream (one thread), for the mask sample's
+ * device-side iteration (mg_raster_cfg.iteration_dev, Sec. 3.3: a new
+ * Gumbel sample every training step): enqueued after a step, it advances the
+ * counter the next step reads, also inside a captured CUDA graph. */
+mg_status mg_advance_iteration(uint64_t *iteration_dev, uint64_t by, mg_stream_t stream);
+
 /* *loss (device f32) += lambda_m * sum over scenes of L_m, from
  * splats->mask_count (a scene = a distinct Gaussian range among the views,
  * N = its gaussian_count; empty ranges add nothing).  The gradient is added

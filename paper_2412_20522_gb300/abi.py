@@ -27,7 +27,7 @@ EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes",
             "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
             "mg_sort_workspace_bytes", "mg_sort_by_tile", "mg_sort_by_tile_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render", "mg_render_l1",
             "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
-            "mg_mask_loss", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
+            "mg_mask_loss", "mg_advance_iteration", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
             "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
             "mg_version", "mg_selftest_wait_timeout", "mg_selftest_warp_wait_timeout",
             "mg_validate_lists")
@@ -67,7 +67,7 @@ class mg_raster_cfg(C.Structure):
                 ("mask_mode", C.c_int32), ("mask_apply", C.c_int32), ("given_mask", C.c_void_p),
                 ("lambda_m", C.c_float), ("mask_loss", C.c_int32), ("ste_logit", C.c_float),
                 ("bin_mode", C.c_int32), ("render_batch", C.c_int32),
-                ("render_batch_bwd", C.c_int32)]
+                ("render_batch_bwd", C.c_int32), ("iteration_dev", C.c_void_p)]
 
 
 class mg_splats(C.Structure):
@@ -144,6 +144,7 @@ def load(build_if_missing: bool = True):
                                         _P(mg_raster_cfg), _P(mg_splats), vp,
                                         _P(mg_param_grads), vp]),
         "mg_mask_loss": (st, [_P(mg_splats), _P(mg_view), C.c_int32, _P(mg_raster_cfg), vp, vp]),
+        "mg_advance_iteration": (st, [vp, C.c_uint64, vp]),
         "mg_prune_sample": (st, [_P(mg_gaussians), C.c_uint64, C.c_uint64, C.c_int32, vp, vp]),
         "mg_compact": (st, [_P(mg_gaussians), vp, _P(mg_gaussian_arrays), vp, vp, vp, C.c_size_t,
                             vp, vp]),
@@ -303,6 +304,12 @@ def mg_preprocess_backward(g, views, n_views, cfg, splats, grad2d, out, stream):
 def mg_mask_loss(splats, views, n_views, cfg, loss, stream):
     _check("mg_mask_loss", load().mg_mask_loss(C.byref(splats), views, n_views, C.byref(cfg),
                                                ptr(loss), stream))
+
+
+def mg_advance_iteration(iteration_dev, by, stream):
+    """*iteration_dev += by on the stream (the mask sample's device-side
+    iteration, read through mg_raster_cfg.iteration_dev)."""
+    _check("mg_advance_iteration", load().mg_advance_iteration(ptr(iteration_dev), by, stream))
 
 
 def mg_prune_sample(g, seed, iteration, n_draws, keep, stream):

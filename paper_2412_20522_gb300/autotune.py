@@ -49,12 +49,27 @@ class GraphStep:
     """One masked forward + L1 loss + backward captured in a CUDA graph.
 
     All buffers are sized by a synchronising first step; the captured graph
-    then replays the whole sequence (no host synchronisation inside)."""
+    then replays the whole sequence (no host synchronisation inside).
+
+    A captured step keeps the arguments it was captured with, the mask
+    sample's iteration among them.  With ``advance_iteration`` the iteration
+    lives in a device counter (``self.iteration``: the next replay samples
+    with cfg.iteration + its value) that the step itself advances by one
+    after the backward, so successive replays draw successive Gumbel masks
+    (Sec. 3.3), as a training loop needs.  The counter counts every step run,
+    the warm-up ones included; set it (``self.iteration.fill_(k)``) to choose
+    the next replay's iteration."""
 
     def __init__(self, params, cams, cfg: RasterConfig, target, view_ranges=None, warmup=2,
-                 tile_order=True):
+                 tile_order=True, advance_iteration=False):
         self.params = params
         self.cams = cams
+        self.advance_iteration = advance_iteration
+        self.iteration = None
+        if advance_iteration:
+            import dataclasses
+            self.iteration = torch.zeros(1, dtype=torch.int64, device=params["means"].device)
+            cfg = dataclasses.replace(cfg, iteration_dev=self.iteration)
         self.cfg = cfg
         self.target = target
         self.view_ranges = view_ranges
@@ -78,6 +93,9 @@ class GraphStep:
         img, loss, dimg = self.rast.forward_l1(self.params, self.cams, self.cfg, self.target,
                                                view_ranges=self.view_ranges, check=False)
         self.rast.backward(dimg, self.grads)
+        if self.advance_iteration:
+            from . import abi
+            abi.mg_advance_iteration(self.iteration, 1, self.rast._stream())
         self.image = img
         return loss
 

@@ -315,7 +315,8 @@ preprocess_kernel(ViewTable vt, mg_gaussians g, mg_raster_cfg cfg, mg_splats out
     float Mf = active ? 1.0f : 0.0f;
     if (active) {
         if (cfg.mask_mode == MG_MASK_GUMBEL) {
-            const uint4 x = gumbel_counter(i, cfg.iteration, 0u, cfg.seed);
+            const uint64_t it = cfg.iteration + (cfg.iteration_dev ? *cfg.iteration_dev : 0ull);
+            const uint4 x = gumbel_counter(i, it, 0u, cfg.seed);
             const float2 l = __ldg(reinterpret_cast<const float2 *>(g.mask_logits) + i);  // FP32
             const float d = gumbel_margin(l, x);
             Mf = d >= 0.0f ? 1.0f : 0.0f;
@@ -921,6 +922,22 @@ __global__ void mask_loss_kernel(SceneList sl, const uint32_t *__restrict__ mask
     *loss += (float)((double)lambda_m * acc);
 }
 }  // namespace mg
+
+namespace mg {
+__global__ void advance_iteration_kernel(uint64_t *it, uint64_t by) {
+    grid_dependency_wait();
+    *it += by;
+}
+}  // namespace mg
+
+extern "C" mg_status mg_advance_iteration(uint64_t *iteration_dev, uint64_t by,
+                                          mg_stream_t stream) {
+    if (iteration_dev == nullptr || (reinterpret_cast<uintptr_t>(iteration_dev) & 7u) != 0)
+        return MG_ERR_INVALID_ARG;
+    launch_pdl(advance_iteration_kernel, dim3(1), dim3(1), 0, (cudaStream_t)stream,
+        iteration_dev, by);
+    return mg_host::launch_status();
+}
 
 extern "C" mg_status mg_mask_loss(const mg_splats *splats, const mg_view *views, int32_t n_views,
                                   const mg_raster_cfg *cfg, float *loss, mg_stream_t stream) {

@@ -42,6 +42,10 @@ class RasterConfig:
     # forward, 128 backward; also 128 forward, 64 backward)
     render_batch: int = 0
     render_batch_bwd: int = 0
+    # int64 [1] on the device (optional): added to `iteration` by the mask
+    # sample, so a captured step draws a new mask each replay when the
+    # counter is advanced between replays (abi.mg_advance_iteration)
+    iteration_dev: torch.Tensor | None = None
 
     @staticmethod
     def ste_logit_of(theta: float) -> float:
@@ -67,6 +71,7 @@ class RasterConfig:
         cfg.bin_mode = int(self.bin_mode)
         cfg.render_batch = int(self.render_batch)
         cfg.render_batch_bwd = int(self.render_batch_bwd)
+        cfg.iteration_dev = abi.ptr(self.iteration_dev) if self.iteration_dev is not None else None
         return cfg
 
 

@@ -123,3 +123,6 @@ def test_mask_pruning_and_inference_arguments_rejected_on_host(lib):
     assert lib.mg_tile_order(None, 10, None, None) == abi.MG_ERR_INVALID_ARG
     assert lib.mg_selftest_wait_timeout(10, None, None) == abi.MG_ERR_INVALID_ARG
     assert lib.mg_selftest_warp_wait_timeout(10, None, None) == abi.MG_ERR_INVALID_ARG
+    # the device-side iteration counter: a null or misaligned word
+    assert lib.mg_advance_iteration(None, 1, None) == abi.MG_ERR_INVALID_ARG
+    assert lib.mg_advance_iteration(C.c_void_p(4), 1, None) == abi.MG_ERR_INVALID_ARG
