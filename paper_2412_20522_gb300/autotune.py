@@ -61,14 +61,18 @@ class GraphStep:
     the next replay's iteration."""
 
     def __init__(self, params, cams, cfg: RasterConfig, target, view_ranges=None, warmup=2,
-                 tile_order=True, advance_iteration=False):
+                 tile_order=True, advance_iteration=False, iteration=None):
         self.params = params
         self.cams = cams
-        self.advance_iteration = advance_iteration
-        self.iteration = None
-        if advance_iteration:
+        # ``iteration``: a device counter (int64 [1]) to read and advance,
+        # shared with other captured steps (the slots of a pipeline, replayed
+        # in turn on one stream); implies advance_iteration
+        self.advance_iteration = advance_iteration or iteration is not None
+        self.iteration = iteration
+        if self.advance_iteration:
             import dataclasses
-            self.iteration = torch.zeros(1, dtype=torch.int64, device=params["means"].device)
+            if self.iteration is None:
+                self.iteration = torch.zeros(1, dtype=torch.int64, device=params["means"].device)
             cfg = dataclasses.replace(cfg, iteration_dev=self.iteration)
         self.cfg = cfg
         self.target = target

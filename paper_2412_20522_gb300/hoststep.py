@@ -9,6 +9,10 @@ input and output buffers are double-buffered; events order every reuse.
 All compute is the libmaskgs step: by default each slot replays its own
 captured CUDA graph of the whole step (``autotune.GraphStep``, no launch
 gaps); ``graph=False`` issues the same kernels one by one (``Rasterizer``).
+With ``advance_iteration`` the steps share one device-side iteration counter
+(``self.iteration``, mg_raster_cfg.iteration_dev) that each step advances
+after its backward, so step k draws the Gumbel mask of iteration
+cfg.iteration + k (Sec. 3.3); the counter starts at 0 for the first step.
 """
 from __future__ import annotations
 
@@ -19,8 +23,14 @@ from .rasterize import PARAM_NAMES, RasterConfig, Rasterizer
 
 class HostPipeline:
     def __init__(self, host_params: dict, host_target: torch.Tensor, cams, cfg: RasterConfig,
-                 device="cuda", view_ranges=None, graph: bool = True):
+                 device="cuda", view_ranges=None, graph: bool = True,
+                 advance_iteration: bool = False):
         self.dev = torch.device(device)
+        self.iteration = None
+        if advance_iteration:
+            import dataclasses
+            self.iteration = torch.zeros(1, dtype=torch.int64, device=self.dev)
+            cfg = dataclasses.replace(cfg, iteration_dev=self.iteration)
         self.cams, self.cfg, self.view_ranges = cams, cfg, view_ranges
         for k, t in host_params.items():
             if not t.is_pinned():
@@ -64,11 +74,15 @@ class HostPipeline:
             # writing its own gradients, image and loss
             from .autotune import GraphStep
             self.graphs = [GraphStep(self.params[b], cams, cfg, self.target[b],
-                                     view_ranges=view_ranges) for b in range(2)]
+                                     view_ranges=view_ranges, iteration=self.iteration)
+                           for b in range(2)]
             for b in range(2):
                 self.grads[b] = self.graphs[b].grads
                 self.image[b] = self.graphs[b].image
                 self.loss[b] = self.graphs[b].loss
+            torch.cuda.synchronize(self.dev)
+        if self.iteration is not None:     # the warm-up steps advanced it: step 0 reads 0
+            self.iteration.zero_()
             torch.cuda.synchronize(self.dev)
         self.i = 0
 
@@ -104,6 +118,9 @@ class HostPipeline:
                                                        self.target[b],
                                                        view_ranges=self.view_ranges, check=False)
                 self.rast.backward(dimg, self.grads[b])
+                if self.iteration is not None:
+                    from . import abi
+                    abi.mg_advance_iteration(self.iteration, 1, self.rast._stream())
                 self.image[b].copy_(img)
                 self.loss[b].copy_(loss)
             self.ev_comp[b] = torch.cuda.Event()
