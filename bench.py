@@ -301,6 +301,8 @@ def run_ours(args):
                     "block_ms_max": max(blocks), "timed_s": sum(blocks) / 1e3}
     if gs.status() != abi.MG_OK:
         raise RuntimeError(f"device status {gs.status()} after the graph steps")
+    # the timed step's launches (the graph step's rasteriser: fused L1 render)
+    gpu_launches_per_step = gs.rast.launches_per_step() + gs.rast.backward_launches()
     del gs
     stage_ms = {k: statistics.mean(e[k][0].elapsed_time(e[k][1]) for e in evs) for k in stage_names}
     # per-step distribution: first stage's start to last stage's end of each step
@@ -335,7 +337,6 @@ def run_ours(args):
     so = rast.splat_outputs()
     visible = int((so["radius"] > 0).sum().item())
     mask_on = float(so["mask"].float().mean().item())
-    gpu_launches_per_step = rast.launches_per_step() + rast.backward_launches()
 
     # end to end through the C ABI with host buffers: every step copies the
     # parameters and the target from pinned host memory and the image, loss

@@ -406,6 +406,18 @@ mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
                        float *image, float *final_T, uint32_t *n_contrib, const float *target,
                        float *dL_dimage, float *loss, mg_stream_t stream);
 
+/* mg_render_l1 that also zeroes grad2d[R][12] (16-byte aligned), the
+ * accumulator of the render backward, for mg_render_backward_accumulate: the
+ * render kernel's CTAs store the zeros while they render (its memory path is
+ * nearly idle), so the training step needs no separate reset between the
+ * render and its backward.  No paper counterpart: a scheduling choice. */
+mg_status mg_render_l1_reset2d(const mg_splats *splats, const uint32_t *sorted_vals,
+                               const uint32_t *ranges, const uint32_t *tile_order,
+                               const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                               float *image, float *final_T, uint32_t *n_contrib,
+                               const float *target, float *dL_dimage, float *loss, float *grad2d,
+                               mg_stream_t stream);
+
 /* ---- 5. L1 render loss ------------------------------------------------------ */
 /* For count = sum_v 3 W_v H_v values: dL_dimage[i] = sign(image[i] - target[i])
  * / (3 W_v H_v) of the view holding i (sign(0) = 0), and *loss (device f32)
@@ -436,6 +448,15 @@ mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_val
                              const float *final_T, const uint32_t *n_contrib,
                              const float *dL_dimage, float *grad2d, uint64_t *counters,
                              mg_stream_t stream);
+
+/* The same, adding into grad2d instead of zeroing it first: the caller provides
+ * it zeroed (mg_render_l1_reset2d does so while it renders). */
+mg_status mg_render_backward_accumulate(const mg_splats *splats, const uint32_t *sorted_vals,
+                                        const uint32_t *ranges, const uint32_t *tile_order,
+                                        const mg_view *views, int32_t n_views,
+                                        const mg_raster_cfg *cfg, const float *final_T,
+                                        const uint32_t *n_contrib, const float *dL_dimage,
+                                        float *grad2d, uint64_t *counters, mg_stream_t stream);
 
 /* ---- 7. preprocess backward ------------------------------------------------- */
 /* Chain rule from grad2d through the 2D covariance (P = J W R S), the

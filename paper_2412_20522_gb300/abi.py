@@ -25,8 +25,9 @@ MG_GRAD2D_FLOATS = 12
 
 EXPORTED = ("mg_preprocess", "mg_depth_order", "mg_depth_order_workspace_bytes", "mg_bin",
             "mg_bin_noalloc", "mg_bin_workspace_bytes", "mg_sort",
-            "mg_sort_workspace_bytes", "mg_sort_by_tile", "mg_sort_by_tile_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render", "mg_render_l1",
-            "mg_l1_loss_grad", "mg_render_backward", "mg_preprocess_backward",
+            "mg_sort_workspace_bytes", "mg_sort_by_tile", "mg_sort_by_tile_workspace_bytes", "mg_tile_bits", "mg_total_tiles", "mg_render", "mg_render_l1", "mg_render_l1_reset2d",
+            "mg_l1_loss_grad", "mg_render_backward", "mg_render_backward_accumulate",
+            "mg_preprocess_backward",
             "mg_mask_loss", "mg_advance_iteration", "mg_prune_sample", "mg_compact", "mg_compact_workspace_bytes",
             "mg_render_inference", "mg_tile_order", "mg_read_status", "mg_status_string",
             "mg_version", "mg_selftest_wait_timeout", "mg_selftest_warp_wait_timeout",
@@ -136,10 +137,15 @@ def load(build_if_missing: bool = True):
                            _P(mg_raster_cfg), vp, vp, vp, vp, vp]),
         "mg_render_l1": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
                               _P(mg_raster_cfg), vp, vp, vp, vp, vp, vp, vp]),
+        "mg_render_l1_reset2d": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
+                                      _P(mg_raster_cfg), vp, vp, vp, vp, vp, vp, vp, vp]),
         "mg_tile_order": (st, [vp, C.c_int64, vp, vp]),
         "mg_l1_loss_grad": (st, [vp, vp, _P(mg_view), C.c_int32, vp, vp, vp]),
         "mg_render_backward": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view), C.c_int32,
                                     _P(mg_raster_cfg), vp, vp, vp, vp, vp, vp]),
+        "mg_render_backward_accumulate": (st, [_P(mg_splats), vp, vp, vp, _P(mg_view),
+                                               C.c_int32, _P(mg_raster_cfg), vp, vp, vp, vp, vp,
+                                               vp]),
         "mg_preprocess_backward": (st, [_P(mg_gaussians), _P(mg_view), C.c_int32,
                                         _P(mg_raster_cfg), _P(mg_splats), vp,
                                         _P(mg_param_grads), vp]),
@@ -282,6 +288,15 @@ def mg_render_l1(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, i
         ptr(loss), stream))
 
 
+def mg_render_l1_reset2d(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, image,
+                         final_T, n_contrib, target, dL_dimage, loss, grad2d, stream):
+    """mg_render_l1 that also zeroes grad2d for mg_render_backward_accumulate."""
+    _check("mg_render_l1_reset2d", load().mg_render_l1_reset2d(
+        C.byref(splats), ptr(sorted_vals), ptr(ranges), ptr(tile_order), views, n_views,
+        C.byref(cfg), ptr(image), ptr(final_T), ptr(n_contrib), ptr(target), ptr(dL_dimage),
+        ptr(loss), ptr(grad2d), stream))
+
+
 def mg_l1_loss_grad(image, target, views, n_views, dL_dimage, loss, stream):
     _check("mg_l1_loss_grad", load().mg_l1_loss_grad(ptr(image), ptr(target), views, n_views,
                                                      ptr(dL_dimage), ptr(loss), stream))
@@ -290,6 +305,15 @@ def mg_l1_loss_grad(image, target, views, n_views, dL_dimage, loss, stream):
 def mg_render_backward(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, final_T,
                        n_contrib, dL_dimage, grad2d, counters, stream):
     _check("mg_render_backward", load().mg_render_backward(
+        C.byref(splats), ptr(sorted_vals), ptr(ranges), ptr(tile_order), views, n_views,
+        C.byref(cfg),
+        ptr(final_T), ptr(n_contrib), ptr(dL_dimage), ptr(grad2d), ptr(counters), stream))
+
+
+def mg_render_backward_accumulate(splats, sorted_vals, ranges, tile_order, views, n_views, cfg,
+                                  final_T, n_contrib, dL_dimage, grad2d, counters, stream):
+    """mg_render_backward adding into grad2d, which the caller has zeroed."""
+    _check("mg_render_backward_accumulate", load().mg_render_backward_accumulate(
         C.byref(splats), ptr(sorted_vals), ptr(ranges), ptr(tile_order), views, n_views,
         C.byref(cfg),
         ptr(final_T), ptr(n_contrib), ptr(dL_dimage), ptr(grad2d), ptr(counters), stream))

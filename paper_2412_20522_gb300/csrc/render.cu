@@ -201,8 +201,19 @@ render_forward_kernel(ViewTable vt, const float4 *__restrict__ rec, const uint32
                       float *__restrict__ image, float *__restrict__ final_T,
                       uint32_t *__restrict__ n_contrib, unsigned long long *frag_count,
                       const float *__restrict__ target = nullptr,
-                      float *__restrict__ dL_dimage = nullptr, float *loss = nullptr) {
+                      float *__restrict__ dL_dimage = nullptr, float *loss = nullptr,
+                      float4 *__restrict__ reset4 = nullptr, int64_t reset_n4 = 0) {
     grid_dependency_wait();
+    // the training forward also resets the backward's 2D-gradient accumulator:
+    // each CTA stores zeros over its share (the kernel's memory path is nearly
+    // idle, and the backward starts only once this kernel has completed)
+    if (reset4 != nullptr) {
+        const int64_t per = (reset_n4 + gridDim.x - 1) / gridDim.x;
+        const int64_t q0 = (int64_t)blockIdx.x * per;
+        const int64_t q1 = min(q0 + per, reset_n4);
+        for (int64_t q = q0 + threadIdx.x; q < q1; q += kRenderThreads)
+            reset4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
     __shared__ uint8_t sM[BATCH];
     __shared__ unsigned long long s_frags[4];
@@ -765,16 +776,18 @@ static bool bwd_batch(const mg_raster_cfg *cfg, int *b) {
     return *b == 64 || *b == 128;
 }
 
-extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
-                                  const uint32_t *ranges, const uint32_t *tile_order,
-                                  const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
-                                  float *image, float *final_T, uint32_t *n_contrib,
-                                  const float *target, float *dL_dimage, float *loss,
-                                  mg_stream_t stream) {
+// The render with the L1 loss; grad2d (nullable) is reset on the way.
+static mg_status render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
+                           const uint32_t *ranges, const uint32_t *tile_order,
+                           const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                           float *image, float *final_T, uint32_t *n_contrib, const float *target,
+                           float *dL_dimage, float *loss, float *grad2d, mg_stream_t stream) {
     if (!splats || !splats->record || !sorted_vals || !ranges || !image || !final_T ||
         !n_contrib || !target || !dL_dimage || !loss)
         return MG_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(splats->record) & 15u) != 0) return MG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats->record) & 15u) != 0 ||
+        (reinterpret_cast<uintptr_t>(grad2d) & 15u) != 0)
+        return MG_ERR_INVALID_ARG;
     ViewTable vt;
     mg_status st = mg_host::build_view_table(views, n_views, cfg, &vt);
     if (st != MG_OK) return st;
@@ -783,17 +796,48 @@ extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorte
     int batch;
     if (!fwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
+    float4 *reset4 = reinterpret_cast<float4 *>(grad2d);
+    const int64_t reset_n4 = grad2d ? vt.rec_off[n_views] * (MG_GRAD2D_FLOATS / 4) : 0;
+    if (tiles == 0) {   // no tile to carry the reset
+        if (grad2d && reset_n4 > 0 &&
+            mg_host::zero_async(grad2d, sizeof(float4) * (size_t)reset_n4, (cudaStream_t)stream) !=
+                MG_OK)
+            return MG_ERR_CUDA;
+        return MG_OK;
+    }
     if (batch == 128)
         launch_pdl(render_forward_kernel<false, true, true, 128>, dim3((unsigned)tiles),
             dim3(kRenderThreads), 0, (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order,
             cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T, n_contrib, nullptr, target,
-            dL_dimage, loss);
+            dL_dimage, loss, reset4, reset_n4);
     else
         launch_pdl(render_forward_kernel<false, true, true>, dim3((unsigned)tiles),
             dim3(kRenderThreads), 0, (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order,
             cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T, n_contrib, nullptr, target,
-            dL_dimage, loss);
+            dL_dimage, loss, reset4, reset_n4);
     return mg_host::launch_status();
+}
+
+extern "C" mg_status mg_render_l1(const mg_splats *splats, const uint32_t *sorted_vals,
+                                  const uint32_t *ranges, const uint32_t *tile_order,
+                                  const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                                  float *image, float *final_T, uint32_t *n_contrib,
+                                  const float *target, float *dL_dimage, float *loss,
+                                  mg_stream_t stream) {
+    return render_l1(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, image, final_T,
+                     n_contrib, target, dL_dimage, loss, nullptr, stream);
+}
+
+extern "C" mg_status mg_render_l1_reset2d(const mg_splats *splats, const uint32_t *sorted_vals,
+                                          const uint32_t *ranges, const uint32_t *tile_order,
+                                          const mg_view *views, int32_t n_views,
+                                          const mg_raster_cfg *cfg, float *image, float *final_T,
+                                          uint32_t *n_contrib, const float *target,
+                                          float *dL_dimage, float *loss, float *grad2d,
+                                          mg_stream_t stream) {
+    if (grad2d == nullptr) return MG_ERR_INVALID_ARG;
+    return render_l1(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, image, final_T,
+                     n_contrib, target, dL_dimage, loss, grad2d, stream);
 }
 
 extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_vals,
@@ -816,16 +860,18 @@ extern "C" mg_status mg_render(const mg_splats *splats, const uint32_t *sorted_v
         launch_pdl(render_forward_kernel<true>, dim3((unsigned)tiles), dim3(kRenderThreads), 0,
             (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1],
             cfg->bg[2], image, final_T, n_contrib,
-            reinterpret_cast<unsigned long long *>(frag_count), nullptr, nullptr, nullptr);
+            reinterpret_cast<unsigned long long *>(frag_count), nullptr, nullptr, nullptr, nullptr,
+            (int64_t)0);
     else if (batch == 128)
         launch_pdl(render_forward_kernel<false, true, false, 128>, dim3((unsigned)tiles),
             dim3(kRenderThreads), 0, (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order,
             cfg->bg[0], cfg->bg[1], cfg->bg[2], image, final_T, n_contrib, nullptr, nullptr,
-            nullptr, nullptr);
+            nullptr, nullptr, nullptr, (int64_t)0);
     else
         launch_pdl(render_forward_kernel<false>, dim3((unsigned)tiles), dim3(kRenderThreads), 0,
             (cudaStream_t)stream, vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1],
-            cfg->bg[2], image, final_T, n_contrib, nullptr, nullptr, nullptr, nullptr);
+            cfg->bg[2], image, final_T, n_contrib, nullptr, nullptr, nullptr, nullptr, nullptr,
+            (int64_t)0);
     return mg_host::launch_status();
 }
 
@@ -849,22 +895,22 @@ extern "C" mg_status mg_render_inference(const mg_splats *splats, const uint32_t
             dim3(kRenderThreads), 0, (cudaStream_t)stream, vt,
             reinterpret_cast<const float4 *>(splats->record), sorted_vals, ranges, tile_order,
             cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr, nullptr, nullptr, nullptr, nullptr,
-            nullptr);
+            nullptr, nullptr, (int64_t)0);
     else
         launch_pdl(render_forward_kernel<false, false>, dim3((unsigned)tiles), dim3(kRenderThreads),
             0, (cudaStream_t)stream, vt, reinterpret_cast<const float4 *>(splats->record),
             sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, nullptr,
-            nullptr, nullptr, nullptr, nullptr, nullptr);
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (int64_t)0);
     return mg_host::launch_status();
 }
 
-extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
-                                        const uint32_t *ranges, const uint32_t *tile_order,
-                                        const mg_view *views, int32_t n_views,
-                                        const mg_raster_cfg *cfg,
-                                        const float *final_T, const uint32_t *n_contrib,
-                                        const float *dL_dimage, float *grad2d,
-                                        uint64_t *counters, mg_stream_t stream) {
+// The render backward, resetting grad2d first (zero) or adding into it.
+static mg_status render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
+                                 const uint32_t *ranges, const uint32_t *tile_order,
+                                 const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+                                 const float *final_T, const uint32_t *n_contrib,
+                                 const float *dL_dimage, float *grad2d, uint64_t *counters,
+                                 mg_stream_t stream, bool zero) {
     if (!splats || !splats->record || !sorted_vals || !ranges || !final_T || !n_contrib ||
         !dL_dimage || !grad2d)
         return MG_ERR_INVALID_ARG;
@@ -879,8 +925,8 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
     int batch;
     if (!bwd_batch(cfg, &batch)) return MG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (R > 0 && mg_host::zero_async(grad2d, sizeof(float) * MG_GRAD2D_FLOATS * (size_t)R, s) !=
-                     MG_OK)
+    if (zero && R > 0 &&
+        mg_host::zero_async(grad2d, sizeof(float) * MG_GRAD2D_FLOATS * (size_t)R, s) != MG_OK)
         return MG_ERR_CUDA;
     const float4 *rec = reinterpret_cast<const float4 *>(splats->record);
     if (counters != nullptr)
@@ -896,6 +942,26 @@ extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t 
             vt, rec, sorted_vals, ranges, tile_order, cfg->bg[0], cfg->bg[1], cfg->bg[2], final_T,
             n_contrib, dL_dimage, grad2d, nullptr);
     return mg_host::launch_status();
+}
+
+extern "C" mg_status mg_render_backward(const mg_splats *splats, const uint32_t *sorted_vals,
+                                        const uint32_t *ranges, const uint32_t *tile_order,
+                                        const mg_view *views, int32_t n_views,
+                                        const mg_raster_cfg *cfg,
+                                        const float *final_T, const uint32_t *n_contrib,
+                                        const float *dL_dimage, float *grad2d,
+                                        uint64_t *counters, mg_stream_t stream) {
+    return render_backward(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, final_T,
+                           n_contrib, dL_dimage, grad2d, counters, stream, true);
+}
+
+extern "C" mg_status mg_render_backward_accumulate(
+    const mg_splats *splats, const uint32_t *sorted_vals, const uint32_t *ranges,
+    const uint32_t *tile_order, const mg_view *views, int32_t n_views, const mg_raster_cfg *cfg,
+    const float *final_T, const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+    uint64_t *counters, mg_stream_t stream) {
+    return render_backward(splats, sorted_vals, ranges, tile_order, views, n_views, cfg, final_T,
+                           n_contrib, dL_dimage, grad2d, counters, stream, false);
 }
 
 extern "C" mg_status mg_l1_loss_grad(const float *image, const float *target,

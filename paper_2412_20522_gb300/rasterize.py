@@ -167,6 +167,9 @@ class Rasterizer:
         self.num_sorted = torch.zeros(1, dtype=torch.int64, device=self.device)
         self._l1_fused = False
         self._sort_mode = "radix8"
+        # records of the 2D-gradient accumulator that a fused training forward
+        # reset (0: none); the first backward after it only accumulates
+        self._grad2d_reset_R = 0
 
     # -- buffers -------------------------------------------------------------
     def _get(self, name, numel, dtype):
@@ -336,8 +339,12 @@ class Rasterizer:
             loss = self._buf["loss"][:1]           # zeroed before the preprocess
         ev.begin("render")
         if fused:
-            abi.mg_render_l1(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image,
-                             final_T, n_contrib, l1_target, dimg, loss, stream)
+            # the render kernel also resets the backward's 2D-gradient accumulator
+            grad2d = self._get("grad2d", max(R, 1) * abi.MG_GRAD2D_FLOATS, torch.float32)
+            abi.mg_render_l1_reset2d(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg,
+                                     image, final_T, n_contrib, l1_target, dimg, loss, grad2d,
+                                     stream)
+            self._grad2d_reset_R = R
         else:
             abi.mg_render(splats, sorted_vals, ranges_buf, tile_order, views, V, ccfg, image,
                           final_T, n_contrib, self.frag_count if count_fragments else None, stream)
@@ -358,7 +365,8 @@ class Rasterizer:
         return self._fwd_launches
 
     def backward_launches(self):
-        return 3                                  # 2D-gradient reset, render, preprocess
+        # 2D-gradient reset (taken by the fused render when it ran), render, preprocess
+        return 2 if self._l1_fused else 3
 
     def forward_l1(self, params: dict, cams, cfg: RasterConfig, target, view_ranges=None,
                    check=True, count_fragments=False, stage_events=None):
@@ -442,13 +450,18 @@ class Rasterizer:
             cfg = abi.mg_raster_cfg.from_buffer_copy(cfg)
             cfg.lambda_m = float(lambda_m)
         grad2d = self._get("grad2d", s["R"] * abi.MG_GRAD2D_FLOATS, torch.float32)
+        # the accumulator a fused training forward reset serves the first
+        # backward after it (same stream, same buffer); any other backward
+        # resets it itself
+        reset = 0 < s["R"] <= self._grad2d_reset_R
+        self._grad2d_reset_R = 0
         ev.begin("render_bwd")
         if count_iterations:
             self.bwd_count.zero_()
-        abi.mg_render_backward(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"],
-                               s["views"], s["V"], cfg, buf["final_T"],
-                               buf["n_contrib"], dL_dimage, grad2d,
-                               self.bwd_count if count_iterations else None, stream)
+        render_bwd = abi.mg_render_backward_accumulate if reset else abi.mg_render_backward
+        render_bwd(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"], s["views"],
+                   s["V"], cfg, buf["final_T"], buf["n_contrib"], dL_dimage, grad2d,
+                   self.bwd_count if count_iterations else None, stream)
         if out is None:
             out = {k: torch.empty(s["params"][k].shape, dtype=torch.float32, device=self.device)
                    for k in PARAM_NAMES}
