@@ -296,11 +296,18 @@ struct SortWS {
 // Digit counts of every pass in one read of the keys: a few blocks per SM,
 // each with a shared-memory histogram flushed once (the flush contends on the
 // same 256 counters per pass, so the grid stays small).
+// reset (nullable): reset_n words the caller wants zeroed before the sort's
+// later kernels (the tile ranges), cleared here in passing.
 template <typename K>
 __global__ void sort_histogram_kernel(const K *__restrict__ keys, const uint64_t *d_n,
                                       uint64_t capacity, int begin_bit, int passes, SortWS *ws,
-                                      int64_t max_parts, bool drop) {
+                                      int64_t max_parts, bool drop, uint32_t *__restrict__ reset,
+                                      int64_t reset_n) {
     grid_dependency_wait();
+    if (reset != nullptr)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < reset_n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            reset[i] = 0u;
     __shared__ uint32_t h[kMaxPasses][256];
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -591,7 +598,8 @@ template <typename K>
 static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
                             const uint64_t *d_n, uint64_t capacity, int begin_bit, int passes,
                             bool drop, SortWS *ws, mg_status_word *st, cudaStream_t s,
-                            bool *in_alt, const K *src_keys = nullptr) {
+                            bool *in_alt, const K *src_keys = nullptr,
+                            uint32_t *reset = nullptr, int64_t reset_n = 0) {
     *in_alt = (passes & 1) != 0;
     if (mg_host::zero_async(&ws->hist[0][0], sizeof(ws->hist) + sizeof(ws->counter), s) != MG_OK)
         return MG_ERR_CUDA;
@@ -603,7 +611,7 @@ static mg_status radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     const K *k0 = src_keys != nullptr ? src_keys : keys;
     launch_pdl(sort_histogram_kernel<K>,
         dim3((unsigned)(hblocks < hcap ? (hblocks > 0 ? hblocks : 1) : hcap)), dim3(512), 0, s, k0,
-        d_n, capacity, begin_bit, passes, ws, max_parts, drop);
+        d_n, capacity, begin_bit, passes, ws, max_parts, drop, reset, reset_n);
     launch_pdl(sort_offsets_kernel, dim3(passes), dim3(256), 0, s, ws);
     const size_t stage_bytes = (sizeof(K) + sizeof(uint32_t)) * (size_t)kSortPart;
     if (sort_smem_optin<K>(stage_bytes) != MG_OK) return MG_ERR_CUDA;
@@ -1152,12 +1160,16 @@ extern "C" mg_status mg_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     const int passes = (key_bits + 7) / 8;
     cudaStream_t s = (cudaStream_t)stream;
     SortWS *ws = reinterpret_cast<SortWS *>(workspace);
-    if (mg_host::zero_async(ranges, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) != MG_OK)
-        return MG_ERR_CUDA;
     bool in_alt = false;
-    // filtered instances (key kDroppedKey) leave in the first pass
+    // filtered instances (key kDroppedKey) leave in the first pass; the
+    // histogram kernel also clears the ranges (tiles with no instance keep
+    // [0, 0)) -- or a reset kernel does when there is nothing to sort
+    if (capacity == 0 &&
+        mg_host::zero_async(ranges, sizeof(uint32_t) * 2 * (size_t)n_tiles_total, s) != MG_OK)
+        return MG_ERR_CUDA;
     mg_status st = radix_sort<uint32_t>(keys, vals, keys_alt, vals_alt, d_num_instances, capacity,
-                                        0, passes, true, ws, d_status, s, &in_alt);
+                                        0, passes, true, ws, d_status, s, &in_alt, nullptr, ranges,
+                                        2 * n_tiles_total);
     if (st != MG_OK) return st;
     *result_in_alt = in_alt ? 1 : 0;
     if (capacity == 0) return mg_host::launch_status();
