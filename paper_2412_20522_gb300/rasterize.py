@@ -310,11 +310,11 @@ class Rasterizer:
         image = self._get("image", 3 * pix, torch.float32)
         # kernels of ours per forward: preprocess (with the depth keys); with
         # the radix sort: a workspace reset, histogram, offsets and 4 digit
-        # passes of the depth order, a reset, scan, duplicate, resets of the
-        # ranges and the workspace, histogram, offsets, one pass per tile
+        # passes of the depth order, a reset, scan, duplicate, a workspace
+        # reset, histogram (clearing the ranges), offsets, one pass per tile
         # digit, ranges; with the bucket sort: a reset, scan, duplicate,
         # count, scan, scatter, order; then the tile order and the render
-        sort_launches = 5 if bucket else 7 + 3 + 5 + (key_bits + 7) // 8
+        sort_launches = 5 if bucket else 7 + 3 + 4 + (key_bits + 7) // 8
         self._fwd_launches = 1 + sort_launches + (2 if bucket else 0) + 1 + \
             (tile_order is not None)
         self._sort_mode = cfg.sort
