@@ -23,6 +23,11 @@
  *   7. mg_preprocess_backward the chain rule back to the Gaussian parameters,
  *                             and through the straight-through Gumbel-softmax
  *                             to the existence scores
+ * Fused forms of the same step: mg_render_l1 takes steps 4-5 in one kernel;
+ * mg_render_l1_reset2d also resets the 2D-gradient accumulator that
+ * mg_render_backward_accumulate then adds into (step 6 without its own
+ * reset); mg_advance_iteration moves a device-side iteration on, so a step
+ * captured in a CUDA graph samples a new mask on every replay.
  *
  * Conventions
  *   - Every array pointer is a caller-owned DEVICE pointer unless the comment
