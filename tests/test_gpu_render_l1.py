@@ -41,3 +41,54 @@ def test_fused_l1_equals_separate_passes():
     for k in ga:
         scale = float(ga[k].abs().max()) + 1e-30
         assert float((ga[k] - gb[k]).abs().max()) / scale < 1e-5, k
+
+
+def test_reset_in_the_render_then_accumulating_backward():
+    """mg_render_l1_reset2d zeroes exactly the R rows of grad2d while it
+    renders (here filled with NaN first, and a sentinel past them), and
+    mg_render_backward_accumulate adding into them gives the 2D gradients of
+    mg_render_l1 + mg_render_backward (which resets the rows itself), to
+    float-atomic rounding."""
+    from paper_2412_20522_gb300 import abi
+    from paper_2412_20522_gb300.rasterize import RasterConfig, Rasterizer
+    g = scenes.cluster_gaussians(30_000, seed=52, centre_radius=1.5, reject_radius=2.0,
+                                 log_scale_mu=-4.0, log_scale_sigma=0.5)
+    cams = [scenes.ring_camera(0.7, 4.0, 150, 110, 120.0),
+            scenes.ring_camera(2.1, 4.0, 90, 70, 80.0)]
+    tgt = torch.cat([torch.as_tensor(scenes.target_image(c.height, c.width, seed=70 + k))
+                     .reshape(-1) for k, c in enumerate(cams)]).cuda()
+    p = to_device(g)
+    rast = Rasterizer()
+    img, _, dimg = rast.forward_l1(p, cams, RasterConfig(), tgt)
+    torch.cuda.synchronize()
+    s = rast._state
+    R = s["R"]
+    F = abi.MG_GRAD2D_FLOATS
+    stream = rast._stream()
+    buf = rast._buf
+    outs = []
+    for fused in (False, True):
+        g2d = torch.full((R * F + 64,), float("nan"), device="cuda")
+        g2d[R * F:] = 7.0                                   # past the rows: untouched
+        image = torch.empty_like(img)
+        dl = torch.empty_like(dimg)
+        loss = torch.zeros(1, device="cuda")
+        if fused:
+            abi.mg_render_l1_reset2d(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"],
+                                     s["views"], s["V"], s["cfg"], image, buf["final_T"],
+                                     buf["n_contrib"], tgt, dl, loss, g2d, stream)
+            backward = abi.mg_render_backward_accumulate
+        else:
+            abi.mg_render_l1(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"],
+                             s["views"], s["V"], s["cfg"], image, buf["final_T"],
+                             buf["n_contrib"], tgt, dl, loss, stream)
+            backward = abi.mg_render_backward
+        backward(s["splats"], s["sorted_vals"], s["ranges"], s["tile_order"], s["views"], s["V"],
+                 s["cfg"], buf["final_T"], buf["n_contrib"], dl, g2d, None, stream)
+        torch.cuda.synchronize()
+        assert torch.equal(image, img) and torch.equal(dl, dimg)
+        assert bool(torch.isfinite(g2d[:R * F]).all())
+        assert bool((g2d[R * F:] == 7.0).all())
+        outs.append(g2d[:R * F].clone())
+    scale = float(outs[0].abs().max()) + 1e-30
+    assert float((outs[0] - outs[1]).abs().max()) / scale < 1e-5
